@@ -1,0 +1,161 @@
+"""CPU oracle for RIANN's per-frame query step (test infrastructure only).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It wraps ``riann_oracle.c`` (plain C99 +
+OpenMP) through ctypes and numpy; it shares no code with the CUDA library.
+
+Every function takes numpy arrays in the layouts of ``riann_oracle.h``:
+frames uint8 [H][W][C], reference patches uint8 [n][8][8][C], previous ANN
+field int32 [H-7][W-7].  ``qidx`` (optional int64 list of query indices
+y*(W-7)+x) restricts the work to a sample; outputs then follow the list order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "riann_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP) into oracle/_build/liboracle.so."""
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and \
+            os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC),
+                                                os.path.getmtime(os.path.join(_HERE, "riann_oracle.h"))):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-std=c99", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall", "-Wextra",
+           "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            i32, i64, u32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+            lib.oracle_ring_member.argtypes = [u32, u32, u32, i32, i32]
+            lib.oracle_ring_member.restype = ctypes.c_int
+            lib.oracle_key_distances.argtypes = [P, i32, i32, P, i32, P]
+            lib.oracle_sort_tables.argtypes = [P, i32, i32, P, P]
+            lib.oracle_exact_nn.argtypes = [P, i32, i32, i32, P, i32, P, i64, P, P, P]
+            lib.oracle_riann_definitional.argtypes = [P, i32, i32, i32, P, i32, P, i32, P, P,
+                                                      i32, i32, i32, P, i64, P, P, P, P]
+            lib.oracle_riann_indexed.argtypes = [P, i32, i32, i32, P, i32, P, i32, P, P, P, P,
+                                                 i32, i32, i32, P, i64, P, P, P, P]
+            lib.oracle_num_threads.restype = ctypes.c_int
+            lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: Optional[np.ndarray]):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def num_threads() -> int:
+    return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    _load().oracle_set_num_threads(int(n))
+
+
+def ring_member(A: int, B: int, C: int, p: int, q: int) -> bool:
+    """Exact |sqrt(A) - sqrt(B)| <= (p/q) sqrt(C)."""
+    return bool(_load().oracle_ring_member(A, B, C, p, q))
+
+
+class Index:
+    """Oracle-side pre-processing: key-point distances and sorted per-key lists."""
+
+    def __init__(self, R: np.ndarray, KP: np.ndarray):
+        lib = _load()
+        self.R = _c(R, np.uint8)
+        self.KP = _c(KP, np.uint8)
+        self.n = self.R.shape[0]
+        self.C = self.R.shape[-1]
+        self.D = 64 * self.C
+        self.K = self.KP.shape[0]
+        assert self.R.shape[1:] == (8, 8, self.C) and self.KP.shape[1:] == (8, 8, self.C)
+        self.P = np.empty((self.n, self.K), np.uint32)
+        lib.oracle_key_distances(_ptr(self.R), self.n, self.D, _ptr(self.KP), self.K, _ptr(self.P))
+        self.TA = np.empty((self.K, self.n), np.uint32)
+        self.Tid = np.empty((self.K, self.n), np.int32)
+        lib.oracle_sort_tables(_ptr(self.P), self.n, self.K, _ptr(self.TA), _ptr(self.Tid))
+
+
+def _outputs(frame: np.ndarray, qidx):
+    H, W = frame.shape[:2]
+    shape = (len(qidx),) if qidx is not None else (H - 7, W - 7)
+    return (np.empty(shape, np.int32), np.empty(shape, np.uint32),
+            np.empty(shape, np.uint32), np.empty(shape, np.uint32))
+
+
+def _frame3(frame):
+    f = _c(frame, np.uint8)
+    return f if f.ndim == 3 else f[:, :, None]
+
+
+def exact_nn(frame: np.ndarray, R: np.ndarray, qidx=None):
+    """Brute-force exact NN field: (annf, dist, count)."""
+    lib = _load()
+    f = _frame3(frame)
+    H, W, C = f.shape
+    R = _c(R, np.uint8)
+    q = None if qidx is None else _c(qidx, np.int64)
+    annf, dist, count, _ = _outputs(f, q)
+    lib.oracle_exact_nn(_ptr(f), H, W, C, _ptr(R), R.shape[0], _ptr(q),
+                        0 if q is None else len(q), _ptr(annf), _ptr(dist), _ptr(count))
+    return annf, dist, count
+
+
+def riann_frame(index: Index, frame: np.ndarray, prev: Optional[np.ndarray],
+                alpha=(1, 4), ring_limit: int = -1, qidx=None, mode: str = "indexed"):
+    """One RIANN query step: (annf, dist, count, nseed).
+
+    prev None means frame 0 (brute force).  alpha is (num, den).  ring_limit < 0
+    never falls back to brute force.  mode is "indexed" or "definitional".
+    """
+    lib = _load()
+    f = _frame3(frame)
+    H, W, C = f.shape
+    assert C == index.C
+    q = None if qidx is None else _c(qidx, np.int64)
+    pv = None if prev is None else _c(prev, np.int32)
+    if pv is not None:
+        assert pv.shape == (H - 7, W - 7)
+    annf, dist, count, nseed = _outputs(f, q)
+    nq = 0 if q is None else len(q)
+    if mode == "definitional":
+        lib.oracle_riann_definitional(_ptr(f), H, W, C, _ptr(index.R), index.n, _ptr(index.KP),
+                                      index.K, _ptr(index.P), _ptr(pv), alpha[0], alpha[1],
+                                      ring_limit, _ptr(q), nq, _ptr(annf), _ptr(dist),
+                                      _ptr(count), _ptr(nseed))
+    elif mode == "indexed":
+        lib.oracle_riann_indexed(_ptr(f), H, W, C, _ptr(index.R), index.n, _ptr(index.KP),
+                                 index.K, _ptr(index.P), _ptr(index.TA), _ptr(index.Tid),
+                                 _ptr(pv), alpha[0], alpha[1], ring_limit, _ptr(q), nq,
+                                 _ptr(annf), _ptr(dist), _ptr(count), _ptr(nseed))
+    else:
+        raise ValueError(mode)
+    return annf, dist, count, nseed

@@ -1,0 +1,336 @@
+/*
+ * riann_oracle.c -- plain CPU oracle for RIANN's per-frame query step.
+ *
+ * TEST INFRASTRUCTURE ONLY: called by the tests, the smoke check and the CPU
+ * baseline of the benchmark; never by the product path.  Plain C99 + OpenMP
+ * over queries (queries are independent: Alg. 1 treats each query patch on its
+ * own and the method uses no spatial propagation, Sec. 6).  No blocking, no
+ * vectorisation tricks, no shared code with the CUDA library.
+ *
+ * Parity pins (tests/test_oracle_pins.py): brute force vs an independent numpy
+ * argmin; alpha = 1 reduces RIANN to exact NN (triangle inequality); alpha = 0
+ * special case; the membership test vs high-precision decimal square roots and
+ * exact-boundary perfect squares; hand-worked constant-patch fixtures under
+ * tests/golden/; definitional == indexed; key-point permutation invariance.
+ * The full alpha = 1/4 output has no external pin (the paper prints no values):
+ * parity unpinned against the paper's own outputs.
+ */
+#include "riann_oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define PATCH 8
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+void oracle_set_num_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
+/* squared L2 distance of two D-byte vectors (the paper's dist, squared; Sec. 3.1) */
+static uint32_t sqdist(const uint8_t* a, const uint8_t* b, int32_t D) {
+  uint32_t s = 0;
+  for (int32_t i = 0; i < D; ++i) {
+    int32_t d = (int32_t)a[i] - (int32_t)b[i];
+    s += (uint32_t)(d * d);
+  }
+  return s;
+}
+
+/* the 8x8xC query patch with top-left (y, x), in (dy, dx, c) order (Sec. 4) */
+static void extract_query(const uint8_t* frame, int32_t W, int32_t C, int32_t y, int32_t x,
+                          uint8_t* q) {
+  int32_t k = 0;
+  for (int32_t dy = 0; dy < PATCH; ++dy)
+    for (int32_t dx = 0; dx < PATCH; ++dx)
+      for (int32_t c = 0; c < C; ++c)
+        q[k++] = frame[((int64_t)(y + dy) * W + (x + dx)) * C + c];
+}
+
+/*
+ * Ring membership (Sec. 3.2: a ring of radius dist(anchor, q) and half-width
+ * epsilon = alpha * dist(q, r_i); Alg. 1 candidate-set conditions
+ * d - eps <= dist(anchor, r) <= d + eps).  With A = ||k - r||^2,
+ * B = ||k - q||^2, C = ||q - r_p||^2 and alpha = p/q the condition is
+ *     |sqrt(A) - sqrt(B)| <= (p/q) sqrt(C).
+ * Squaring both (non-negative) sides:
+ *     q^2 (A + B) - p^2 C <= 2 q^2 sqrt(A B).
+ * Writing L for the left side, it holds when L <= 0, else iff L^2 <= 4 q^4 A B.
+ * Evaluated in 128-bit integers, so there is no rounding anywhere.
+ */
+int oracle_ring_member(uint32_t A, uint32_t B, uint32_t C, int32_t p, int32_t q) {
+  __int128 qq = (__int128)q * q;
+  __int128 L = qq * ((__int128)A + (__int128)B) - (__int128)p * p * (__int128)C;
+  if (L <= 0) return 1;
+  unsigned __int128 lhs = (unsigned __int128)L * (unsigned __int128)L;
+  unsigned __int128 rhs = (unsigned __int128)4 * (unsigned __int128)(qq * qq) *
+                          (unsigned __int128)A * (unsigned __int128)B;
+  return lhs <= rhs;
+}
+
+/* Distances from every reference to every key point (Sec. 3.3 pre-processing:
+ * the distance lists, here only towards the K fixed anchors). */
+void oracle_key_distances(const uint8_t* R, int32_t n, int32_t D,
+                          const uint8_t* KP, int32_t K, uint32_t* P) {
+#pragma omp parallel for schedule(static)
+  for (int32_t r = 0; r < n; ++r)
+    for (int32_t m = 0; m < K; ++m)
+      P[(int64_t)r * K + m] = sqdist(KP + (int64_t)m * D, R + (int64_t)r * D, D);
+}
+
+typedef struct { uint32_t a; int32_t id; } entry_t;
+
+static int cmp_entry(const void* x, const void* y) {
+  const entry_t* u = (const entry_t*)x;
+  const entry_t* v = (const entry_t*)y;
+  if (u->a != v->a) return u->a < v->a ? -1 : 1;
+  if (u->id != v->id) return u->id < v->id ? -1 : 1;
+  return 0;
+}
+
+/* Sorted lists (Sec. 3.3: "for each reference patch a sorted list of its
+ * distances", here one list per key point), ascending by (distance, index). */
+void oracle_sort_tables(const uint32_t* P, int32_t n, int32_t K, uint32_t* TA, int32_t* Tid) {
+#pragma omp parallel for schedule(static)
+  for (int32_t m = 0; m < K; ++m) {
+    entry_t* e = (entry_t*)malloc(sizeof(entry_t) * (size_t)n);
+    for (int32_t r = 0; r < n; ++r) { e[r].a = P[(int64_t)r * K + m]; e[r].id = r; }
+    qsort(e, (size_t)n, sizeof(entry_t), cmp_entry);
+    for (int32_t j = 0; j < n; ++j) {
+      TA[(int64_t)m * n + j] = e[j].a;
+      Tid[(int64_t)m * n + j] = e[j].id;
+    }
+    free(e);
+  }
+}
+
+/* argmin over all of R with the lower index winning ties (exact NN; used for
+ * the frame-0 initialisation and for queries whose rings are too wide) */
+static void brute_force(const uint8_t* q, const uint8_t* R, int32_t n, int32_t D,
+                        int32_t* best_id, uint32_t* best_d) {
+  int32_t bi = 0;
+  uint32_t bd = sqdist(q, R, D);
+  for (int32_t r = 1; r < n; ++r) {
+    uint32_t d = sqdist(q, R + (int64_t)r * D, D);
+    if (d < bd) { bd = d; bi = r; }
+  }
+  *best_id = bi;
+  *best_d = bd;
+}
+
+static int64_t query_at(const int64_t* qidx, int64_t i) { return qidx ? qidx[i] : i; }
+
+void oracle_exact_nn(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                     const uint8_t* R, int32_t n,
+                     const int64_t* qidx, int64_t nq,
+                     int32_t* annf, uint32_t* dist, uint32_t* count) {
+  const int32_t D = PATCH * PATCH * C;
+  const int32_t Wq = W - PATCH + 1;
+  const int64_t Q = (int64_t)(H - PATCH + 1) * Wq;
+  const int64_t N = qidx ? nq : Q;
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < N; ++i) {
+    uint8_t q[PATCH * PATCH * 3];
+    int64_t qi = query_at(qidx, i);
+    extract_query(frame, W, C, (int32_t)(qi / Wq), (int32_t)(qi % Wq), q);
+    int32_t bi; uint32_t bd;
+    brute_force(q, R, n, D, &bi, &bd);
+    annf[i] = bi;
+    if (dist) dist[i] = bd;
+    if (count) count[i] = (uint32_t)n;
+  }
+}
+
+/*
+ * Definitional mode.  Alg. 1 for one query, in the paper's order:
+ *   r_p = ANNF^(t-1)(x, y);  d = dist(q, r_p);  eps = alpha * d
+ *   candidate set = references inside every ring (here the K key-point rings)
+ *   ANNF^(t)(x, y) = argmin over the candidates (and r_p) of dist(q, s)
+ * Every ring is evaluated over all references with the exact predicate.
+ */
+void oracle_riann_definitional(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                               const uint8_t* R, int32_t n,
+                               const uint8_t* KP, int32_t K, const uint32_t* P,
+                               const int32_t* prev, int32_t alpha_num, int32_t alpha_den,
+                               int32_t ring_limit,
+                               const int64_t* qidx, int64_t nq,
+                               int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* nseed) {
+  const int32_t D = PATCH * PATCH * C;
+  const int32_t Wq = W - PATCH + 1;
+  const int64_t Q = (int64_t)(H - PATCH + 1) * Wq;
+  const int64_t N = qidx ? nq : Q;
+#pragma omp parallel
+  {
+    uint8_t q[PATCH * PATCH * 3];
+    uint32_t* B = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)K);
+    uint32_t* ring_size = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)K);
+    uint8_t* in_all = (uint8_t*)malloc((size_t)n);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < N; ++i) {
+      int64_t qi = query_at(qidx, i);
+      extract_query(frame, W, C, (int32_t)(qi / Wq), (int32_t)(qi % Wq), q);
+      if (!prev) {                                   /* frame 0: exact NN */
+        int32_t bi; uint32_t bd;
+        brute_force(q, R, n, D, &bi, &bd);
+        annf[i] = bi;
+        if (dist) dist[i] = bd;
+        if (count) count[i] = (uint32_t)n;
+        if (nseed) nseed[i] = 0;
+        continue;
+      }
+      const int32_t rp = prev[qi];
+      const uint32_t Cd = sqdist(q, R + (int64_t)rp * D, D);      /* dist(q, r_p)^2 */
+      for (int32_t m = 0; m < K; ++m) B[m] = sqdist(q, KP + (int64_t)m * D, D);
+      for (int32_t m = 0; m < K; ++m) ring_size[m] = 0;
+      uint32_t s_size = 0;
+      for (int32_t r = 0; r < n; ++r) {
+        int inside = 1;
+        for (int32_t m = 0; m < K; ++m) {
+          int mem = oracle_ring_member(P[(int64_t)r * K + m], B[m], Cd, alpha_num, alpha_den);
+          ring_size[m] += (uint32_t)mem;
+          inside &= mem;
+        }
+        in_all[r] = (uint8_t)inside;
+        s_size += (uint32_t)inside;
+      }
+      uint32_t ns = ring_size[0];
+      for (int32_t m = 1; m < K; ++m) if (ring_size[m] < ns) ns = ring_size[m];
+      if (nseed) nseed[i] = ns;
+      if (ring_limit >= 0 && ns > (uint32_t)ring_limit) {   /* rings too wide: brute force */
+        int32_t bi; uint32_t bd;
+        brute_force(q, R, n, D, &bi, &bd);
+        annf[i] = bi;
+        if (dist) dist[i] = bd;
+        if (count) count[i] = (uint32_t)n;
+        continue;
+      }
+      int32_t bi = rp;                                /* r_p is always verified */
+      uint32_t bd = Cd;
+      for (int32_t r = 0; r < n; ++r) {
+        if (!in_all[r]) continue;
+        uint32_t d = sqdist(q, R + (int64_t)r * D, D);
+        if (d < bd || (d == bd && r < bi)) { bd = d; bi = r; }
+      }
+      annf[i] = bi;
+      if (dist) dist[i] = bd;
+      if (count) count[i] = s_size;
+    }
+    free(B); free(ring_size); free(in_all);
+  }
+}
+
+/* A sorted list splits into three runs around a ring: references below it
+ * (not members, A < B), the members, and references above it (not members,
+ * A > B).  The members are one contiguous run because |sqrt(A) - sqrt(B)|
+ * falls and then rises as A grows. */
+typedef struct { const uint32_t* a; uint32_t B, C; int32_t p, q; int below; } ring_pred_t;
+
+/* below == 1: "strictly below the ring";  below == 0: "not above the ring".
+ * Either predicate is true on a prefix of the sorted list. */
+static int in_prefix(const ring_pred_t* s, uint32_t A) {
+  int mem = oracle_ring_member(A, s->B, s->C, s->p, s->q);
+  if (s->below) return !mem && A < s->B;
+  return mem || A <= s->B;
+}
+
+/* first j in [lo, hi) where the prefix predicate is false (binary search) */
+static int32_t partition_point(const ring_pred_t* s, int32_t lo, int32_t hi) {
+  while (lo < hi) {
+    int32_t mid = lo + (hi - lo) / 2;
+    if (in_prefix(s, s->a[mid])) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+/*
+ * Indexed mode (Sec. 3.3): each ring is found with two binary searches in the
+ * sorted list of its anchor; the candidates are the members of the smallest
+ * ring that lie inside every other ring; then the argmin of Alg. 1.
+ */
+void oracle_riann_indexed(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                          const uint8_t* R, int32_t n,
+                          const uint8_t* KP, int32_t K, const uint32_t* P,
+                          const uint32_t* TA, const int32_t* Tid,
+                          const int32_t* prev, int32_t alpha_num, int32_t alpha_den,
+                          int32_t ring_limit,
+                          const int64_t* qidx, int64_t nq,
+                          int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* nseed) {
+  const int32_t D = PATCH * PATCH * C;
+  const int32_t Wq = W - PATCH + 1;
+  const int64_t Q = (int64_t)(H - PATCH + 1) * Wq;
+  const int64_t N = qidx ? nq : Q;
+#pragma omp parallel
+  {
+    uint8_t q[PATCH * PATCH * 3];
+    uint32_t* B = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)K);
+    int32_t* lo = (int32_t*)malloc(sizeof(int32_t) * (size_t)K);
+    int32_t* hi = (int32_t*)malloc(sizeof(int32_t) * (size_t)K);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < N; ++i) {
+      int64_t qi = query_at(qidx, i);
+      extract_query(frame, W, C, (int32_t)(qi / Wq), (int32_t)(qi % Wq), q);
+      if (!prev) {
+        int32_t bi; uint32_t bd;
+        brute_force(q, R, n, D, &bi, &bd);
+        annf[i] = bi;
+        if (dist) dist[i] = bd;
+        if (count) count[i] = (uint32_t)n;
+        if (nseed) nseed[i] = 0;
+        continue;
+      }
+      const int32_t rp = prev[qi];
+      const uint32_t Cd = sqdist(q, R + (int64_t)rp * D, D);
+      int32_t seed = 0;
+      for (int32_t m = 0; m < K; ++m) {
+        B[m] = sqdist(q, KP + (int64_t)m * D, D);
+        ring_pred_t s = { TA + (int64_t)m * n, B[m], Cd, alpha_num, alpha_den, 1 };
+        lo[m] = partition_point(&s, 0, n);
+        s.below = 0;
+        hi[m] = partition_point(&s, lo[m], n);
+        if (hi[m] - lo[m] < hi[seed] - lo[seed]) seed = m;
+      }
+      const uint32_t ns = (uint32_t)(hi[seed] - lo[seed]);
+      if (nseed) nseed[i] = ns;
+      if (ring_limit >= 0 && ns > (uint32_t)ring_limit) {
+        int32_t bi; uint32_t bd;
+        brute_force(q, R, n, D, &bi, &bd);
+        annf[i] = bi;
+        if (dist) dist[i] = bd;
+        if (count) count[i] = (uint32_t)n;
+        continue;
+      }
+      int32_t bi = rp;
+      uint32_t bd = Cd, s_size = 0;
+      for (int32_t j = lo[seed]; j < hi[seed]; ++j) {
+        const int32_t r = Tid[(int64_t)seed * n + j];
+        int inside = 1;
+        for (int32_t m = 0; m < K && inside; ++m) {
+          if (m == seed) continue;
+          inside = oracle_ring_member(P[(int64_t)r * K + m], B[m], Cd, alpha_num, alpha_den);
+        }
+        if (!inside) continue;
+        ++s_size;
+        uint32_t d = sqdist(q, R + (int64_t)r * D, D);
+        if (d < bd || (d == bd && r < bi)) { bd = d; bi = r; }
+      }
+      annf[i] = bi;
+      if (dist) dist[i] = bd;
+      if (count) count[i] = s_size;
+    }
+    free(B); free(lo); free(hi);
+  }
+}

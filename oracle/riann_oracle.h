@@ -1,0 +1,86 @@
+/*
+ * riann_oracle.h -- plain, slow, obviously-correct CPU oracle for RIANN's
+ * per-frame query step (Ben-Zrihem & Zelnik-Manor, "Approximate Nearest
+ * Neighbor Fields in Video", arXiv 1508.07953).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline of the benchmark call this code.  It shares no code with the CUDA
+ * library and includes none of its headers.
+ *
+ * Conventions (all integer):
+ *   patch      8x8xC uint8, vector order (dy, dx, c)  -- D = 64*C bytes
+ *   frame      uint8 [H][W][C], row-major
+ *   query q    top-left corner (y, x), 0 <= y < H-7, 0 <= x < W-7,
+ *              query index = y*(W-7) + x                      (Sec. 4: all patches)
+ *   dist       squared L2 over the D bytes, exact in uint32  (<= 192*255^2)
+ *   ANN field  int32 [H-7][W-7] of 0-based reference indices  (Alg. 1 output)
+ *
+ * Reading of the method taken here (fixed key points, Sec. 3.2 rings):
+ *   ring of key point k_m for query q, with previous match r_p:
+ *       Ring_m = { r : | ||k_m - r|| - ||k_m - q|| | <= alpha * ||q - r_p|| }
+ *   (rings of Sec. 3.2 / Alg. 1, with the anchors fixed to K key points and the
+ *    half-width epsilon = alpha * dist(q, r_p) of Alg. 1's first ring for all rings)
+ *   S = intersection of all K rings;  N_seed = min_m |Ring_m|
+ *   if N_seed > ring_limit (ring_limit >= 0): brute force over all of R, count = n
+ *   else ANNF(q) = argmin over S u {r_p} of dist(q, r), count = |S|
+ *   with ties broken by the lower reference index.
+ *   Frame 0 (no previous field): brute force, count = n.
+ */
+#ifndef RIANN_ORACLE_H
+#define RIANN_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Exact ring membership |sqrt(A) - sqrt(B)| <= (p/q) sqrt(C) (Sec. 3.2). */
+int oracle_ring_member(uint32_t A, uint32_t B, uint32_t C, int32_t p, int32_t q);
+
+/* P[r*K + m] = ||k_m - R_r||^2 (Sec. 3.3 pre-processing, restricted to key points). */
+void oracle_key_distances(const uint8_t* R, int32_t n, int32_t D,
+                          const uint8_t* KP, int32_t K, uint32_t* P);
+
+/* Per key point m, the references sorted ascending by (P[r][m], r):
+ * TA[m*n + j] = distance, Tid[m*n + j] = reference index (Sec. 3.3 sorted lists). */
+void oracle_sort_tables(const uint32_t* P, int32_t n, int32_t K, uint32_t* TA, int32_t* Tid);
+
+/* Exact nearest neighbour by brute force (frame-0 initialisation).
+ * qidx: optional list of nq query indices (NULL = all, nq ignored);
+ * outputs are indexed by list position.  count[i] = n. */
+void oracle_exact_nn(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                     const uint8_t* R, int32_t n,
+                     const int64_t* qidx, int64_t nq,
+                     int32_t* annf, uint32_t* dist, uint32_t* count);
+
+/* RIANN query step, definitional mode: every ring is evaluated by the exact
+ * predicate over all n references.  prev == NULL means frame 0 (brute force).
+ * nseed (nullable) receives min_m |Ring_m| (0 for brute-forced frame-0 queries). */
+void oracle_riann_definitional(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                               const uint8_t* R, int32_t n,
+                               const uint8_t* KP, int32_t K, const uint32_t* P,
+                               const int32_t* prev, int32_t alpha_num, int32_t alpha_den,
+                               int32_t ring_limit,
+                               const int64_t* qidx, int64_t nq,
+                               int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* nseed);
+
+/* RIANN query step, indexed mode: ring bounds by binary search on the sorted
+ * per-key lists (Sec. 3.3, "two binary searches"), candidates enumerated from
+ * the smallest ring and filtered by the other rings. */
+void oracle_riann_indexed(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                          const uint8_t* R, int32_t n,
+                          const uint8_t* KP, int32_t K, const uint32_t* P,
+                          const uint32_t* TA, const int32_t* Tid,
+                          const int32_t* prev, int32_t alpha_num, int32_t alpha_den,
+                          int32_t ring_limit,
+                          const int64_t* qidx, int64_t nq,
+                          int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* nseed);
+
+/* Number of OpenMP threads the oracle uses (1 when built without OpenMP). */
+int oracle_num_threads(void);
+void oracle_set_num_threads(int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
