@@ -1,0 +1,192 @@
+/*
+ * riann.h -- C ABI of the RIANN per-frame query engine for NVIDIA GB300
+ * (sm_103a).  RIANN: Ben-Zrihem & Zelnik-Manor, "Approximate Nearest Neighbor
+ * Fields in Video" (arXiv 1508.07953).
+ *
+ * Problem (Sec. 1, Fig. 1; Alg. 1 inputs/outputs): a fixed set R of n
+ * reference patches, a stream of video frames, and for every frame a dense
+ * ANN field: for each overlapping 8x8 patch of the frame, the index of a near
+ * reference patch.
+ *
+ * Layouts (all integer, all row-major, no padding):
+ *   patch      uint8 [8][8][C], element order (dy, dx, c); D = 64*C; C in {1, 3}
+ *   frame      uint8 [H][W][C]
+ *   ANN field  int32 [H-7][W-7]; entry (y, x) belongs to the patch whose
+ *              top-left pixel is (y, x) (stride 1, valid region only)
+ *   distance   squared L2 over the D bytes, uint32 (at most 192*255^2)
+ *
+ * Method as computed here (fixed key points k_0..k_{K-1}; Sec. 3.2, Alg. 1):
+ *   eps(q)   = alpha * ||q - r_p||, r_p = previous field at the same position
+ *   Ring_m   = { r : | ||k_m - r|| - ||k_m - q|| | <= eps(q) }   (closed, exact)
+ *   S        = intersection of the K rings
+ *   if min_m |Ring_m| > ring_limit (ring_limit >= 0): brute force over R,
+ *       count = n
+ *   else field(q) = argmin over S u {r_p} of ||q - r||^2, count = |S|
+ *   ties go to the lower reference index.  With no previous field (frame 0,
+ *   Alg. 1 "Initialize") every query is answered by brute force.
+ * Membership is decided exactly in integers, so results are bit-reproducible.
+ *
+ * Memory ownership: the caller owns every buffer it passes in; the library
+ * owns what it allocates (index tables, scratch) and frees it in the matching
+ * destroy call.  Device pointers must point to memory of the current device.
+ *
+ * Execution: every call is asynchronous on the given stream unless its
+ * comment says otherwise.  Calls that share an index share its scratch, so
+ * they must be ordered on one stream (or use separate sessions).
+ *
+ * Errors: every int-returning call returns RIANN_OK (0) or one of the codes
+ * below; argument errors are detected on the host before any work is queued.
+ * Errors found by a kernel (e.g. a previous-field entry outside [0, n)) are
+ * OR-ed into a per-index device status word read by riann_status().
+ */
+#ifndef RIANN_H
+#define RIANN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+struct CUstream_st;
+typedef struct CUstream_st* riann_stream_t;
+
+typedef struct riann_index_s* riann_index_t;
+
+enum {
+  RIANN_OK = 0,
+  RIANN_ERR_INVALID_ARG = 1,  /* a size, pointer or parameter is out of range   */
+  RIANN_ERR_OOM = 2,          /* a device or pinned-host allocation failed        */
+  RIANN_ERR_UNSUPPORTED = 3,  /* device is not sm_103 / feature not built         */
+  RIANN_ERR_CUDA = 4,         /* a CUDA runtime call failed                       */
+  RIANN_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                    */
+  RIANN_ERR_ADMISSION = 6,    /* server: the stream does not fit the budget       */
+  RIANN_ERR_DEVICE = 7        /* a kernel reported bad input (see riann_status)   */
+};
+
+/* Bits of the device status word. */
+#define RIANN_DEV_BAD_PREV 0x1u   /* a previous-field entry was outside [0, n)  */
+#define RIANN_DEV_BOUNDS 0x2u     /* ring-bound refinement did not converge      */
+#define RIANN_DEV_TIMEOUT 0x4u    /* a bounded spin-wait in a kernel gave up      */
+
+typedef struct {
+  /* Ring half-width eps = (alpha_num / alpha_den) * dist(q, r_p)
+   * (Sec. 3.2: "epsilon = alpha * dist(r_i, q)", alpha = 0.25 in the paper).
+   * 1 <= alpha_den <= 8, 0 <= alpha_num <= 8 * alpha_den. */
+  int32_t alpha_num;
+  int32_t alpha_den;
+  /* A query whose smallest ring holds more than ring_limit references is
+   * answered by brute force over all of R (count = n).  -1: never. */
+  int32_t ring_limit;
+  /* Performance knob only (candidate-scan granularity threshold); results
+   * never depend on it.  0 = library default. */
+  int32_t cap;
+} riann_params;
+
+/* alpha = 1/4 (Sec. 3.2), ring_limit = n/8, cap = 0. */
+riann_params riann_default_params(int32_t n);
+
+typedef struct {
+  int32_t n, K, channels, dim;   /* dim = 64 * channels */
+  size_t device_bytes;           /* bytes of device memory the index holds */
+} riann_index_info_t;
+
+/*
+ * Pre-processing (Sec. 3.3 "at the pre-processing stage we compute ... a
+ * sorted list of its distances"; Sec. 3.4 "Building a reference model").
+ * Copies the n reference patches and K key points, computes every
+ * key-point-to-reference distance and, per key point, the references sorted by
+ * (distance, index); also a bf16 copy of R for the brute-force path.
+ *   d_patches   device uint8 [n][8][8][channels]; 1 <= n <= 2^24
+ *   d_keypoints device uint8 [K][8][8][channels]; 1 <= K <= 64
+ *   channels    1 or 3
+ * Asynchronous on `stream`; inputs may be freed once the stream reaches the
+ * end of the build.  *out receives the handle (NULL on error).
+ */
+int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t channels,
+                                const uint8_t* d_keypoints, int32_t K,
+                                riann_stream_t stream, riann_index_t* out);
+
+/* Synchronises the device and frees the index and its scratch.  NULL is a no-op. */
+void riann_index_destroy(riann_index_t idx);
+
+int riann_index_info(riann_index_t idx, riann_index_info_t* out);
+
+/*
+ * Copies the pre-processed tables into caller buffers (device or host
+ * pointers; each nullable), for inspection and testing (Sec. 3.3 lists):
+ *   P    uint32 [n][K]  squared distance of reference r to key point m
+ *   TA   uint32 [K][n]  per key point, those distances in ascending order
+ *   Tid  int32  [K][n]  per key point, the reference index of each TA entry
+ *                       (ties in distance ordered by index)
+ * Synchronous (returns after the copies completed on `stream`).
+ */
+int riann_index_tables(riann_index_t idx, riann_stream_t stream,
+                       uint32_t* P, uint32_t* TA, int32_t* Tid);
+
+/*
+ * One RIANN query step over a whole frame (Alg. 1, one iteration of the
+ * frame loop: every query patch of the frame).
+ *   d_frame       device uint8 [H][W][channels]; 8 <= H, W; (H-7)*(W-7) < 2^31
+ *   d_prev_annf   device int32 [H-7][W-7], the previous field; NULL = frame 0
+ *                 (every query answered by brute force, Alg. 1 "Initialize")
+ *   d_out_annf    device int32 [H-7][W-7] (required; may not alias d_prev_annf)
+ *   d_out_dist    device uint32 [H-7][W-7], squared distance of the match (nullable)
+ *   d_out_count   device uint32 [H-7][W-7], |S| or n for brute force (nullable)
+ * Asynchronous on `stream`.  Uses the index's scratch (grown on first use of
+ * a larger frame, which allocates and synchronises).
+ */
+int riann_annf_frame(riann_index_t idx, const riann_params* p, riann_stream_t stream,
+                     const uint8_t* d_frame, int32_t H, int32_t W,
+                     const int32_t* d_prev_annf, int32_t* d_out_annf,
+                     uint32_t* d_out_dist, uint32_t* d_out_count);
+
+/*
+ * Brute-force exact nearest neighbour field (the dense tensor-core path on its
+ * own; Alg. 1 "Initialize" replaced by exact NN).  Arguments as riann_annf_frame.
+ */
+int riann_exact_nn(riann_index_t idx, riann_stream_t stream,
+                   const uint8_t* d_frame, int32_t H, int32_t W,
+                   int32_t* d_out_annf, uint32_t* d_out_dist);
+
+/* Work counters of the most recent riann_annf_frame / riann_exact_nn call on
+ * this index (the work measure of Sec. 3.3 / Fig. 5: rings and candidates
+ * grow with temporal change). */
+typedef struct {
+  uint64_t ring_queries;     /* queries answered by ring intersection           */
+  uint64_t dense_queries;    /* queries answered by brute force (incl. frame 0)  */
+  uint64_t sum_seed;         /* sum over ring queries of min_m |Ring_m|         */
+  uint64_t sum_candidates;   /* sum over ring queries of |S|                    */
+} riann_frame_stats_t;
+
+/* Synchronises `stream` and reads the counters. */
+int riann_frame_stats(riann_index_t idx, riann_stream_t stream, riann_frame_stats_t* out);
+
+/*
+ * Per-kernel timing.  When enabled, every kernel of a frame is bracketed by
+ * CUDA events recorded on the frame's stream.  riann_profile_read
+ * synchronises `stream` and writes, per slot, the duration in milliseconds of
+ * that kernel's most recent launch (-1 if it did not run since the last read):
+ *   slot 0  ring-intersection kernel (patch, key distances, rings, verification)
+ *   slot 1  brute-force kernel (frame 0 and queries routed to it)
+ *   slot 2  query-row preparation of the brute-force path
+ */
+#define RIANN_SLOT_RING 0
+#define RIANN_SLOT_DENSE 1
+#define RIANN_SLOT_PREP 2
+int riann_profile_enable(riann_index_t idx, int on);
+int riann_profile_read(riann_index_t idx, riann_stream_t stream, float* ms, int32_t nslots);
+
+/* Synchronises `stream`, then returns RIANN_OK if the device status word is
+ * clear, RIANN_ERR_DEVICE otherwise (and clears it); *bits (nullable) receives
+ * the word. */
+int riann_status(riann_index_t idx, riann_stream_t stream, uint32_t* bits);
+
+const char* riann_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIANN_H */

@@ -1,0 +1,119 @@
+// common.cuh -- internal declarations of the RIANN CUDA library (sm_103a).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+
+#include "../../include/riann.h"
+
+namespace riann {
+
+constexpr int kPatch = 8;
+constexpr int kMaxK = 64;
+constexpr int kMaxDim = 192;
+constexpr int kDenseTileN = 256;   // reference rows per tensor-core tile
+constexpr int kDenseTileM = 128;   // query rows per tensor-core tile
+
+// Work counters of the last frame (riann_frame_stats).
+enum StatSlot { kStatRingQueries = 0, kStatDenseQueries, kStatSumSeed, kStatSumS, kStats = 8 };
+
+// Kernel slots of the per-kernel event profiler (riann_profile_*).
+enum KernelSlot { kSlotSparse = 0, kSlotDense = 1, kSlotPrep = 2, kSlots = 4 };
+
+// Largest possible squared distance between two patches of `dim` bytes.
+__host__ __device__ constexpr uint32_t max_sqdist(int dim) { return (uint32_t)dim * 255u * 255u; }
+
+// Device-resident index (Sec. 3.3 pre-processing restricted to K key points).
+struct Index {
+  int device = 0;
+  int n = 0, K = 0, C = 0, D = 0;
+  int n_pad = 0;                  // n rounded up to kDenseTileN
+  uint8_t* R = nullptr;           // [n][D] reference patches
+  uint8_t* KP = nullptr;          // [K][D] key points
+  __nv_bfloat16* Rbf = nullptr;   // [n_pad][D] bf16 copy (exact: values 0..255); pad rows zero
+  float* rnorm = nullptr;         // [n_pad] ||r||^2 (exact integers in fp32); pad rows +inf
+  uint32_t* P = nullptr;          // [n][K] ||k_m - r||^2
+  uint32_t* TA = nullptr;         // [K][n] per key: distances ascending
+  int32_t* Tid = nullptr;         // [K][n] per key: reference index of each TA entry
+  uint32_t* status = nullptr;     // device status word (RIANN_DEV_* bits)
+  unsigned long long* stats = nullptr;  // [kStats] counters of the last frame
+  size_t device_bytes = 0;
+
+  // optional per-kernel timing with CUDA events recorded on the launch stream
+  bool profile = false;
+  bool prof_recorded[kSlots] = {};
+  cudaEvent_t prof_ev[kSlots][2] = {};
+
+  // scratch for riann_annf_frame / riann_exact_nn, sized in queries
+  std::mutex mu;
+  int64_t scratch_q = 0;
+  int32_t* dense_list = nullptr;  // [scratch_q] queries routed to brute force
+  uint32_t* dense_count = nullptr;
+  unsigned long long* best = nullptr;   // [scratch_q] packed (dist << 32 | index)
+  __nv_bfloat16* Aq = nullptr;    // [scratch_q padded to 128][D] bf16 query rows
+  uint32_t* qnorm = nullptr;      // [scratch_q padded] ||q||^2
+
+  // TMA descriptors of the brute-force operands
+  CUtensorMap tmRbf;              // Rbf rows, box 64 x (reference rows per tile)
+  CUtensorMap tmAq;               // Aq rows, box 64 x 128
+  bool tm_ready = false;          // both maps encoded
+};
+
+// Arguments of the fused sparse query kernel (a1-a4).
+struct SparseArgs {
+  const uint8_t* frame;
+  int H, W, Hq, Wq;
+  const int32_t* prev;
+  int32_t* out_annf;
+  uint32_t* out_dist;
+  uint32_t* out_count;
+  const uint8_t* R;
+  const uint8_t* KP;
+  const uint32_t* P;
+  const uint32_t* TA;
+  const int32_t* Tid;
+  int n, K;
+  int alpha_num, alpha_den, ring_limit;
+  int32_t* dense_list;
+  uint32_t* dense_count;
+  uint32_t* status;
+  unsigned long long* stats;      // nullable
+};
+
+// Arguments of the brute-force path (a5).
+struct DenseArgs {
+  const uint8_t* frame;
+  int H, W, Hq, Wq;
+  int64_t Q;                      // queries in the frame
+  const int32_t* list;            // nullptr: all queries in order
+  const uint32_t* list_count;     // device count of `list` (nullptr: Q)
+  int32_t* out_annf;
+  uint32_t* out_dist;
+  uint32_t* out_count;
+  const uint8_t* R;
+  int n;
+  unsigned long long* stats;      // nullable; a whole-frame launch records Q brute-force queries
+};
+
+// Record the start/end event of a profiled kernel slot (no-op when profiling is off).
+void prof_begin(Index& ix, int slot, cudaStream_t s);
+void prof_end(Index& ix, int slot, cudaStream_t s);
+
+// 2-D SWIZZLE_128B tensor map over bf16 rows of D elements.
+bool make_row_map(CUtensorMap* m, const void* base, uint64_t rows, int D, int box_rows);
+int dense_ref_rows_per_tile(int C);
+cudaError_t launch_dense_tc(const DenseArgs& a, Index& ix, cudaStream_t s);
+
+// launchers (return cudaGetLastError())
+cudaError_t launch_index_build(Index& ix, cudaStream_t s);
+cudaError_t launch_sparse(const SparseArgs& a, int C, cudaStream_t s);
+cudaError_t launch_dense(const DenseArgs& a, Index& ix, cudaStream_t s);
+
+int sm_count();
+
+}  // namespace riann

@@ -1,0 +1,557 @@
+// dense_tc.cu -- brute-force exact nearest neighbours on the 5th-generation
+// tensor cores (tcgen05 + TMEM + TMA, sm_103a).  Used for the frame-0
+// initialisation and for queries whose rings are too wide.
+//
+// argmin_r ||q - r||^2 = argmin_r (||r||^2 - 2 q.r).  The dot products q.r are
+// one GEMM  S = Aq * R^T  with Aq [queries][D] and R [refs][D] in bf16.  uint8
+// values 0..255 are exact in bf16, every product is exact in fp32 and every
+// partial sum is a non-negative integer below 192*255^2 < 2^24, so the fp32
+// accumulation is exact and the argmin is bit-identical to integer arithmetic.
+// (INT8 MMA, tcgen05 kind::i8, is not available on sm_103a.)
+//
+// Pipeline per CTA (persistent, one CTA per SM, 12 warps):
+//   warp 0      TMA producer: one query tile (128 rows) per work item, then a
+//               ring of reference tiles (BN rows), SWIZZLE_128B layout
+//   warp 1      TMEM allocator and MMA issuer (one thread): D/16 MMAs of
+//               128 x BN x 16 per reference tile into one of two TMEM
+//               accumulators
+//   warps 4-11  epilogue: tcgen05.ld of the accumulator (2 warps per TMEM lane
+//               quadrant, each half the columns), fused ||r||^2 - 2 q.r and a
+//               running (value, index) minimum per query row; results merge
+//               across work items with a 64-bit atomicMin on (dist << 32 | index)
+// Every wait is bounded; on timeout the CTA records RIANN_DEV_TIMEOUT, drains
+// and frees its TMEM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+
+namespace riann {
+namespace {
+
+constexpr int kM = 128;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = (4 + kEpiWarps) * 32;
+constexpr long long kSpinLimit = 2000000000LL;   // clock cycles (about 1 s)
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int C>
+struct Cfg;
+template <>
+struct Cfg<1> {
+  static constexpr int D = 64, ATOMS = 1, BN = 256, STAGES = 4, TMEM_COLS = 512;
+};
+template <>
+struct Cfg<3> {
+  static constexpr int D = 192, ATOMS = 3, BN = 128, STAGES = 3, TMEM_COLS = 256;
+};
+
+template <int C>
+constexpr int smem_bytes() {
+  using G = Cfg<C>;
+  return 1024 /* alignment slack */ + G::ATOMS * kM * 128 + G::STAGES * G::ATOMS * G::BN * 128 + 256;
+}
+
+struct TcArgs {
+  CUtensorMap tmA;                // Aq  [rows][D] bf16, box 64 x 128
+  CUtensorMap tmB;                // Rbf [n_pad][D] bf16, box 64 x BN
+  const float* rnorm;             // [n_pad]
+  const uint32_t* qnorm;          // [rows]
+  const uint32_t* count;          // device count of query rows (nullptr: Qfix)
+  int64_t Qfix;
+  int n_pad;
+  unsigned long long* best;       // [rows] packed (dist << 32 | index), pre-set to ~0
+  uint32_t* status;
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase with the given parity; false on timeout/abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kSpinLimit) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 B, 8-row groups 1024 B apart (the layout TMA SWIZZLE_128B writes).
+__device__ __forceinline__ uint64_t sw128_desc(const void* p) {
+  const uint32_t addr = smem_u32(p);
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);   // start address >> 4
+  d |= (uint64_t)1 << 16;                           // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                           // descriptor version for sm_100 family
+  d |= (uint64_t)2 << 61;                           // layout: SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+        "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+        "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+        "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ float min3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// the GEMM + argmin kernel
+// ---------------------------------------------------------------------------
+template <int C>
+__global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant__ TcArgs a) {
+  using G = Cfg<C>;
+  constexpr uint32_t IDESC = instr_desc(kM, G::BN);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;                                        // [ATOMS][128][128 B]
+  uint8_t* sB = sA + G::ATOMS * kM * 128;                    // [STAGES][ATOMS][BN][128 B]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + G::STAGES * G::ATOMS * G::BN * 128);
+  uint64_t* full = bars;
+  uint64_t* empty = full + G::STAGES;
+  uint64_t* tfull = empty + G::STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* afull = tempty + 2;
+  uint64_t* aempty = afull + 1;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(aempty + 1);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t Qd = a.count ? (int64_t)*a.count : a.Qfix;
+  const int64_t n_qt = (Qd + kM - 1) / kM;
+  const int n_rt = a.n_pad / G::BN;
+  int nsplit = 1;   // split the reference tiles when there are few query tiles
+  if (n_qt > 0 && n_qt < 2 * (int64_t)gridDim.x) {
+    nsplit = (int)((2 * (int64_t)gridDim.x + n_qt - 1) / n_qt);
+    if (nsplit > n_rt) nsplit = n_rt;
+  }
+  const int per = (n_rt + nsplit - 1) / nsplit;
+  const int64_t n_items = n_qt * nsplit;
+  if ((int64_t)blockIdx.x >= n_items) return;   // uniform for the whole CTA
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < G::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(&tfull[s], 1);
+      mbar_init(&tempty[s], kEpiWarps);
+    }
+    mbar_init(afull, 1);
+    mbar_init(aempty, 1);
+    *s_abort = 0;
+    fence_barrier_init();
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                 "r"(G::TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer ----------------
+      int stage = 0;
+      uint32_t phase = 0, a_phase = 0;
+      bool first = true, ok = true;
+      for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        const int qt = (int)(it / nsplit), part = (int)(it % nsplit);
+        const int rt0 = part * per, rt1 = min(n_rt, rt0 + per);
+        if (!first) {
+          if (!(ok = mbar_wait(aempty, a_phase, s_abort))) break;
+          a_phase ^= 1;
+        }
+        first = false;
+        mbar_expect_tx(afull, G::ATOMS * kM * 128);
+        for (int at = 0; at < G::ATOMS; ++at) tma_load_2d(sA + at * kM * 128, &a.tmA, afull, 64 * at, qt * kM);
+        for (int rt = rt0; rt < rt1; ++rt) {
+          if (!(ok = mbar_wait(&empty[stage], phase ^ 1, s_abort))) break;
+          mbar_expect_tx(&full[stage], G::ATOMS * G::BN * 128);
+          for (int at = 0; at < G::ATOMS; ++at)
+            tma_load_2d(sB + (stage * G::ATOMS + at) * G::BN * 128, &a.tmB, &full[stage], 64 * at, rt * G::BN);
+          if (++stage == G::STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+      // tail: every stage released and the last query tile consumed before exit
+      for (int s = 0; s < G::STAGES && ok; ++s) {
+        ok = mbar_wait(&empty[stage], phase ^ 1, s_abort);
+        if (++stage == G::STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (ok && !first) mbar_wait(aempty, a_phase, s_abort);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      int stage = 0, acc = 0;
+      uint32_t phase = 0, a_phase = 0, acc_phase = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+        const int part = (int)(it % nsplit);
+        const int rt0 = part * per, rt1 = min(n_rt, rt0 + per);
+        if (!(ok = mbar_wait(afull, a_phase, s_abort))) break;
+        a_phase ^= 1;
+        for (int rt = rt0; rt < rt1; ++rt) {
+          if (!(ok = mbar_wait(&full[stage], phase, s_abort))) break;
+          if (!(ok = mbar_wait(&tempty[acc], acc_phase ^ 1, s_abort))) break;
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(acc * G::BN);
+#pragma unroll
+          for (int kk = 0; kk < G::D / 16; ++kk) {
+            const int at = kk >> 2, ko = (kk & 3) * 32;
+            tc_mma(d, sw128_desc(sA + at * kM * 128 + ko),
+                   sw128_desc(sB + (stage * G::ATOMS + at) * G::BN * 128 + ko), IDESC, kk > 0 ? 1u : 0u);
+          }
+          tc_commit(&empty[stage]);
+          tc_commit(&tfull[acc]);
+          if (++stage == G::STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+          if (++acc == 2) {
+            acc = 0;
+            acc_phase ^= 1;
+          }
+        }
+        if (ok) tc_commit(aempty);
+      }
+    }
+  } else if (warp >= 4) {
+    // ---------------- epilogue ----------------
+    const int quad = warp & 3;                 // TMEM lanes this warp may read
+    const int half = (warp - 4) >> 2;          // which half of the BN columns
+    const int row = quad * 32 + lane;          // query row within the tile
+    constexpr int HALF = G::BN / 2;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
+      const int qt = (int)(it / nsplit), part = (int)(it % nsplit);
+      const int rt0 = part * per, rt1 = min(n_rt, rt0 + per);
+      float bv = __int_as_float(0x7f800000);
+      int bi = 0;
+      for (int rt = rt0; rt < rt1; ++rt) {
+        ok = mbar_wait(&tfull[acc], acc_phase, s_abort);
+        if (!__all_sync(kFull, ok)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * G::BN + half * HALF);
+#pragma unroll 1
+        for (int c = 0; c < HALF; c += 32) {
+          uint32_t v[32];
+          tmem_ld32(tb + (uint32_t)c, v);
+          const int col0 = rt * G::BN + half * HALF + c;
+          const float4* rn4 = reinterpret_cast<const float4*>(a.rnorm + col0);
+          float x[32];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float4 r = __ldg(rn4 + j);
+            x[4 * j + 0] = fmaf(-2.f, __uint_as_float(v[4 * j + 0]), r.x);
+            x[4 * j + 1] = fmaf(-2.f, __uint_as_float(v[4 * j + 1]), r.y);
+            x[4 * j + 2] = fmaf(-2.f, __uint_as_float(v[4 * j + 2]), r.z);
+            x[4 * j + 3] = fmaf(-2.f, __uint_as_float(v[4 * j + 3]), r.w);
+          }
+          float m[11];
+#pragma unroll
+          for (int j = 0; j < 10; ++j) m[j] = min3(x[3 * j], x[3 * j + 1], x[3 * j + 2]);
+          m[10] = fminf(x[30], x[31]);
+          const float m0 = min3(m[0], m[1], m[2]), m1 = min3(m[3], m[4], m[5]);
+          const float m2 = min3(m[6], m[7], m[8]), m3 = fminf(m[9], m[10]);
+          const float cmin = fminf(min3(m0, m1, m2), m3);
+          if (cmin < bv) {       // rare after the first tiles: locate the lowest column
+            int jj = 31;
+#pragma unroll
+            for (int j = 31; j >= 0; --j)
+              if (x[j] == cmin) jj = j;
+            bv = cmin;
+            bi = col0 + jj;
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[acc]);
+        if (++acc == 2) {
+          acc = 0;
+          acc_phase ^= 1;
+        }
+      }
+      const int64_t i = (int64_t)qt * kM + row;
+      if (ok && i < Qd && bv < __int_as_float(0x7f800000)) {
+        const uint32_t dist = (uint32_t)((float)a.qnorm[i] + bv);   // exact: integer < 2^24
+        atomicMin(a.best + i, ((unsigned long long)dist << 32) | (unsigned)bi);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G::TMEM_COLS)
+                 : "memory");
+  }
+  if (threadIdx.x == 0 && *s_abort) atomicOr(a.status, RIANN_DEV_TIMEOUT);
+}
+
+// ---------------------------------------------------------------------------
+// query rows in, results out
+// ---------------------------------------------------------------------------
+struct PrepArgs {
+  const uint8_t* frame;
+  int W, Wq;
+  int64_t Q;
+  const int32_t* list;
+  const uint32_t* list_count;
+  __nv_bfloat16* Aq;
+  uint32_t* qnorm;
+  unsigned long long* best;
+};
+
+// Row i of Aq = bf16 bytes of the i-th query patch ((dy, dx, c) order), its
+// squared norm, and a reset best slot.  One thread per query.
+template <int C>
+__global__ void k_dense_prep(PrepArgs a) {
+  constexpr int NW = 16 * C;
+  const int64_t nq = a.list ? (int64_t)*a.list_count : a.Q;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t qi = a.list ? (int64_t)a.list[i] : i;
+    const int y = (int)(qi / a.Wq), x = (int)(qi % a.Wq);
+    uint2* dst = reinterpret_cast<uint2*>(a.Aq + i * (64 * C));
+    uint32_t nrm = 0;
+#pragma unroll 4
+    for (int w = 0; w < NW; ++w) {
+      const int dy = w / (2 * C), j = w % (2 * C);
+      const uint8_t* p = a.frame + ((int64_t)(y + dy) * a.W + x) * C + 4 * j;
+      const uint32_t b0 = p[0], b1 = p[1], b2 = p[2], b3 = p[3];
+      nrm += b0 * b0 + b1 * b1 + b2 * b2 + b3 * b3;
+      // bf16 of an integer 0..255: exact; pack two per 32-bit word
+      const uint32_t h0 = __bfloat16_as_ushort(__float2bfloat16_rn((float)b0));
+      const uint32_t h1 = __bfloat16_as_ushort(__float2bfloat16_rn((float)b1));
+      const uint32_t h2 = __bfloat16_as_ushort(__float2bfloat16_rn((float)b2));
+      const uint32_t h3 = __bfloat16_as_ushort(__float2bfloat16_rn((float)b3));
+      dst[w] = make_uint2(h0 | (h1 << 16), h2 | (h3 << 16));
+    }
+    a.qnorm[i] = nrm;
+    a.best[i] = ~0ull;
+  }
+}
+
+struct FinishArgs {
+  const int32_t* list;
+  const uint32_t* list_count;
+  int64_t Q;
+  const unsigned long long* best;
+  int32_t* out_annf;
+  uint32_t* out_dist;
+  uint32_t* out_count;
+  int n;
+  unsigned long long* stats;
+};
+
+__global__ void k_dense_finish(FinishArgs a) {
+  const int64_t nq = a.list ? (int64_t)*a.list_count : a.Q;
+  if (!a.list && a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[kStatDenseQueries] = (unsigned long long)nq;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t qi = a.list ? (int64_t)a.list[i] : i;
+    const unsigned long long k = a.best[i];
+    a.out_annf[qi] = (int32_t)(k & 0xffffffffu);
+    if (a.out_dist) a.out_dist[qi] = (uint32_t)(k >> 32);
+    if (a.out_count) a.out_count[qi] = (uint32_t)a.n;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+}  // namespace
+
+// 2-D tensor map over bf16 rows of D elements: boxes of 64 elements x box_rows
+// rows with the 128-byte swizzle (the operand layout the MMA descriptors use).
+bool make_row_map(CUtensorMap* m, const void* base, uint64_t rows, int D, int box_rows) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)D, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)D * 2};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1u, 1u};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int dense_ref_rows_per_tile(int C) { return C == 1 ? Cfg<1>::BN : Cfg<3>::BN; }
+
+cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, cudaStream_t s) {
+  if (!ix.tm_ready) return cudaErrorNotSupported;
+  const int C = ix.C;
+  PrepArgs p;
+  p.frame = d.frame;
+  p.W = d.W;
+  p.Wq = d.Wq;
+  p.Q = d.Q;
+  p.list = d.list;
+  p.list_count = d.list_count;
+  p.Aq = ix.Aq;
+  p.qnorm = ix.qnorm;
+  p.best = ix.best;
+  int64_t blocks = (d.Q + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  prof_begin(ix, kSlotPrep, s);
+  if (C == 1) k_dense_prep<1><<<(unsigned)blocks, 256, 0, s>>>(p);
+  else k_dense_prep<3><<<(unsigned)blocks, 256, 0, s>>>(p);
+  prof_end(ix, kSlotPrep, s);
+
+  TcArgs t;
+  t.tmA = ix.tmAq;
+  t.tmB = ix.tmRbf;
+  t.rnorm = ix.rnorm;
+  t.qnorm = ix.qnorm;
+  t.count = d.list ? d.list_count : nullptr;
+  t.Qfix = d.Q;
+  t.n_pad = ix.n_pad;
+  t.best = ix.best;
+  t.status = ix.status;
+  const int grid = sm_count();
+  prof_begin(ix, kSlotDense, s);
+  if (C == 1) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_dense_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>());
+      attr = true;
+    }
+    k_dense_tc<1><<<grid, kThreads, smem_bytes<1>(), s>>>(t);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_dense_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<3>());
+      attr = true;
+    }
+    k_dense_tc<3><<<grid, kThreads, smem_bytes<3>(), s>>>(t);
+  }
+  prof_end(ix, kSlotDense, s);
+
+  FinishArgs f;
+  f.list = d.list;
+  f.list_count = d.list_count;
+  f.Q = d.Q;
+  f.best = ix.best;
+  f.out_annf = d.out_annf;
+  f.out_dist = d.out_dist;
+  f.out_count = d.out_count;
+  f.n = ix.n;
+  f.stats = d.stats;
+  k_dense_finish<<<(unsigned)blocks, 256, 0, s>>>(f);
+  return cudaGetLastError();
+}
+
+}  // namespace riann

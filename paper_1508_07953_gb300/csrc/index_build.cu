@@ -1,0 +1,143 @@
+// index_build.cu -- pre-processing of the reference set (Sec. 3.3: distances
+// from the anchors to every reference, sorted ascending per anchor; here the
+// anchors are the K fixed key points).  Runs once per reference set.
+#include "common.cuh"
+
+namespace riann {
+namespace {
+
+// P[r][m] = ||k_m - R_r||^2.  One thread per (r, m); words compared with
+// per-byte absolute differences and a 4-way dot product of them with themselves.
+__global__ void k_key_distances(const uint8_t* __restrict__ R, const uint8_t* __restrict__ KP,
+                                int n, int K, int D, uint32_t* __restrict__ P) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * K) return;
+  int r = (int)(t / K), m = (int)(t % K);
+  const uint32_t* a = reinterpret_cast<const uint32_t*>(R + (int64_t)r * D);
+  const uint32_t* b = reinterpret_cast<const uint32_t*>(KP + (int64_t)m * D);
+  uint32_t s = 0;
+  for (int w = 0; w < D / 4; ++w) {
+    uint32_t d = __vabsdiffu4(a[w], b[w]);
+    s = __dp4a(d, d, s);
+  }
+  P[t] = s;
+}
+
+// bf16 copy of R (0..255 are exact in bf16) and ||r||^2 (exact in fp32: < 2^24).
+// Rows n..n_pad-1 are zero with norm +inf so padded columns never win an argmin.
+__global__ void k_prep_refs(const uint8_t* __restrict__ R, int n, int n_pad, int D,
+                            __nv_bfloat16* __restrict__ Rbf, float* __restrict__ rnorm) {
+  int r = blockIdx.x;
+  if (r >= n_pad) return;
+  uint32_t s = 0;
+  for (int i = threadIdx.x; i < D; i += blockDim.x) {
+    uint32_t v = r < n ? R[(int64_t)r * D + i] : 0u;
+    Rbf[(int64_t)r * D + i] = __float2bfloat16_rn((float)v);
+    s += v * v;
+  }
+  __shared__ uint32_t red[32];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t tot = 0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot += red[w];
+    rnorm[r] = r < n ? (float)tot : __int_as_float(0x7f800000);
+  }
+}
+
+// keys[m][j] = (P[j][m] << 32) | j for j < n, all-ones padding up to NP.
+__global__ void k_make_keys(const uint32_t* __restrict__ P, int n, int K, int NP,
+                            unsigned long long* __restrict__ keys) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int m = blockIdx.y;
+  if (j >= NP) return;
+  keys[(int64_t)m * NP + j] =
+      j < n ? (((unsigned long long)P[(int64_t)j * K + m]) << 32) | (unsigned)j : ~0ull;
+}
+
+constexpr int kChunk = 2048;   // elements sorted in shared memory by one block
+
+__device__ __forceinline__ void cmp_swap(unsigned long long& a, unsigned long long& b, bool up) {
+  if ((a > b) == up) {
+    unsigned long long t = a;
+    a = b;
+    b = t;
+  }
+}
+
+// Bitonic sort of each kChunk-aligned chunk for stages k <= kChunk, or (merge
+// mode) the j < kChunk steps of stage k.  Direction follows the global index so
+// the chunks compose into the full network.  1024 threads, 2 elements each.
+__global__ void k_bitonic_shared(unsigned long long* keys, int NP, int k_only) {
+  __shared__ unsigned long long s[kChunk];
+  unsigned long long* seg = keys + (int64_t)blockIdx.y * NP;
+  const int base = blockIdx.x * kChunk;
+  for (int i = threadIdx.x; i < kChunk; i += blockDim.x) s[i] = seg[base + i];
+  __syncthreads();
+  const int k_lo = k_only ? k_only : 2;
+  const int k_hi = k_only ? k_only : kChunk;
+  for (int k = k_lo; k <= k_hi; k <<= 1) {
+    for (int j = (k_only ? kChunk : k) >> 1; j > 0; j >>= 1) {
+      int t = threadIdx.x;                        // pair index
+      int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+      bool up = ((base + i) & k) == 0;
+      cmp_swap(s[i], s[i + j], up);
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < kChunk; i += blockDim.x) seg[base + i] = s[i];
+}
+
+// One global step (k, j) with j >= kChunk: thread per compared pair.
+__global__ void k_bitonic_global(unsigned long long* keys, int NP, int k, int j) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= NP / 2) return;
+  unsigned long long* seg = keys + (int64_t)blockIdx.y * NP;
+  int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+  bool up = (i & k) == 0;
+  unsigned long long a = seg[i], b = seg[i + j];
+  if ((a > b) == up) {
+    seg[i] = b;
+    seg[i + j] = a;
+  }
+}
+
+__global__ void k_split_keys(const unsigned long long* __restrict__ keys, int n, int NP,
+                             uint32_t* __restrict__ TA, int32_t* __restrict__ Tid) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  int m = blockIdx.y;
+  if (j >= n) return;
+  unsigned long long v = keys[(int64_t)m * NP + j];
+  TA[(int64_t)m * n + j] = (uint32_t)(v >> 32);
+  Tid[(int64_t)m * n + j] = (int32_t)(v & 0xffffffffu);
+}
+
+}  // namespace
+
+cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
+  const int n = ix.n, K = ix.K, D = ix.D;
+  {
+    int64_t tot = (int64_t)n * K;
+    k_key_distances<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ix.R, ix.KP, n, K, D, ix.P);
+  }
+  k_prep_refs<<<ix.n_pad, 64, 0, s>>>(ix.R, n, ix.n_pad, D, ix.Rbf, ix.rnorm);
+  int NP = kChunk;
+  while (NP < n) NP <<= 1;
+  unsigned long long* keys = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&keys, sizeof(unsigned long long) * (size_t)NP * K, s);
+  if (e != cudaSuccess) return e;
+  k_make_keys<<<dim3((NP + 255) / 256, K), 256, 0, s>>>(ix.P, n, K, NP, keys);
+  k_bitonic_shared<<<dim3(NP / kChunk, K), kChunk / 2, 0, s>>>(keys, NP, 0);
+  for (int k = 2 * kChunk; k <= NP; k <<= 1) {
+    for (int j = k >> 1; j >= kChunk; j >>= 1)
+      k_bitonic_global<<<dim3((NP / 2 + 255) / 256, K), 256, 0, s>>>(keys, NP, k, j);
+    k_bitonic_shared<<<dim3(NP / kChunk, K), kChunk / 2, 0, s>>>(keys, NP, k);
+  }
+  k_split_keys<<<dim3((n + 255) / 256, K), 256, 0, s>>>(keys, n, NP, ix.TA, ix.Tid);
+  e = cudaFreeAsync(keys, s);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace riann

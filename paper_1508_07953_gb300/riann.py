@@ -1,0 +1,263 @@
+"""Thin Python binding of the RIANN C ABI (include/riann.h).
+
+Argument marshalling only: torch tensors are passed as raw device pointers and
+``torch.cuda.Stream`` objects as ``cudaStream_t`` handles.  Every step of the
+query path runs in the CUDA library; there is no CPU fallback -- importing this
+module raises if ``libriann.so`` has not been built.
+
+Function names match the C entry points.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import torch
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libriann.so")
+if not os.path.exists(_LIB_PATH):
+    raise ImportError(
+        f"RIANN CUDA library not found at {_LIB_PATH}; build it with "
+        "`python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = ctypes.CDLL(_LIB_PATH)
+
+RIANN_OK = 0
+RIANN_ERR_INVALID_ARG = 1
+RIANN_ERR_OOM = 2
+RIANN_ERR_UNSUPPORTED = 3
+RIANN_ERR_CUDA = 4
+RIANN_ERR_TIMEOUT = 5
+RIANN_ERR_ADMISSION = 6
+RIANN_ERR_DEVICE = 7
+RIANN_DEV_BAD_PREV = 0x1
+RIANN_DEV_BOUNDS = 0x2
+RIANN_DEV_TIMEOUT = 0x4
+
+
+class riann_params(ctypes.Structure):
+    _fields_ = [("alpha_num", ctypes.c_int32), ("alpha_den", ctypes.c_int32),
+                ("ring_limit", ctypes.c_int32), ("cap", ctypes.c_int32)]
+
+    def __repr__(self):
+        return (f"riann_params(alpha={self.alpha_num}/{self.alpha_den}, "
+                f"ring_limit={self.ring_limit}, cap={self.cap})")
+
+
+class riann_index_info_t(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("K", ctypes.c_int32), ("channels", ctypes.c_int32),
+                ("dim", ctypes.c_int32), ("device_bytes", ctypes.c_size_t)]
+
+
+class riann_frame_stats_t(ctypes.Structure):
+    _fields_ = [("ring_queries", ctypes.c_uint64), ("dense_queries", ctypes.c_uint64),
+                ("sum_seed", ctypes.c_uint64), ("sum_candidates", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_i32 = ctypes.c_int32
+_lib.riann_default_params.argtypes = [_i32]
+_lib.riann_default_params.restype = riann_params
+_lib.riann_strerror.argtypes = [ctypes.c_int]
+_lib.riann_strerror.restype = ctypes.c_char_p
+_lib.riann_build_reference_index.argtypes = [_P, _i32, _i32, _P, _i32, _P, ctypes.POINTER(_P)]
+_lib.riann_index_destroy.argtypes = [_P]
+_lib.riann_index_destroy.restype = None
+_lib.riann_index_info.argtypes = [_P, ctypes.POINTER(riann_index_info_t)]
+_lib.riann_index_tables.argtypes = [_P, _P, _P, _P, _P]
+_lib.riann_annf_frame.argtypes = [_P, ctypes.POINTER(riann_params), _P, _P, _i32, _i32, _P, _P, _P, _P]
+_lib.riann_exact_nn.argtypes = [_P, _P, _P, _i32, _i32, _P, _P]
+_lib.riann_frame_stats.argtypes = [_P, _P, ctypes.POINTER(riann_frame_stats_t)]
+_lib.riann_profile_enable.argtypes = [_P, ctypes.c_int]
+_lib.riann_profile_read.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_float), _i32]
+_lib.riann_status.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_uint32)]
+
+
+class RiannError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {_lib.riann_strerror(code).decode()} (code {code})")
+        self.code = code
+
+
+def _check(code: int, what: str):
+    if code != RIANN_OK:
+        raise RiannError(code, what)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _stream(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t: Optional[torch.Tensor], dtypes, name: str, numel: Optional[int] = None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype not in dtypes:
+        raise ValueError(f"{name} must have dtype in {dtypes}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name} must hold {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+_I32 = (torch.int32,)
+_U32 = (torch.int32, torch.uint32)
+
+
+def riann_default_params(n: int) -> riann_params:
+    return _lib.riann_default_params(int(n))
+
+
+class RiannIndex:
+    """Owns a ``riann_index_t``; destroyed with the object (or ``close()``)."""
+
+    def __init__(self, handle: int, n: int, K: int, C: int):
+        self.handle = ctypes.c_void_p(handle)
+        self.n, self.K, self.C = n, K, C
+
+    def info(self) -> riann_index_info_t:
+        out = riann_index_info_t()
+        _check(_lib.riann_index_info(self.handle, ctypes.byref(out)), "riann_index_info")
+        return out
+
+    def close(self):
+        if self.handle and self.handle.value:
+            _lib.riann_index_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def riann_build_reference_index(patches: torch.Tensor, keypoints: torch.Tensor,
+                                stream: Optional[torch.cuda.Stream] = None) -> RiannIndex:
+    """patches uint8 [n][8][8][C] and keypoints uint8 [K][8][8][C] on the GPU."""
+    if patches.dim() != 4 or patches.shape[1:3] != (8, 8):
+        raise ValueError("patches must be [n][8][8][C]")
+    n, C = patches.shape[0], patches.shape[3]
+    if keypoints.dim() != 4 or tuple(keypoints.shape[1:]) != (8, 8, C):
+        raise ValueError("keypoints must be [K][8][8][C] with the patches' C")
+    K = keypoints.shape[0]
+    h = ctypes.c_void_p(0)
+    _check(_lib.riann_build_reference_index(_dev(patches, (torch.uint8,), "patches"), n, C,
+                                            _dev(keypoints, (torch.uint8,), "keypoints"), K,
+                                            _stream(stream), ctypes.byref(h)),
+           "riann_build_reference_index")
+    return RiannIndex(h.value, n, K, C)
+
+
+def _frame_dims(frame: torch.Tensor, C: int):
+    if frame.dim() == 2:
+        H, W = frame.shape
+        fc = 1
+    else:
+        H, W, fc = frame.shape
+    if fc != C:
+        raise ValueError(f"frame has {fc} channels, index has {C}")
+    return int(H), int(W)
+
+
+def riann_index_tables(index: RiannIndex, P: Optional[torch.Tensor] = None,
+                       TA: Optional[torch.Tensor] = None, Tid: Optional[torch.Tensor] = None,
+                       stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Copy P [n][K], TA [K][n] (uint32 bits in int32/uint32 tensors) and Tid [K][n] out."""
+    nk = index.n * index.K
+
+    def ptr(t, name):
+        if t is None:
+            return None
+        if t.dtype not in _U32 or not t.is_contiguous() or t.numel() != nk:
+            raise ValueError(f"{name} must be a contiguous 32-bit tensor of {nk} elements")
+        return ctypes.c_void_p(t.data_ptr())
+
+    _check(_lib.riann_index_tables(index.handle, _stream(stream), ptr(P, "P"), ptr(TA, "TA"),
+                                   ptr(Tid, "Tid")), "riann_index_tables")
+
+
+def riann_annf_frame(index: RiannIndex, params: riann_params, frame: torch.Tensor,
+                     prev_annf: Optional[torch.Tensor], out_annf: torch.Tensor,
+                     out_dist: Optional[torch.Tensor] = None,
+                     out_count: Optional[torch.Tensor] = None,
+                     stream: Optional[torch.cuda.Stream] = None) -> None:
+    """One query step; prev_annf None means frame 0 (brute force)."""
+    H, W = _frame_dims(frame, index.C)
+    Q = (H - 7) * (W - 7)
+    _check(_lib.riann_annf_frame(index.handle, ctypes.byref(params), _stream(stream),
+                                 _dev(frame, (torch.uint8,), "frame"), H, W,
+                                 _dev(prev_annf, _I32, "prev_annf", Q),
+                                 _dev(out_annf, _I32, "out_annf", Q),
+                                 _dev(out_dist, _U32, "out_dist", Q),
+                                 _dev(out_count, _U32, "out_count", Q)),
+           "riann_annf_frame")
+
+
+def riann_exact_nn(index: RiannIndex, frame: torch.Tensor, out_annf: torch.Tensor,
+                   out_dist: Optional[torch.Tensor] = None,
+                   stream: Optional[torch.cuda.Stream] = None) -> None:
+    H, W = _frame_dims(frame, index.C)
+    Q = (H - 7) * (W - 7)
+    _check(_lib.riann_exact_nn(index.handle, _stream(stream), _dev(frame, (torch.uint8,), "frame"),
+                               H, W, _dev(out_annf, _I32, "out_annf", Q),
+                               _dev(out_dist, _U32, "out_dist", Q)),
+           "riann_exact_nn")
+
+
+def riann_frame_stats(index: RiannIndex, stream: Optional[torch.cuda.Stream] = None) -> dict:
+    """Counters of the last frame run on this index (synchronises the stream)."""
+    out = riann_frame_stats_t()
+    _check(_lib.riann_frame_stats(index.handle, _stream(stream), ctypes.byref(out)),
+           "riann_frame_stats")
+    return out.as_dict()
+
+
+RIANN_SLOT_RING = 0
+RIANN_SLOT_DENSE = 1
+RIANN_SLOT_PREP = 2
+
+
+def riann_profile_enable(index: RiannIndex, on: bool = True) -> None:
+    _check(_lib.riann_profile_enable(index.handle, int(bool(on))), "riann_profile_enable")
+
+
+def riann_profile_read(index: RiannIndex, stream: Optional[torch.cuda.Stream] = None, nslots: int = 3):
+    """Per-kernel milliseconds of the most recent launches (-1: did not run)."""
+    buf = (ctypes.c_float * nslots)()
+    _check(_lib.riann_profile_read(index.handle, _stream(stream), buf, nslots), "riann_profile_read")
+    return [float(x) for x in buf]
+
+
+def riann_status(index: RiannIndex, stream: Optional[torch.cuda.Stream] = None) -> int:
+    """Synchronise and return the device status bits (0 = clean); clears them."""
+    bits = ctypes.c_uint32(0)
+    _lib.riann_status(index.handle, _stream(stream), ctypes.byref(bits))
+    return int(bits.value)
+
+
+# ---------------------------------------------------------------------------
+# convenience: allocate outputs and run a frame
+# ---------------------------------------------------------------------------
+def annf(index: RiannIndex, frame: torch.Tensor, prev: Optional[torch.Tensor],
+         params: Optional[riann_params] = None, stream=None):
+    """Allocate outputs and run one frame: returns (annf int32, dist int32, count int32)."""
+    H, W = _frame_dims(frame, index.C)
+    shape = (H - 7, W - 7)
+    dev = frame.device
+    out = torch.empty(shape, dtype=torch.int32, device=dev)
+    dist = torch.empty(shape, dtype=torch.int32, device=dev)
+    cnt = torch.empty(shape, dtype=torch.int32, device=dev)
+    riann_annf_frame(index, params if params is not None else riann_default_params(index.n),
+                     frame, prev, out, dist, cnt, stream)
+    return out, dist, cnt

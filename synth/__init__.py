@@ -271,7 +271,7 @@ def random_case(seed: int, n: int, K: int, C: int, H: int, W: int):
     """A small random (R, KP, frame, prev) case of uniform bytes, for edge-case tests."""
     rng = np.random.default_rng(seed)
     R = rng.integers(0, 256, size=(n, PATCH, PATCH, C), dtype=np.uint8)
-    KP = R[rng.choice(n, size=K, replace=False)].copy()
+    KP = R[rng.choice(n, size=K, replace=K > n)].copy()
     frame = rng.integers(0, 256, size=(H, W, C), dtype=np.uint8)
     prev = rng.integers(0, n, size=(H - PATCH + 1, W - PATCH + 1), dtype=np.int32)
     return R, KP, frame, prev
