@@ -63,7 +63,8 @@ enum {
   RIANN_ERR_CUDA = 4,         /* a CUDA runtime call failed                       */
   RIANN_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                    */
   RIANN_ERR_ADMISSION = 6,    /* server: the stream does not fit the budget       */
-  RIANN_ERR_DEVICE = 7        /* a kernel reported bad input (see riann_status)   */
+  RIANN_ERR_DEVICE = 7,       /* a kernel reported bad input (see riann_status)   */
+  RIANN_ERR_TOO_LARGE = 8     /* frame exceeds riann_exact_nn_noalloc's fixed scratch */
 };
 
 /* Bits of the device status word. */
@@ -160,6 +161,31 @@ typedef struct {
   uint64_t sum_seed;         /* sum over ring queries of min_m |Ring_m|         */
   uint64_t sum_candidates;   /* sum over ring queries of |S|                    */
 } riann_frame_stats_t;
+
+/*
+ * Allocation-free brute force (the paper has no counterpart: this is a
+ * deployment variant of riann_exact_nn).  For callers that may not allocate
+ * device memory while running -- a real-time pipeline whose memory budget is
+ * fixed at start-up, or a plug-in whose host application owns all
+ * allocations.  Same arguments and results as riann_exact_nn, but its scratch
+ * is a 16 MiB device array compiled into the library (held on every GPU that
+ * loads the library until the process exits), so it calls no allocator.
+ *   - Frames with more than riann_exact_nn_noalloc_max_queries(channels)
+ *     queries ((H-7)*(W-7)) are rejected with RIANN_ERR_TOO_LARGE.
+ *   - The first call on a device looks up the array's device address and
+ *     builds its TMA descriptors; make that first call before any stream
+ *     capture.
+ *   - All calls share the array: calls that overlap on the GPU (e.g. on two
+ *     streams at once) race and must be serialised by the caller.
+ *   - The current device must be the index's device.
+ */
+int riann_exact_nn_noalloc(riann_index_t idx, riann_stream_t stream,
+                           const uint8_t* d_frame, int32_t H, int32_t W,
+                           int32_t* d_out_annf, uint32_t* d_out_dist);
+
+/* Largest query count (H-7)*(W-7) riann_exact_nn_noalloc accepts for 1 or 3
+ * channels (0 for other values). */
+int64_t riann_exact_nn_noalloc_max_queries(int32_t channels);
 
 /* Synchronises `stream` and reads the counters. */
 int riann_frame_stats(riann_index_t idx, riann_stream_t stream, riann_frame_stats_t* out);

@@ -145,6 +145,7 @@ const char* riann_strerror(int code) {
     case RIANN_ERR_TIMEOUT: return "bounded device wait timed out";
     case RIANN_ERR_ADMISSION: return "admission rejected: budget exceeded";
     case RIANN_ERR_DEVICE: return "kernel reported invalid input (see status bits)";
+    case RIANN_ERR_TOO_LARGE: return "frame has more queries than the fixed scratch of riann_exact_nn_noalloc holds";
     default: return "unknown error";
   }
 }
@@ -378,6 +379,40 @@ int riann_profile_read(riann_index_t idx, riann_stream_t stream, float* ms, int3
     }
   }
   return RIANN_OK;
+}
+
+int64_t riann_exact_nn_noalloc_max_queries(int32_t channels) {
+  if (channels != 1 && channels != 3) return 0;
+  return noalloc_max_queries(channels);
+}
+
+int riann_exact_nn_noalloc(riann_index_t idx, riann_stream_t stream, const uint8_t* d_frame, int32_t H,
+                           int32_t W, int32_t* d_out_annf, uint32_t* d_out_dist) {
+  if (!idx || !d_frame || !d_out_annf || !frame_ok(H, W)) return RIANN_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RIANN_ERR_CUDA;
+  if (dev != idx->device) return RIANN_ERR_INVALID_ARG;
+  const int64_t Q = (int64_t)(H - 7) * (W - 7);
+  if (Q > noalloc_max_queries(idx->C)) return RIANN_ERR_TOO_LARGE;
+  DenseArgs da;
+  da.frame = d_frame;
+  da.H = H;
+  da.W = W;
+  da.Hq = H - 7;
+  da.Wq = W - 7;
+  da.Q = Q;
+  da.list = nullptr;
+  da.list_count = nullptr;
+  da.out_annf = d_out_annf;
+  da.out_dist = d_out_dist;
+  da.out_count = nullptr;
+  da.R = idx->R;
+  da.n = idx->n;
+  da.stats = nullptr;
+  cudaError_t e = launch_exact_nn_noalloc(da, *idx, reinterpret_cast<cudaStream_t>(stream));
+  if (e == cudaErrorInvalidValue) return RIANN_ERR_TOO_LARGE;
+  if (e == cudaErrorNotSupported) return RIANN_ERR_UNSUPPORTED;
+  return from_cuda(e);
 }
 
 int riann_status(riann_index_t idx, riann_stream_t stream, uint32_t* bits) {

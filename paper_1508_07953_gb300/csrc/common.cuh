@@ -108,6 +108,8 @@ void prof_end(Index& ix, int slot, cudaStream_t s);
 bool make_row_map(CUtensorMap* m, const void* base, uint64_t rows, int D, int box_rows);
 int dense_ref_rows_per_tile(int C);
 cudaError_t launch_dense_tc(const DenseArgs& a, Index& ix, cudaStream_t s);
+int64_t noalloc_max_queries(int C);
+cudaError_t launch_exact_nn_noalloc(const DenseArgs& a, Index& ix, cudaStream_t s);
 
 // launchers (return cudaGetLastError())
 cudaError_t launch_index_build(Index& ix, cudaStream_t s);

@@ -554,4 +554,141 @@ cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free brute force.
+//
+// Some callers may not allocate device memory once they are running: a
+// real-time video pipeline that fixes its memory budget at start-up, or a
+// plug-in whose host application owns every allocation.  For them the
+// brute-force path can run with its scratch (bf16 query rows, query norms and
+// the packed per-query best slots) in the fixed device array below instead of
+// the index's growable scratch.  Every GPU that loads this library holds the
+// array until the process exits.
+//
+// Host code must not pass `g_noalloc_scratch` itself to a kernel: on the host
+// that name is only a stand-in for the device symbol.  The device address is
+// looked up once per device (cudaGetSymbolAddress, with that device current)
+// on the first call made on that device, together with the TMA descriptors
+// over it.  That first call should therefore come before any stream capture.
+// All calls share the array and it keeps the last call's contents; the
+// per-query best slots are reset by every call before use.  Calls that overlap
+// on the GPU (e.g. issued on two streams) race on the array.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoallocBytes = size_t(16) << 20;   // 16 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+constexpr size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+struct NoallocLayout {
+  int64_t rows;        // query rows that fit (multiple of 128)
+  size_t qnorm_off;    // byte offset of the uint32 norms
+  size_t best_off;     // byte offset of the uint64 best slots
+};
+
+NoallocLayout noalloc_layout(int C) {
+  const size_t per = (size_t)128 * C + 4 + 8;            // bf16 row + norm + best slot
+  int64_t rows = (int64_t)((kNoallocBytes - 1024) / per) / kM * kM;
+  NoallocLayout L;
+  L.rows = rows;
+  L.qnorm_off = align256((size_t)rows * 128 * C);
+  L.best_off = align256(L.qnorm_off + (size_t)rows * 4);
+  return L;
+}
+
+struct NoallocDevice {
+  std::once_flag once;
+  cudaError_t err = cudaSuccess;
+  unsigned char* base = nullptr;   // device address of g_noalloc_scratch
+  CUtensorMap map[2];              // [0] gray rows (D = 64), [1] RGB rows (D = 192)
+  bool map_ok[2] = {false, false};
+};
+
+constexpr int kMaxDevices = 64;
+NoallocDevice g_noalloc_dev[kMaxDevices];
+
+}  // namespace
+
+int64_t noalloc_max_queries(int C) { return noalloc_layout(C).rows; }
+
+// Returns cudaErrorInvalidValue when the frame has more queries than fit.
+cudaError_t launch_exact_nn_noalloc(const DenseArgs& d, Index& ix, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  NoallocDevice& nd = g_noalloc_dev[dev];
+  std::call_once(nd.once, [&nd] {
+    void* p = nullptr;
+    nd.err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (nd.err != cudaSuccess) return;
+    nd.base = static_cast<unsigned char*>(p);
+    for (int k = 0; k < 2; ++k) {
+      const int C = k ? 3 : 1;
+      nd.map_ok[k] = make_row_map(&nd.map[k], nd.base, (uint64_t)noalloc_layout(C).rows, 64 * C, kM);
+    }
+  });
+  if (nd.err != cudaSuccess) return nd.err;
+  const int C = ix.C;
+  const int k = C == 1 ? 0 : 1;
+  if (!nd.map_ok[k] || !ix.tm_ready) return cudaErrorNotSupported;
+  const NoallocLayout L = noalloc_layout(C);
+  if (d.Q > L.rows) return cudaErrorInvalidValue;
+  __nv_bfloat16* Aq = reinterpret_cast<__nv_bfloat16*>(nd.base);
+  uint32_t* qnorm = reinterpret_cast<uint32_t*>(nd.base + L.qnorm_off);
+  unsigned long long* best = reinterpret_cast<unsigned long long*>(nd.base + L.best_off);
+
+  PrepArgs p;
+  p.frame = d.frame;
+  p.W = d.W;
+  p.Wq = d.Wq;
+  p.Q = d.Q;
+  p.list = nullptr;
+  p.list_count = nullptr;
+  p.Aq = Aq;
+  p.qnorm = qnorm;
+  p.best = best;
+  int64_t blocks = (d.Q + 255) / 256;
+  const int64_t cap = (int64_t)sm_count() * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  if (C == 1) k_dense_prep<1><<<(unsigned)blocks, 256, 0, s>>>(p);
+  else k_dense_prep<3><<<(unsigned)blocks, 256, 0, s>>>(p);
+
+  TcArgs t;
+  t.tmA = nd.map[k];
+  t.tmB = ix.tmRbf;
+  t.rnorm = ix.rnorm;
+  t.qnorm = qnorm;
+  t.count = nullptr;
+  t.Qfix = d.Q;
+  t.n_pad = ix.n_pad;
+  t.best = best;
+  t.status = ix.status;
+  const int grid = sm_count();
+  if (C == 1) {
+    e = cudaFuncSetAttribute(k_dense_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>());
+    if (e != cudaSuccess) return e;
+    k_dense_tc<1><<<grid, kThreads, smem_bytes<1>(), s>>>(t);
+  } else {
+    e = cudaFuncSetAttribute(k_dense_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<3>());
+    if (e != cudaSuccess) return e;
+    k_dense_tc<3><<<grid, kThreads, smem_bytes<3>(), s>>>(t);
+  }
+
+  FinishArgs f;
+  f.list = nullptr;
+  f.list_count = nullptr;
+  f.Q = d.Q;
+  f.best = best;
+  f.out_annf = d.out_annf;
+  f.out_dist = d.out_dist;
+  f.out_count = nullptr;
+  f.n = ix.n;
+  f.stats = nullptr;
+  k_dense_finish<<<(unsigned)blocks, 256, 0, s>>>(f);
+  return cudaGetLastError();
+}
+
 }  // namespace riann

@@ -30,6 +30,7 @@ RIANN_ERR_CUDA = 4
 RIANN_ERR_TIMEOUT = 5
 RIANN_ERR_ADMISSION = 6
 RIANN_ERR_DEVICE = 7
+RIANN_ERR_TOO_LARGE = 8
 RIANN_DEV_BAD_PREV = 0x1
 RIANN_DEV_BOUNDS = 0x2
 RIANN_DEV_TIMEOUT = 0x4
@@ -73,6 +74,9 @@ _lib.riann_exact_nn.argtypes = [_P, _P, _P, _i32, _i32, _P, _P]
 _lib.riann_frame_stats.argtypes = [_P, _P, ctypes.POINTER(riann_frame_stats_t)]
 _lib.riann_profile_enable.argtypes = [_P, ctypes.c_int]
 _lib.riann_profile_read.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_float), _i32]
+_lib.riann_exact_nn_noalloc.argtypes = [_P, _P, _P, _i32, _i32, _P, _P]
+_lib.riann_exact_nn_noalloc_max_queries.argtypes = [_i32]
+_lib.riann_exact_nn_noalloc_max_queries.restype = ctypes.c_int64
 _lib.riann_status.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_uint32)]
 
 
@@ -237,6 +241,23 @@ def riann_profile_read(index: RiannIndex, stream: Optional[torch.cuda.Stream] = 
     buf = (ctypes.c_float * nslots)()
     _check(_lib.riann_profile_read(index.handle, _stream(stream), buf, nslots), "riann_profile_read")
     return [float(x) for x in buf]
+
+
+def riann_exact_nn_noalloc(index: RiannIndex, frame: torch.Tensor, out_annf: torch.Tensor,
+                           out_dist: Optional[torch.Tensor] = None,
+                           stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Brute force with the library's fixed scratch: allocates nothing (see riann.h)."""
+    H, W = _frame_dims(frame, index.C)
+    Q = (H - 7) * (W - 7)
+    _check(_lib.riann_exact_nn_noalloc(index.handle, _stream(stream),
+                                       _dev(frame, (torch.uint8,), "frame"), H, W,
+                                       _dev(out_annf, _I32, "out_annf", Q),
+                                       _dev(out_dist, _U32, "out_dist", Q)),
+           "riann_exact_nn_noalloc")
+
+
+def riann_exact_nn_noalloc_max_queries(channels: int) -> int:
+    return int(_lib.riann_exact_nn_noalloc_max_queries(int(channels)))
 
 
 def riann_status(index: RiannIndex, stream: Optional[torch.cuda.Stream] = None) -> int:
