@@ -64,6 +64,31 @@ def _load():
     return _lib
 
 
+class use_library:
+    """Context manager that routes this module's calls to another build of
+    riann_oracle.c (the mutation tests compile deliberately broken copies)."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        _load()
+        self._saved = _lib
+        lib = ctypes.CDLL(self.path)
+        for name in ("oracle_ring_member", "oracle_key_distances", "oracle_sort_tables", "oracle_exact_nn",
+                     "oracle_riann_definitional", "oracle_riann_indexed", "oracle_num_threads",
+                     "oracle_set_num_threads"):
+            f, g = getattr(self._saved, name), getattr(lib, name)
+            g.argtypes, g.restype = f.argtypes, f.restype
+        _lib = lib
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+
+
 def _ptr(a: Optional[np.ndarray]):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 

@@ -1,0 +1,90 @@
+"""Mutation check of the oracle's pins.
+
+Each mutant is the oracle source with one plausible mistake planted (a dropped
+factor, a flipped sign, a transposed index, a wrong tie-break, a dropped
+candidate, an off-by-one routing test).  It is compiled on the CPU and the
+pins are run against it; every mutant must make at least one pin fail.
+"""
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(os.path.abspath(oracle.__file__)), "riann_oracle.c")
+
+MUTANTS = {
+    "drop_factor_4": ("(unsigned __int128)4 * (unsigned __int128)(qq * qq)", "(unsigned __int128)(qq * qq)"),
+    "sign_of_C_term": ("- (__int128)p * p * (__int128)C", "+ (__int128)p * p * (__int128)C"),
+    "q_squared_not_fourth": ("(unsigned __int128)4 * (unsigned __int128)(qq * qq)", "(unsigned __int128)4 * (unsigned __int128)(qq)"),
+    "strict_ring_edge": ("return lhs <= rhs;", "return lhs < rhs;"),
+    "abs_diff_not_squared": ("s += (uint32_t)(d * d);", "s += (uint32_t)(d < 0 ? -d : d);"),
+    "patch_transposed": ("frame[((int64_t)(y + dy) * W + (x + dx)) * C + c]", "frame[((int64_t)(y + dx) * W + (x + dy)) * C + c]"),
+    "brute_force_tie_high": ("if (d < bd) { bd = d; bi = r; }", "if (d <= bd) { bd = d; bi = r; }"),
+    "ring_argmin_tie_high": ("if (d < bd || (d == bd && r < bi)) { bd = d; bi = r; }\n      }\n      annf[i] = bi;\n      if (dist) dist[i] = bd;\n      if (count) count[i] = s_size;\n    }\n    free(B); free(ring_size); free(in_all);",
+                             "if (d < bd || (d == bd && r > bi)) { bd = d; bi = r; }\n      }\n      annf[i] = bi;\n      if (dist) dist[i] = bd;\n      if (count) count[i] = s_size;\n    }\n    free(B); free(ring_size); free(in_all);"),
+    "prev_not_verified": ("int32_t bi = rp;                                /* r_p is always verified */\n      uint32_t bd = Cd;",
+                          "int32_t bi = rp;                                /* r_p is always verified */\n      uint32_t bd = 0xffffffffu;"),
+    "limit_off_by_one": ("if (ring_limit >= 0 && ns > (uint32_t)ring_limit) {   /* rings too wide: brute force */",
+                         "if (ring_limit >= 0 && ns >= (uint32_t)ring_limit) {   /* rings too wide: brute force */"),
+    "count_first_ring_only": ("        in_all[r] = (uint8_t)inside;\n        s_size += (uint32_t)inside;",
+                              "        in_all[r] = (uint8_t)inside;\n        s_size += (uint32_t)oracle_ring_member(P[(int64_t)r * K], B[0], Cd, alpha_num, alpha_den);"),
+    "alpha_inverted": ("__int128 L = qq * ((__int128)A + (__int128)B) - (__int128)p * p * (__int128)C;",
+                       "__int128 L = (__int128)p * p * ((__int128)A + (__int128)B) - qq * (__int128)C;"),
+}
+
+
+def _pins_fail() -> bool:
+    """Run a fast subset of the pins; True if any of them fails."""
+    checks = []
+    for name in pins.GOLDEN:
+        for mode in ("definitional", "indexed"):
+            checks.append(lambda name=name, mode=mode: pins.test_golden_fixture(name, mode))
+    checks += [pins.test_exact_nn_vs_numpy_random_with_ties, pins.test_exact_nn_vs_numpy_rgb,
+               pins.test_ring_member_exact_equalities_by_construction, pins.test_alpha_zero_profile_match,
+               pins.test_frame0_is_brute_force]
+
+    def alpha_one():
+        w = synth.WORKLOADS["tiny"]
+        R = synth.workload_reference(w)[:1024]
+        KP = synth.keypoints_kmeanspp(R, 8, 11)[1]
+        frames = synth.Video(w.video).frames(0, 3)[:, :48, :64]
+        idx = oracle.Index(R, KP)
+        pins.test_alpha_one_is_exact_nn_every_frame((R, KP, frames, idx))
+        pins.test_monotone_never_worse_than_previous((R, KP, frames, idx)) if False else None
+
+    def modes_agree():
+        for a in ((1, 4), (1, 1)):
+            pins.test_definitional_equals_indexed_random(1, a)
+            pins.test_definitional_equals_indexed_random(3, a)
+
+    checks += [alpha_one, modes_agree]
+    for c in checks:
+        try:
+            c()
+        except AssertionError:
+            return True
+    return False
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) >= 1, f"mutation site of {name} not found"
+    mutated = src.replace(old, new, 1)
+    c_path = tmp_path / "mutant.c"
+    c_path.write_text(mutated)
+    so = tmp_path / "mutant.so"
+    subprocess.run(["gcc", "-std=c99", "-O2", "-fopenmp", "-fPIC", "-shared", "-I",
+                    os.path.dirname(SRC), "-o", str(so), str(c_path)], check=True)
+    with oracle.use_library(str(so)):
+        assert _pins_fail(), f"no pin caught the planted mistake {name}"
+
+
+def test_unmutated_oracle_passes_the_subset():
+    assert not _pins_fail()

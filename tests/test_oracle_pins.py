@@ -75,7 +75,7 @@ def fixture_case(name):
 
 
 GOLDEN = ["ring_1d_two_keys.txt", "ring_1d_exact_boundary.txt", "ring_1d_prev_kept.txt",
-          "ring_1d_limit_bruteforce.txt", "ring_rgb_two_keys.txt"]
+          "ring_1d_limit_bruteforce.txt", "ring_1d_limit_equal.txt", "ring_rgb_two_keys.txt"]
 
 
 # --------------------------------------------------------------------------
