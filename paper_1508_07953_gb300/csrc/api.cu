@@ -74,6 +74,10 @@ void free_index(Index* ix) {
   cudaFree(ix->P);
   cudaFree(ix->TA);
   cudaFree(ix->Tid);
+  cudaFree(ix->E);
+  cudaFree(ix->RB);
+  cudaFree(ix->CW);
+  cudaFree(ix->CWE);
   cudaFree(ix->status);
   cudaFree(ix->stats);
   for (int k = 0; k < kSlots; ++k)
@@ -172,6 +176,9 @@ int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t cha
   ix->C = channels;
   ix->D = 64 * channels;
   ix->n_pad = (n + kDenseTileN - 1) / kDenseTileN * kDenseTileN;
+  ix->G = (K + 3) / 4;
+  ix->GP = (ix->G + 3) / 4 * 4;
+  ix->nw = (n + 3) / 4 * 4;
   const int D = ix->D;
   size_t& tot = ix->device_bytes;
   cudaError_t e = dalloc(&ix->R, (size_t)n * D, tot);
@@ -181,6 +188,10 @@ int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t cha
   if (e == cudaSuccess) e = dalloc(&ix->P, (size_t)n * K, tot);
   if (e == cudaSuccess) e = dalloc(&ix->TA, (size_t)n * K, tot);
   if (e == cudaSuccess) e = dalloc(&ix->Tid, (size_t)n * K, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->E, (size_t)K * kBuckets, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->RB, (size_t)K * (kBuckets + 1), tot);
+  if (e == cudaSuccess) e = dalloc(&ix->CW, (size_t)K * ix->G * ix->nw, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->CWE, (size_t)K * ix->GP * n, tot);
   if (e == cudaSuccess) e = dalloc(&ix->status, 1, tot);
   if (e == cudaSuccess) e = dalloc(&ix->stats, kStats, tot);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -288,8 +299,15 @@ int riann_annf_frame(riann_index_t idx, const riann_params* p, riann_stream_t st
   sa.P = ix.P;
   sa.TA = ix.TA;
   sa.Tid = ix.Tid;
+  sa.E = ix.E;
+  sa.RB = ix.RB;
+  sa.CW = ix.CW;
+  sa.CWE = ix.CWE;
+  sa.GP = ix.GP;
+  sa.nw = ix.nw;
   sa.n = ix.n;
   sa.K = ix.K;
+  sa.G = ix.G;
   sa.alpha_num = p->alpha_num;
   sa.alpha_den = p->alpha_den;
   sa.ring_limit = p->ring_limit;

@@ -18,6 +18,7 @@ constexpr int kMaxK = 64;
 constexpr int kMaxDim = 192;
 constexpr int kDenseTileN = 256;   // reference rows per tensor-core tile
 constexpr int kDenseTileM = 128;   // query rows per tensor-core tile
+constexpr int kBuckets = 256;      // quantile buckets per key point (8-bit codes)
 
 // Work counters of the last frame (riann_frame_stats).
 enum StatSlot { kStatRingQueries = 0, kStatDenseQueries, kStatSumSeed, kStatSumS, kStats = 8 };
@@ -40,6 +41,17 @@ struct Index {
   uint32_t* P = nullptr;          // [n][K] ||k_m - r||^2
   uint32_t* TA = nullptr;         // [K][n] per key: distances ascending
   int32_t* Tid = nullptr;         // [K][n] per key: reference index of each TA entry
+  // 8-bit bucket codes: code_m(A) = max{b : E[m][b] <= A}, edges at every
+  // ceil(n/256)-th rank of TA[m]; monotone in A, so a whole bucket strictly
+  // inside a ring's code range lies inside the ring.
+  uint32_t* E = nullptr;          // [K][kBuckets] bucket edges (UINT32_MAX past the end)
+  uint32_t* RB = nullptr;         // [K][kBuckets + 1] first rank of each bucket in TA[m]; RB[m][256] = n
+  uint32_t* CW = nullptr;         // [K][G][nw] in key m's sorted order, codes of keys 4g..4g+3 (one byte
+                                  // each); rows padded to nw = n rounded up to 4 (16-byte aligned rows)
+  uint32_t* CWE = nullptr;        // [K][n][GP] the same codes entry-major (GP = G rounded up to 4 words)
+  int G = 0;                      // ceil(K / 4)
+  int GP = 0;                     // ceil(G / 4) * 4
+  int nw = 0;                     // n rounded up to 4
   uint32_t* status = nullptr;     // device status word (RIANN_DEV_* bits)
   unsigned long long* stats = nullptr;  // [kStats] counters of the last frame
   size_t device_bytes = 0;
@@ -77,7 +89,11 @@ struct SparseArgs {
   const uint32_t* P;
   const uint32_t* TA;
   const int32_t* Tid;
-  int n, K;
+  const uint32_t* E;
+  const uint32_t* RB;
+  const uint32_t* CW;
+  const uint32_t* CWE;
+  int n, K, G, GP, nw;
   int alpha_num, alpha_den, ring_limit;
   int32_t* dense_list;
   uint32_t* dense_count;

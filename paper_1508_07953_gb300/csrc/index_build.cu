@@ -113,6 +113,61 @@ __global__ void k_split_keys(const unsigned long long* __restrict__ keys, int n,
   Tid[(int64_t)m * n + j] = (int32_t)(v & 0xffffffffu);
 }
 
+// Bucket edges and the first rank of each bucket, per key point.
+__global__ void k_bucket_edges(const uint32_t* __restrict__ TA, int n, int K, uint32_t* __restrict__ E,
+                               uint32_t* __restrict__ RB) {
+  const int m = blockIdx.x, b = threadIdx.x;   // blockDim = kBuckets
+  const int bs = (n + kBuckets - 1) / kBuckets;
+  const uint32_t* t = TA + (int64_t)m * n;
+  const int64_t rank = (int64_t)b * bs;
+  const uint32_t e = rank < n ? t[rank] : 0xffffffffu;
+  E[m * kBuckets + b] = e;
+  int lo = 0, len = n;                         // first rank with t[j] >= e
+  while (len > 0) {
+    const int half = len >> 1;
+    if (t[lo + half] < e) { lo += half + 1; len -= half + 1; } else { len = half; }
+  }
+  RB[m * (kBuckets + 1) + b] = (uint32_t)lo;
+  if (b == 0) RB[m * (kBuckets + 1) + kBuckets] = (uint32_t)n;
+}
+
+// code[r][m] = number of edges of key m that are <= P[r][m], minus one.
+__global__ void k_codes(const uint32_t* __restrict__ P, const uint32_t* __restrict__ E, int n, int K,
+                        uint8_t* __restrict__ code) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * K) return;
+  const int m = (int)(t % K);
+  const uint32_t a = P[t];
+  const uint32_t* e = E + m * kBuckets;
+  int lo = 0, len = kBuckets;                  // first edge > a
+  while (len > 0) {
+    const int half = len >> 1;
+    if (e[lo + half] <= a) { lo += half + 1; len -= half + 1; } else { len = half; }
+  }
+  code[t] = (uint8_t)(lo - 1);                 // lo >= 1: e[0] is the smallest distance
+}
+
+// CW[m][g][j]: codes of keys 4g..4g+3 of reference Tid[m][j] (byte i = key 4g+i;
+// keys past K read as 0).
+__global__ void k_pack_codes(const int32_t* __restrict__ Tid, const uint8_t* __restrict__ code, int n, int K,
+                             int G, int GP, int nw, uint32_t* __restrict__ CW, uint32_t* __restrict__ CWE) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (j >= n) return;
+  const int r = Tid[(int64_t)m * n + j];
+  const uint8_t* c = code + (int64_t)r * K;
+  for (int g = 0; g < G; ++g) {
+    uint32_t w = 0;
+    for (int i = 0; i < 4; ++i) {
+      const int k = 4 * g + i;
+      if (k < K) w |= (uint32_t)c[k] << (8 * i);
+    }
+    CW[((int64_t)m * G + g) * nw + j] = w;
+    CWE[((int64_t)m * n + j) * GP + g] = w;
+  }
+  for (int g = G; g < GP; ++g) CWE[((int64_t)m * n + j) * GP + g] = 0;
+}
+
 }  // namespace
 
 cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
@@ -136,6 +191,20 @@ cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
   }
   k_split_keys<<<dim3((n + 255) / 256, K), 256, 0, s>>>(keys, n, NP, ix.TA, ix.Tid);
   e = cudaFreeAsync(keys, s);
+  if (e != cudaSuccess) return e;
+
+  k_bucket_edges<<<K, kBuckets, 0, s>>>(ix.TA, n, K, ix.E, ix.RB);
+  uint8_t* code = nullptr;
+  e = cudaMallocAsync((void**)&code, (size_t)n * K, s);
+  if (e != cudaSuccess) return e;
+  {
+    const int64_t tot = (int64_t)n * K;
+    k_codes<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ix.P, ix.E, n, K, code);
+  }
+  e = cudaMemsetAsync(ix.CW, 0, sizeof(uint32_t) * (size_t)K * ix.G * ix.nw, s);
+  if (e != cudaSuccess) return e;
+  k_pack_codes<<<dim3((n + 255) / 256, K), 256, 0, s>>>(ix.Tid, code, n, K, ix.G, ix.GP, ix.nw, ix.CW, ix.CWE);
+  e = cudaFreeAsync(code, s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }

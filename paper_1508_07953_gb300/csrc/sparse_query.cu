@@ -1,12 +1,17 @@
 // sparse_query.cu -- the per-query RIANN step for frames with a previous field
-// (Alg. 1 loop body): previous match and temporal change, ring bounds by
-// binary search in the sorted per-key lists (Sec. 3.3), intersection of the
-// rings, verification of the survivors (Alg. 1 final argmin).
+// (Alg. 1 loop body): previous match and temporal change, ring bounds in the
+// sorted per-key lists (Sec. 3.3), intersection of the rings, verification of
+// the survivors (Alg. 1 final argmin).
 //
 // One warp per query.  A CTA owns a TY x TX tile of query positions, stages
 // the (TY+7) x (TX+7) pixels they read plus all key points in shared memory,
 // and hands queries to its warps through a shared counter (candidate counts
 // vary by orders of magnitude between queries, Sec. 3.3 / Fig. 5).
+//
+// Ring sizes and the intersection work on 8-bit bucket codes (see common.cuh):
+// a reference whose code for key m lies strictly inside the code range of the
+// exact ring bounds is a member of ring m, one outside it is not, and one in a
+// boundary bucket is settled exactly from P.
 #include "common.cuh"
 
 namespace riann {
@@ -28,29 +33,33 @@ __device__ __forceinline__ bool in_ring(uint32_t A, uint32_t B, uint32_t C, uint
 }
 
 // Smallest member A in [0, B] (B itself is always a member: |sqrt B - sqrt B| = 0).
-// Membership is false..false true..true on [0, B]; gallop from the estimate,
-// then bisect, so any estimate error only costs iterations.
+// Membership is false..false true..true on [0, B].  The float estimate is
+// usually exact or off by one, so probe it and its neighbour first; otherwise
+// gallop from it and bisect, so an estimate error only costs iterations.
 __device__ uint32_t ring_low(uint32_t B, uint32_t C, uint32_t p2, uint32_t q2, float est) {
-  if (in_ring(0u, B, C, p2, q2)) return 0u;
-  uint32_t a = est <= 0.f ? 0u : (est >= (float)B ? B : (uint32_t)est);
+  uint32_t a = est <= 0.f ? 0u : (est >= (float)B ? B : (uint32_t)ceilf(est));
+  if (a == 0u && in_ring(0u, B, C, p2, q2)) return 0u;
   uint32_t good, bad;   // in_ring(good), !in_ring(bad), bad < good
   if (in_ring(a, B, C, p2, q2)) {
-    good = a;
-    for (uint32_t step = 1;; step <<= 1) {
-      uint32_t c = good > step ? good - step : 0u;
+    if (a == 0u || !in_ring(a - 1, B, C, p2, q2)) return a;
+    good = a - 1;
+    for (uint32_t step = 2;; step <<= 1) {
+      const uint32_t c = good > step ? good - step : 0u;
       if (!in_ring(c, B, C, p2, q2)) { bad = c; break; }
+      if (c == 0u) return 0u;
       good = c;
     }
   } else {
-    bad = a;
-    for (uint32_t step = 1;; step <<= 1) {
-      uint32_t c = (B - bad > step) ? bad + step : B;
+    if (in_ring(a + 1, B, C, p2, q2)) return a + 1;
+    bad = a + 1;
+    for (uint32_t step = 2;; step <<= 1) {
+      const uint32_t c = (B - bad > step) ? bad + step : B;
       if (in_ring(c, B, C, p2, q2)) { good = c; break; }
       bad = c;
     }
   }
   while (good - bad > 1) {
-    uint32_t mid = bad + (good - bad) / 2;
+    const uint32_t mid = bad + (good - bad) / 2;
     if (in_ring(mid, B, C, p2, q2)) good = mid; else bad = mid;
   }
   return good;
@@ -59,47 +68,32 @@ __device__ uint32_t ring_low(uint32_t B, uint32_t C, uint32_t p2, uint32_t q2, f
 // Largest member A in [B, Amax]; membership is true..true false..false there.
 __device__ uint32_t ring_high(uint32_t B, uint32_t C, uint32_t p2, uint32_t q2, float est,
                               uint32_t Amax) {
-  if (in_ring(Amax, B, C, p2, q2)) return Amax;
   uint32_t a = est <= (float)B ? B : (est >= (float)Amax ? Amax : (uint32_t)est);
   uint32_t good, bad;   // in_ring(good), !in_ring(bad), good < bad
   if (in_ring(a, B, C, p2, q2)) {
-    good = a;
-    for (uint32_t step = 1;; step <<= 1) {
-      uint32_t c = (Amax - good > step) ? good + step : Amax;
+    if (a == Amax || !in_ring(a + 1, B, C, p2, q2)) return a;
+    good = a + 1;
+    for (uint32_t step = 2;; step <<= 1) {
+      const uint32_t c = (Amax - good > step) ? good + step : Amax;
       if (!in_ring(c, B, C, p2, q2)) { bad = c; break; }
+      if (c == Amax) return Amax;
       good = c;
     }
   } else {
-    bad = a;
-    for (uint32_t step = 1;; step <<= 1) {
-      uint32_t c = (bad - B > step) ? bad - step : B;
+    // a > B here (B is a member)
+    if (in_ring(a - 1, B, C, p2, q2)) return a - 1;
+    bad = a - 1;
+    for (uint32_t step = 2;; step <<= 1) {
+      const uint32_t c = (bad - B > step) ? bad - step : B;
       if (in_ring(c, B, C, p2, q2)) { good = c; break; }
       bad = c;
     }
   }
   while (bad - good > 1) {
-    uint32_t mid = good + (bad - good) / 2;
+    const uint32_t mid = good + (bad - good) / 2;
     if (in_ring(mid, B, C, p2, q2)) good = mid; else bad = mid;
   }
   return good;
-}
-
-// first j in [0, n) with t[j] >= v  /  first j with t[j] > v
-__device__ __forceinline__ int lower_bound_u32(const uint32_t* __restrict__ t, int n, uint32_t v) {
-  int lo = 0, len = n;
-  while (len > 0) {
-    int half = len >> 1;
-    if (__ldg(t + lo + half) < v) { lo += half + 1; len -= half + 1; } else { len = half; }
-  }
-  return lo;
-}
-__device__ __forceinline__ int upper_bound_u32(const uint32_t* __restrict__ t, int n, uint32_t v) {
-  int lo = 0, len = n;
-  while (len > 0) {
-    int half = len >> 1;
-    if (__ldg(t + lo + half) <= v) { lo += half + 1; len -= half + 1; } else { len = half; }
-  }
-  return lo;
 }
 
 // Sum of squared byte differences of 4 words of q against one 16-byte vector.
@@ -112,21 +106,114 @@ __device__ __forceinline__ uint32_t sq4(const uint32_t* q, uint4 u, uint32_t acc
   return acc;
 }
 
+// code(x) = (number of bucket edges <= x) - 1, in [-1, 255].  Two levels:
+// every 16th edge in shared memory, then the 16 edges of one 64-byte segment.
+__device__ __forceinline__ int bucket_code(const uint32_t* __restrict__ coarse, const uint32_t* __restrict__ e,
+                                           uint32_t x) {
+  int c = 0;   // coarse edges <= x
+#pragma unroll
+  for (int half = 8; half > 0; half >>= 1)
+    if (coarse[c + half - 1] <= x) c += half;
+  if (c == 15 && coarse[15] <= x) c = 16;
+  if (c == 0) return -1;
+  const uint4* seg = reinterpret_cast<const uint4*>(e + 16 * (c - 1));
+  int cnt = 0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const uint4 u = __ldg(seg + v);
+    cnt += (u.x <= x) + (u.y <= x) + (u.z <= x) + (u.w <= x);
+  }
+  return 16 * (c - 1) + cnt - 1;
+}
+
+// Number of entries of the sorted range t[lo, hi) below v (le: at most v),
+// counted by the whole warp with coalesced loads; every lane gets the result.
+__device__ __forceinline__ int warp_count_below(const uint32_t* __restrict__ t, int lo, int hi, uint32_t v,
+                                                bool le, int lane) {
+  int c = 0;
+  for (int base = lo; base < hi; base += 256) {
+    uint32_t x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int j = base + 32 * i + lane;
+      x[i] = j < hi ? __ldg(t + j) : 0xffffffffu;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int j = base + 32 * i + lane;
+      c += __popc(__ballot_sync(kFull, j < hi && (le ? x[i] <= v : x[i] < v)));
+    }
+  }
+  return c;
+}
+
+// Rank range [first >= lo, first > hi) of the exact ring [lo, hi] in TA[m]:
+// the first end lies in bucket clo's rank range, the second in bucket chi's.
+__device__ __forceinline__ int2 ring_run(const uint32_t* __restrict__ ta, const uint32_t* __restrict__ rb,
+                                         int clo, int chi, uint32_t lo, uint32_t hi, int lane) {
+  const int a0 = clo < 0 ? 0 : (int)__ldg(rb + clo), a1 = (int)__ldg(rb + clo + 1);
+  const int b0 = chi < 0 ? 0 : (int)__ldg(rb + chi), b1 = (int)__ldg(rb + chi + 1);
+  const int a = a0 + warp_count_below(ta, a0, a1, lo, false, lane);
+  const int b = b0 + warp_count_below(ta, b0, b1, hi, true, lane);
+  return make_int2(a, b > a ? b : a);
+}
+
+// Byte-wise unsigned compares on four packed 8-bit codes, in plain 32-bit
+// integer operations.  (x | H) - (y & ~H) subtracts the low 7 bits of every
+// byte without a borrow crossing into the next byte; bit 7 of each result byte
+// is then [x_lo7 >= y_lo7], which with the two top bits decides x >= y.
+constexpr uint32_t kHi = 0x80808080u;
+
+__device__ __forceinline__ uint32_t bytes_ge(uint32_t x, uint32_t y) {   // 0x80 where x >= y
+  const uint32_t t = (x | kHi) - (y & ~kHi);
+  return ((x & ~y) | (~(x ^ y) & t)) & kHi;
+}
+
+__device__ __forceinline__ uint32_t bytes_eq(uint32_t x, uint32_t y) {   // 0x80 where x == y
+  const uint32_t z = x ^ y;
+  return ~(((z & ~kHi) + ~kHi) | z) & kHi;
+}
+
+// every byte with lo <= code <= hi, or marked "always passes" in any4
+__device__ __forceinline__ bool codes_pass(uint32_t w, uint32_t lo4, uint32_t hi4, uint32_t any4) {
+  return ((bytes_ge(w, lo4) & bytes_ge(hi4, w)) | (any4 & kHi)) == kHi;
+}
+
+// bit (4g + i) set where byte i of w sits on a boundary bucket of key 4g + i
+__device__ __forceinline__ unsigned long long boundary_bits(uint32_t w, uint32_t lo4, uint32_t hi4, uint32_t any4,
+                                                            int g) {
+  const uint32_t eq = (bytes_eq(w, lo4) | bytes_eq(w, hi4)) & ~any4;
+  const uint32_t b = (((eq >> 7) * 0x00204081u) >> 21) & 0xfu;   // bits 7, 15, 23, 31 -> 0..3
+  return (unsigned long long)b << (4 * g);
+}
+
+constexpr int kQueue = 256;   // per-warp ring buffer of stage-1 survivors
+
 template <int C>
-__global__ void __launch_bounds__(kWarps * 32) k_sparse(SparseArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, C == 1 ? 4 : 2) k_sparse(SparseArgs a) {
   constexpr int D = 64 * C, NW = D / 4;
   constexpr int TROW = (TX + 7) * C;              // tile row bytes
   constexpr int TROWP = ((TROW + 8) + 3) & ~3;    // + room for the 8-byte funnel reads
   constexpr int KPW = NW + 1;                     // key-point row stride in words (odd: no bank conflicts)
+  constexpr int kMaxG = kMaxK / 4;
   __shared__ __align__(16) uint8_t s_tile[(TY + 7) * TROWP];
   __shared__ uint32_t s_kp[kMaxK * KPW];
-  __shared__ uint32_t s_lo[kWarps][kMaxK];
+  __shared__ uint32_t s_coarse[kMaxK][16];        // every 16th bucket edge per key
+  __shared__ uint32_t s_lo[kWarps][kMaxK];        // exact ring bounds on A
   __shared__ uint32_t s_hi[kWarps][kMaxK];
+  __shared__ int16_t s_clo[kWarps][kMaxK];        // their bucket codes (-1..255)
+  __shared__ int16_t s_chi[kWarps][kMaxK];
+  __shared__ uint32_t s_ub[kWarps][kMaxK];        // bucket-granular upper bound on |Ring_m|
+  __shared__ uint32_t s_lo4[kWarps][kMaxG];       // per group: packed code ranges
+  __shared__ uint32_t s_hi4[kWarps][kMaxG];
+  __shared__ uint32_t s_any4[kWarps][kMaxG];      // bytes of keys that always pass (seed, padding)
+  __shared__ uint8_t s_ord[kWarps][kMaxG];        // group check order
+  __shared__ int32_t s_queue[kWarps][kQueue];     // stage-1 survivors (seed-run positions)
   __shared__ int32_t s_dense[TY * TX];
   __shared__ int s_next, s_ndense, s_dense_base;
-  __shared__ unsigned long long s_stat[3];   // ring-answered queries, sum of seed sizes, sum of |S|
+  __shared__ unsigned long long s_stat[3];        // ring-answered queries, scanned entries, sum of |S|
 
-  const int K = a.K, n = a.n;
+  const int K = a.K, n = a.n, G = a.G;
   const int tiles_x = (a.Wq + TX - 1) / TX;
   const int ty0 = (blockIdx.x / tiles_x) * TY;
   const int tx0 = (blockIdx.x % tiles_x) * TX;
@@ -134,6 +221,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_sparse(SparseArgs a) {
   {
     const uint32_t* kp = reinterpret_cast<const uint32_t*>(a.KP);
     for (int i = threadIdx.x; i < K * NW; i += blockDim.x) s_kp[(i / NW) * KPW + (i % NW)] = kp[i];
+    for (int i = threadIdx.x; i < K * 16; i += blockDim.x) s_coarse[i >> 4][i & 15] = __ldg(a.E + (i >> 4) * kBuckets + 16 * (i & 15));
     const int64_t rowb = (int64_t)a.W * C;
     for (int i = threadIdx.x; i < (TY + 7) * TROWP; i += blockDim.x) {
       const int r = i / TROWP, c = i % TROWP;
@@ -191,11 +279,12 @@ __global__ void __launch_bounds__(kWarps * 32) k_sparse(SparseArgs a) {
       for (int v = 0; v < NW / 4; ++v) Cd = sq4(q + 4 * v, __ldg(r4 + v), Cd);
     }
 
-    // a2: per ring, B_m = ||q - k_m||^2, exact bounds [lo, hi] on A, and the
-    // ring's run [jl, jh) in the sorted list of key m (two binary searches).
-    unsigned long long seedkey = ~0ull;
-    int jl[2] = {0, 0}, jh[2] = {0, 0};
+    // a2: per ring m (lane m and m+32): B_m, exact bounds [lo, hi] on A, their
+    // bucket codes, and bucket-granular bounds lb <= |Ring_m| <= ub.
     const float sC = (float)Cd;
+    unsigned long long seedkey = ~0ull;
+    bool small = false;      // some ring certainly holds <= ring_limit references
+    bool maybe = false;      // some ring might (its lower bound is <= ring_limit)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int m = lane + 32 * h;
@@ -211,14 +300,23 @@ __global__ void __launch_bounds__(kWarps * 32) k_sparse(SparseArgs a) {
         const float base = (float)B + alpha * alpha * sC;
         const uint32_t lo = ring_low(B, Cd, p2, q2, base - cross);
         const uint32_t hi = ring_high(B, Cd, p2, q2, base + cross, Amax);
+        const uint32_t* e = a.E + m * kBuckets;
+        const uint32_t* rb = a.RB + m * (kBuckets + 1);
+        const int clo = bucket_code(s_coarse[m], e, lo);
+        const int chi = bucket_code(s_coarse[m], e, hi);
+        const uint32_t ub = __ldg(rb + chi + 1) - (clo < 0 ? 0u : __ldg(rb + clo));
+        const uint32_t lb = chi > clo + 1 ? __ldg(rb + chi) - __ldg(rb + clo + 1) : 0u;
         s_lo[warp][m] = lo;
         s_hi[warp][m] = hi;
-        const uint32_t* ta = a.TA + (int64_t)m * n;
-        jl[h] = lower_bound_u32(ta, n, lo);
-        jh[h] = upper_bound_u32(ta, n, hi);
-        const unsigned long long key =
-            ((unsigned long long)(uint32_t)(jh[h] - jl[h]) << 32) | (unsigned)m;
+        s_clo[warp][m] = (int16_t)clo;
+        s_chi[warp][m] = (int16_t)chi;
+        s_ub[warp][m] = ub;
+        const unsigned long long key = ((unsigned long long)ub << 32) | (unsigned)m;
         seedkey = key < seedkey ? key : seedkey;
+        if (a.ring_limit >= 0) {
+          if (ub <= (uint32_t)a.ring_limit) small = true;
+          else if (lb <= (uint32_t)a.ring_limit) maybe = true;
+        }
       }
     }
 #pragma unroll
@@ -226,33 +324,146 @@ __global__ void __launch_bounds__(kWarps * 32) k_sparse(SparseArgs a) {
       const unsigned long long v = __shfl_xor_sync(kFull, seedkey, o);
       seedkey = v < seedkey ? v : seedkey;
     }
-    const uint32_t nseed = (uint32_t)(seedkey >> 32);
     const int ms = (int)(seedkey & 0xffffffffu);
-    const int jlo = __shfl_sync(kFull, (ms >> 5) ? jl[1] : jl[0], ms & 31);
-    const int jhi = __shfl_sync(kFull, (ms >> 5) ? jh[1] : jh[0], ms & 31);
     __syncwarp();
 
-    if (a.ring_limit >= 0 && nseed > (uint32_t)a.ring_limit) {
-      // rings too wide: brute force over R, done by the dense path afterwards
-      if (lane == 0) s_dense[atomicAdd(&s_ndense, 1)] = (int32_t)qi;
-      continue;
+    // routing: brute force iff every ring holds more than ring_limit references
+    if (a.ring_limit >= 0 && !__any_sync(kFull, small)) {
+      bool found = false;
+      unsigned cand = __ballot_sync(kFull, maybe);
+      // exact sizes of the rings whose bucket bounds straddle the limit
+      for (int h = 0; h < 2 && !found; ++h) {
+        unsigned todo = 0;
+        const int m0 = lane + 32 * h;
+        bool mine = false;
+        if (m0 < K && cand) {
+          const int clo = s_clo[warp][m0], chi = s_chi[warp][m0];
+          const uint32_t* rb = a.RB + m0 * (kBuckets + 1);
+          const uint32_t lb = chi > clo + 1 ? __ldg(rb + chi) - __ldg(rb + clo + 1) : 0u;
+          mine = s_ub[warp][m0] > (uint32_t)a.ring_limit && lb <= (uint32_t)a.ring_limit;
+        }
+        todo = __ballot_sync(kFull, mine);
+        while (todo && !found) {
+          const int m = __ffs(todo) - 1 + 32 * h;
+          todo &= todo - 1;
+          const int2 run = ring_run(a.TA + (int64_t)m * n, a.RB + m * (kBuckets + 1), s_clo[warp][m],
+                                    s_chi[warp][m], s_lo[warp][m], s_hi[warp][m], lane);
+          if ((uint32_t)(run.y - run.x) <= (uint32_t)a.ring_limit) found = true;
+        }
+      }
+      if (!found) {
+        if (lane == 0) s_dense[atomicAdd(&s_ndense, 1)] = (int32_t)qi;
+        continue;
+      }
     }
 
-    // a3 + a4: enumerate the seed ring, keep references inside every other
-    // ring, verify survivors by full distance; r_p is always a candidate.
+    // exact run of the seed ring in its sorted list (the whole warp searches)
+    const int2 run = ring_run(a.TA + (int64_t)ms * n, a.RB + ms * (kBuckets + 1), s_clo[warp][ms],
+                              s_chi[warp][ms], s_lo[warp][ms], s_hi[warp][ms], lane);
+    const int jlo = run.x, jhi = run.y;
+
+    // per group of 4 keys: packed code ranges, keys that always pass, and an
+    // estimate of the fraction of references passing (product of ub / n)
+    float est = 2.f;
+    if (lane < G) {
+      uint32_t lo4 = 0, hi4 = 0, any4 = 0;
+      est = 1.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int k = 4 * lane + i;
+        uint32_t l = 0, hh = 255, any = 0xffu;
+        if (k < K && k != ms) {
+          const int clo = s_clo[warp][k], chi = s_chi[warp][k];
+          l = (uint32_t)(clo < 0 ? 0 : clo);
+          hh = (uint32_t)(chi < 0 ? 0 : chi);
+          if (chi < 0) l = 1;                 // empty ring: no code fits
+          any = 0;
+          est *= (float)s_ub[warp][k] / (float)n;
+        }
+        lo4 |= l << (8 * i);
+        hi4 |= hh << (8 * i);
+        any4 |= any << (8 * i);
+      }
+      s_lo4[warp][lane] = lo4;
+      s_hi4[warp][lane] = hi4;
+      s_any4[warp][lane] = any4;
+    }
+    {
+      // rank of this lane's group by ascending estimate (ties: lower group)
+      int rank = 0;
+      for (int g2 = 0; g2 < G; ++g2) {
+        const float e2 = __shfl_sync(kFull, est, g2);
+        rank += (e2 < est) || (e2 == est && g2 < lane);
+      }
+      if (lane < G) s_ord[warp][rank] = (uint8_t)lane;
+    }
+    __syncwarp();
+
+    // a3 + a4.  Stage 1: each lane tests 4 consecutive seed-run entries (one
+    // 16-byte load of the most selective group's codes, next chunk prefetched)
+    // and the survivors against the next two groups; survivors go to a
+    // per-warp ring buffer (warp prefix sum).  Stage 2: each batch of 32
+    // queued entries is tested against every group (entry-major codes),
+    // boundary buckets are settled exactly from P, members are verified.
     unsigned long long best = lane == 0 ? (((unsigned long long)Cd << 32) | (unsigned)rp) : ~0ull;
     uint32_t cnt = 0;
+    const uint32_t* cw = a.CW + (int64_t)ms * G * a.nw;
     const int32_t* tid = a.Tid + (int64_t)ms * n;
-    for (int j = jlo + lane; j < jhi; j += 32) {
-      const int r = __ldg(tid + j);
-      const uint32_t* pr = a.P + (int64_t)r * K;
-      bool ok = true;
-      for (int m = 0; m < K; ++m) {
-        if (m == ms) continue;
-        const uint32_t v = __ldg(pr + m);
-        if (v < s_lo[warp][m] || v > s_hi[warp][m]) { ok = false; break; }
+    const int ns1 = G < 3 ? G : 3;
+    const int g0 = s_ord[warp][0];
+    const int g1 = s_ord[warp][ns1 > 1 ? 1 : 0];
+    const int g2 = s_ord[warp][ns1 > 2 ? 2 : 0];
+    const uint32_t lo0 = s_lo4[warp][g0], hi0 = s_hi4[warp][g0], any0 = s_any4[warp][g0];
+    const uint32_t lo1 = s_lo4[warp][g1], hi1 = s_hi4[warp][g1], any1 = s_any4[warp][g1];
+    const uint32_t lo2 = s_lo4[warp][g2], hi2 = s_hi4[warp][g2], any2 = s_any4[warp][g2];
+    const uint4* cw0 = reinterpret_cast<const uint4*>(cw + (int64_t)g0 * a.nw);
+    const uint32_t* cw1 = cw + (int64_t)g1 * a.nw;
+    const uint32_t* cw2 = cw + (int64_t)g2 * a.nw;
+    const uint4* cwe = reinterpret_cast<const uint4*>(a.CWE + (int64_t)ms * n * a.GP);
+    const int gq = a.GP / 4;                       // uint4 words per entry-major row
+    int32_t* queue = s_queue[warp];
+    int qhead = 0, qn = 0;                         // ring buffer: [qhead, qhead + qn)
+
+    auto drain = [&](int take) {
+      bool alive = lane < take;
+      const int j = alive ? queue[(qhead + lane) & (kQueue - 1)] : 0;
+      unsigned long long unc = 0;
+      if (alive) {
+        for (int c4 = 0; c4 < gq && alive; ++c4) {
+          const uint4 w4 = __ldg(cwe + (int64_t)j * gq + c4);
+          const uint32_t ws[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int g = 4 * c4 + u;
+            if (g < G) {
+              const uint32_t lo4 = s_lo4[warp][g], hi4 = s_hi4[warp][g], any4 = s_any4[warp][g];
+              if (!codes_pass(ws[u], lo4, hi4, any4)) alive = false;
+              unc |= boundary_bits(ws[u], lo4, hi4, any4, g);
+            }
+          }
+        }
       }
-      if (ok) {
+      int r = 0;
+      if (alive) {
+        r = __ldg(tid + j);
+        const uint32_t* pr = a.P + (int64_t)r * K;
+        while (unc && alive) {
+          // up to four exact checks with their loads issued together
+          int k[4];
+          uint32_t v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            k[u] = unc ? __ffsll((long long)unc) - 1 : -1;
+            unc &= unc - 1;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = k[u] >= 0 ? __ldg(pr + k[u]) : 0u;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (k[u] >= 0 && (v[u] < s_lo[warp][k[u]] || v[u] > s_hi[warp][k[u]])) alive = false;
+        }
+      }
+      if (alive) {
         ++cnt;
         const uint4* r4 = reinterpret_cast<const uint4*>(a.R + (int64_t)r * D);
         uint32_t d = 0;
@@ -261,6 +472,64 @@ __global__ void __launch_bounds__(kWarps * 32) k_sparse(SparseArgs a) {
         const unsigned long long key = ((unsigned long long)d << 32) | (unsigned)r;
         best = key < best ? key : best;
       }
+    };
+
+    const int ja = jlo & ~3;
+    uint4 cur = make_uint4(0, 0, 0, 0);
+    if (ja + 4 * lane < jhi) cur = __ldg(cw0 + (ja >> 2) + lane);
+    for (int base = ja;; base += 128) {
+      const bool more = base < jhi;
+      if (more) {
+        uint4 nxt = make_uint4(0, 0, 0, 0);
+        if (base + 128 + 4 * lane < jhi) nxt = __ldg(cw0 + ((base + 128) >> 2) + lane);
+        const int j0 = base + 4 * lane;
+        const uint32_t wv[4] = {cur.x, cur.y, cur.z, cur.w};
+        unsigned bits = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (j0 + u >= jlo && j0 + u < jhi && codes_pass(wv[u], lo0, hi0, any0)) bits |= 1u << u;
+        if (ns1 > 1 && __any_sync(kFull, bits != 0)) {
+          uint32_t w1[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) w1[u] = (bits >> u) & 1u ? __ldg(cw1 + j0 + u) : 0u;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (((bits >> u) & 1u) && !codes_pass(w1[u], lo1, hi1, any1)) bits &= ~(1u << u);
+          if (ns1 > 2 && __any_sync(kFull, bits != 0)) {
+            uint32_t w2[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) w2[u] = (bits >> u) & 1u ? __ldg(cw2 + j0 + u) : 0u;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (((bits >> u) & 1u) && !codes_pass(w2[u], lo2, hi2, any2)) bits &= ~(1u << u);
+          }
+        }
+        // warp prefix sum of survivor counts -> append to the ring buffer
+        const int c = __popc(bits);
+        int pre = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(kFull, pre, o);
+          if (lane >= o) pre += v;
+        }
+        const int tot = __shfl_sync(kFull, pre, 31);
+        pre -= c;
+        int slot = qhead + qn + pre;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if ((bits >> u) & 1u) queue[(slot++) & (kQueue - 1)] = j0 + u;
+        qn += tot;
+        cur = nxt;
+      }
+      // drain full batches; after the last chunk also the remainder
+      while (qn >= 32 || (!more && qn > 0)) {
+        const int take = qn < 32 ? qn : 32;
+        __syncwarp();
+        drain(take);
+        qhead = (qhead + take) & (kQueue - 1);
+        qn -= take;
+      }
+      if (!more) break;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -274,7 +543,7 @@ __global__ void __launch_bounds__(kWarps * 32) k_sparse(SparseArgs a) {
       if (a.out_count) a.out_count[qi] = cnt;
       if (a.stats) {
         atomicAdd(&s_stat[0], 1ull);
-        atomicAdd(&s_stat[1], (unsigned long long)nseed);
+        atomicAdd(&s_stat[1], (unsigned long long)(jhi - jlo));
         atomicAdd(&s_stat[2], (unsigned long long)cnt);
       }
     }
