@@ -176,6 +176,7 @@ int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t cha
   ix->C = channels;
   ix->D = 64 * channels;
   ix->n_pad = (n + kDenseTileN - 1) / kDenseTileN * kDenseTileN;
+  ix->Kp = (K + 3) / 4 * 4;
   ix->G = (K + 3) / 4;
   ix->GP = (ix->G + 3) / 4 * 4;
   ix->nw = (n + 3) / 4 * 4;
@@ -185,7 +186,7 @@ int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t cha
   if (e == cudaSuccess) e = dalloc(&ix->KP, (size_t)K * D, tot);
   if (e == cudaSuccess) e = dalloc(&ix->Rbf, (size_t)ix->n_pad * D, tot);
   if (e == cudaSuccess) e = dalloc(&ix->rnorm, (size_t)ix->n_pad, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->P, (size_t)n * K, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->P, (size_t)n * ix->Kp, tot);
   if (e == cudaSuccess) e = dalloc(&ix->TA, (size_t)n * K, tot);
   if (e == cudaSuccess) e = dalloc(&ix->Tid, (size_t)n * K, tot);
   if (e == cudaSuccess) e = dalloc(&ix->E, (size_t)K * kBuckets, tot);
@@ -241,7 +242,9 @@ int riann_index_tables(riann_index_t idx, riann_stream_t stream, uint32_t* P, ui
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t cnt = (size_t)idx->n * idx->K;
   cudaError_t e = cudaSuccess;
-  if (P) e = cudaMemcpyAsync(P, idx->P, cnt * sizeof(uint32_t), cudaMemcpyDefault, s);
+  if (P)
+    e = cudaMemcpy2DAsync(P, sizeof(uint32_t) * idx->K, idx->P, sizeof(uint32_t) * idx->Kp,
+                          sizeof(uint32_t) * idx->K, (size_t)idx->n, cudaMemcpyDefault, s);
   if (e == cudaSuccess && TA) e = cudaMemcpyAsync(TA, idx->TA, cnt * sizeof(uint32_t), cudaMemcpyDefault, s);
   if (e == cudaSuccess && Tid) e = cudaMemcpyAsync(Tid, idx->Tid, cnt * sizeof(int32_t), cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -307,6 +310,7 @@ int riann_annf_frame(riann_index_t idx, const riann_params* p, riann_stream_t st
   sa.nw = ix.nw;
   sa.n = ix.n;
   sa.K = ix.K;
+  sa.Kp = ix.Kp;
   sa.G = ix.G;
   sa.alpha_num = p->alpha_num;
   sa.alpha_den = p->alpha_den;

@@ -33,12 +33,13 @@ __host__ __device__ constexpr uint32_t max_sqdist(int dim) { return (uint32_t)di
 struct Index {
   int device = 0;
   int n = 0, K = 0, C = 0, D = 0;
+  int Kp = 0;                     // K rounded up to 4 (row stride of P)
   int n_pad = 0;                  // n rounded up to kDenseTileN
   uint8_t* R = nullptr;           // [n][D] reference patches
   uint8_t* KP = nullptr;          // [K][D] key points
   __nv_bfloat16* Rbf = nullptr;   // [n_pad][D] bf16 copy (exact: values 0..255); pad rows zero
   float* rnorm = nullptr;         // [n_pad] ||r||^2 (exact integers in fp32); pad rows +inf
-  uint32_t* P = nullptr;          // [n][K] ||k_m - r||^2
+  uint32_t* P = nullptr;          // [n][Kp] ||k_m - r||^2 (rows padded to Kp = K rounded up to 4; pad 0)
   uint32_t* TA = nullptr;         // [K][n] per key: distances ascending
   int32_t* Tid = nullptr;         // [K][n] per key: reference index of each TA entry
   // 8-bit bucket codes: code_m(A) = max{b : E[m][b] <= A}, edges at every
@@ -93,7 +94,7 @@ struct SparseArgs {
   const uint32_t* RB;
   const uint32_t* CW;
   const uint32_t* CWE;
-  int n, K, G, GP, nw;
+  int n, K, Kp, G, GP, nw;
   int alpha_num, alpha_den, ring_limit;
   int32_t* dense_list;
   uint32_t* dense_count;

@@ -6,13 +6,18 @@
 namespace riann {
 namespace {
 
-// P[r][m] = ||k_m - R_r||^2.  One thread per (r, m); words compared with
-// per-byte absolute differences and a 4-way dot product of them with themselves.
+// P[r][m] = ||k_m - R_r||^2 (row stride Kp, pad entries 0).  One thread per
+// (r, m); words compared with per-byte absolute differences and a 4-way dot
+// product of them with themselves.
 __global__ void k_key_distances(const uint8_t* __restrict__ R, const uint8_t* __restrict__ KP,
-                                int n, int K, int D, uint32_t* __restrict__ P) {
+                                int n, int K, int Kp, int D, uint32_t* __restrict__ P) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (int64_t)n * K) return;
-  int r = (int)(t / K), m = (int)(t % K);
+  if (t >= (int64_t)n * Kp) return;
+  int r = (int)(t / Kp), m = (int)(t % Kp);
+  if (m >= K) {
+    P[t] = 0;
+    return;
+  }
   const uint32_t* a = reinterpret_cast<const uint32_t*>(R + (int64_t)r * D);
   const uint32_t* b = reinterpret_cast<const uint32_t*>(KP + (int64_t)m * D);
   uint32_t s = 0;
@@ -47,13 +52,13 @@ __global__ void k_prep_refs(const uint8_t* __restrict__ R, int n, int n_pad, int
 }
 
 // keys[m][j] = (P[j][m] << 32) | j for j < n, all-ones padding up to NP.
-__global__ void k_make_keys(const uint32_t* __restrict__ P, int n, int K, int NP,
+__global__ void k_make_keys(const uint32_t* __restrict__ P, int n, int Kp, int NP,
                             unsigned long long* __restrict__ keys) {
   int j = blockIdx.x * blockDim.x + threadIdx.x;
   int m = blockIdx.y;
   if (j >= NP) return;
   keys[(int64_t)m * NP + j] =
-      j < n ? (((unsigned long long)P[(int64_t)j * K + m]) << 32) | (unsigned)j : ~0ull;
+      j < n ? (((unsigned long long)P[(int64_t)j * Kp + m]) << 32) | (unsigned)j : ~0ull;
 }
 
 constexpr int kChunk = 2048;   // elements sorted in shared memory by one block
@@ -132,12 +137,12 @@ __global__ void k_bucket_edges(const uint32_t* __restrict__ TA, int n, int K, ui
 }
 
 // code[r][m] = number of edges of key m that are <= P[r][m], minus one.
-__global__ void k_codes(const uint32_t* __restrict__ P, const uint32_t* __restrict__ E, int n, int K,
+__global__ void k_codes(const uint32_t* __restrict__ P, const uint32_t* __restrict__ E, int n, int K, int Kp,
                         uint8_t* __restrict__ code) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)n * K) return;
   const int m = (int)(t % K);
-  const uint32_t a = P[t];
+  const uint32_t a = P[(t / K) * Kp + m];
   const uint32_t* e = E + m * kBuckets;
   int lo = 0, len = kBuckets;                  // first edge > a
   while (len > 0) {
@@ -173,8 +178,8 @@ __global__ void k_pack_codes(const int32_t* __restrict__ Tid, const uint8_t* __r
 cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
   const int n = ix.n, K = ix.K, D = ix.D;
   {
-    int64_t tot = (int64_t)n * K;
-    k_key_distances<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ix.R, ix.KP, n, K, D, ix.P);
+    int64_t tot = (int64_t)n * ix.Kp;
+    k_key_distances<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ix.R, ix.KP, n, K, ix.Kp, D, ix.P);
   }
   k_prep_refs<<<ix.n_pad, 64, 0, s>>>(ix.R, n, ix.n_pad, D, ix.Rbf, ix.rnorm);
   int NP = kChunk;
@@ -182,7 +187,7 @@ cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
   unsigned long long* keys = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&keys, sizeof(unsigned long long) * (size_t)NP * K, s);
   if (e != cudaSuccess) return e;
-  k_make_keys<<<dim3((NP + 255) / 256, K), 256, 0, s>>>(ix.P, n, K, NP, keys);
+  k_make_keys<<<dim3((NP + 255) / 256, K), 256, 0, s>>>(ix.P, n, ix.Kp, NP, keys);
   k_bitonic_shared<<<dim3(NP / kChunk, K), kChunk / 2, 0, s>>>(keys, NP, 0);
   for (int k = 2 * kChunk; k <= NP; k <<= 1) {
     for (int j = k >> 1; j >= kChunk; j >>= 1)
@@ -199,7 +204,7 @@ cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   {
     const int64_t tot = (int64_t)n * K;
-    k_codes<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ix.P, ix.E, n, K, code);
+    k_codes<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ix.P, ix.E, n, K, ix.Kp, code);
   }
   e = cudaMemsetAsync(ix.CW, 0, sizeof(uint32_t) * (size_t)K * ix.G * ix.nw, s);
   if (e != cudaSuccess) return e;

@@ -96,13 +96,14 @@ __device__ uint32_t ring_high(uint32_t B, uint32_t C, uint32_t p2, uint32_t q2, 
   return good;
 }
 
-// Sum of squared byte differences of 4 words of q against one 16-byte vector.
+// Sum of squared byte differences of two 16-byte vectors, added to acc.
 __device__ __forceinline__ uint32_t sq4(const uint32_t* q, uint4 u, uint32_t acc) {
+  const uint4 a = *reinterpret_cast<const uint4*>(q);
   uint32_t d;
-  d = __vabsdiffu4(q[0], u.x); acc = __dp4a(d, d, acc);
-  d = __vabsdiffu4(q[1], u.y); acc = __dp4a(d, d, acc);
-  d = __vabsdiffu4(q[2], u.z); acc = __dp4a(d, d, acc);
-  d = __vabsdiffu4(q[3], u.w); acc = __dp4a(d, d, acc);
+  d = __vabsdiffu4(a.x, u.x); acc = __dp4a(d, d, acc);
+  d = __vabsdiffu4(a.y, u.y); acc = __dp4a(d, d, acc);
+  d = __vabsdiffu4(a.z, u.z); acc = __dp4a(d, d, acc);
+  d = __vabsdiffu4(a.w, u.w); acc = __dp4a(d, d, acc);
   return acc;
 }
 
@@ -190,7 +191,7 @@ __device__ __forceinline__ unsigned long long boundary_bits(uint32_t w, uint32_t
 constexpr int kQueue = 256;   // per-warp ring buffer of stage-1 survivors
 
 template <int C>
-__global__ void __launch_bounds__(kWarps * 32, C == 1 ? 4 : 2) k_sparse(SparseArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(SparseArgs a) {
   constexpr int D = 64 * C, NW = D / 4;
   constexpr int TROW = (TX + 7) * C;              // tile row bytes
   constexpr int TROWP = ((TROW + 8) + 3) & ~3;    // + room for the 8-byte funnel reads
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(kWarps * 32, C == 1 ? 4 : 2) k_sparse(SparseAr
   __shared__ uint32_t s_any4[kWarps][kMaxG];      // bytes of keys that always pass (seed, padding)
   __shared__ uint8_t s_ord[kWarps][kMaxG];        // group check order
   __shared__ int32_t s_queue[kWarps][kQueue];     // stage-1 survivors (seed-run positions)
+  __shared__ __align__(16) uint32_t s_q[kWarps][NW];   // the warp's query patch
   __shared__ int32_t s_dense[TY * TX];
   __shared__ int s_next, s_ndense, s_dense_base;
   __shared__ unsigned long long s_stat[3];        // ring-answered queries, scanned entries, sum of |S|
@@ -249,10 +251,10 @@ __global__ void __launch_bounds__(kWarps * 32, C == 1 ? 4 : 2) k_sparse(SparseAr
     if (y >= a.Hq || x >= a.Wq) continue;
     const int64_t qi = (int64_t)y * a.Wq + x;
 
-    // a1: the query patch, 4 bytes per register, (dy, dx, c) order
-    uint32_t q[NW];
-#pragma unroll
-    for (int w = 0; w < NW; ++w) {
+    // a1: the query patch, 4 bytes per word, (dy, dx, c) order, kept in shared
+    // memory for the whole query (registers go to the scan)
+    uint32_t* q = s_q[warp];
+    for (int w = lane; w < NW; w += 32) {
       const int dy = w / (2 * C), j = w % (2 * C);
       const int off = (ly + dy) * TROWP + lx * C + 4 * j;
       const int al = off & ~3;
@@ -260,6 +262,7 @@ __global__ void __launch_bounds__(kWarps * 32, C == 1 ? 4 : 2) k_sparse(SparseAr
       const uint32_t hi = *reinterpret_cast<const uint32_t*>(s_tile + al + 4);
       q[w] = __funnelshift_r(lo, hi, (off & 3) * 8);
     }
+    __syncwarp();
 
     // previous match r_p and temporal change C = ||q - r_p||^2 (Alg. 1: r_i, d_i)
     const int rp = __ldg(a.prev + qi);
@@ -419,91 +422,120 @@ __global__ void __launch_bounds__(kWarps * 32, C == 1 ? 4 : 2) k_sparse(SparseAr
     const uint4* cw0 = reinterpret_cast<const uint4*>(cw + (int64_t)g0 * a.nw);
     const uint32_t* cw1 = cw + (int64_t)g1 * a.nw;
     const uint32_t* cw2 = cw + (int64_t)g2 * a.nw;
+    constexpr int kMaxGl = kMaxK / 4;
+    (void)kMaxGl;
     const uint4* cwe = reinterpret_cast<const uint4*>(a.CWE + (int64_t)ms * n * a.GP);
     const int gq = a.GP / 4;                       // uint4 words per entry-major row
     int32_t* queue = s_queue[warp];
     int qhead = 0, qn = 0;                         // ring buffer: [qhead, qhead + qn)
 
     auto drain = [&](int take) {
+      // round 1: every group's codes (entry-major row) and the reference index
       bool alive = lane < take;
       const int j = alive ? queue[(qhead + lane) & (kQueue - 1)] : 0;
+      uint4 w4[4];
+      int r = 0;
+      if (alive) {
+#pragma unroll
+        for (int c4 = 0; c4 < 4; ++c4)
+          if (c4 < gq) w4[c4] = __ldg(cwe + (int64_t)j * gq + c4);
+        r = __ldg(tid + j);
+      }
       unsigned long long unc = 0;
       if (alive) {
-        for (int c4 = 0; c4 < gq && alive; ++c4) {
-          const uint4 w4 = __ldg(cwe + (int64_t)j * gq + c4);
-          const uint32_t ws[4] = {w4.x, w4.y, w4.z, w4.w};
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int g = 4 * c4 + u;
-            if (g < G) {
-              const uint32_t lo4 = s_lo4[warp][g], hi4 = s_hi4[warp][g], any4 = s_any4[warp][g];
-              if (!codes_pass(ws[u], lo4, hi4, any4)) alive = false;
-              unc |= boundary_bits(ws[u], lo4, hi4, any4, g);
+        for (int c4 = 0; c4 < 4; ++c4) {
+          if (c4 < gq) {
+            const uint32_t ws[4] = {w4[c4].x, w4[c4].y, w4[c4].z, w4[c4].w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const int g = 4 * c4 + u;
+              if (g < G) {
+                const uint32_t lo4 = s_lo4[warp][g], hi4 = s_hi4[warp][g], any4 = s_any4[warp][g];
+                if (!codes_pass(ws[u], lo4, hi4, any4)) alive = false;
+                unc |= boundary_bits(ws[u], lo4, hi4, any4, g);
+              }
             }
           }
         }
       }
-      int r = 0;
+      // round 2: the distances of the boundary-bucket keys, four keys per
+      // 16-byte load; round 3: the reference row of members
       if (alive) {
-        r = __ldg(tid + j);
-        const uint32_t* pr = a.P + (int64_t)r * K;
-        while (unc && alive) {
-          // up to four exact checks with their loads issued together
-          int k[4];
-          uint32_t v[4];
+        const uint4* p4 = reinterpret_cast<const uint4*>(a.P + (int64_t)r * a.Kp);
+        unsigned ug = 0;   // groups holding boundary-bucket keys
+#pragma unroll
+        for (int g = 0; g < kMaxG; ++g)
+          if ((unc >> (4 * g)) & 0xfull) ug |= 1u << g;
+        while (ug && alive) {
+          int gg[4];
+          uint4 pv[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            k[u] = unc ? __ffsll((long long)unc) - 1 : -1;
-            unc &= unc - 1;
+            gg[u] = ug ? __ffs(ug) - 1 : -1;
+            ug &= ug - 1;
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) v[u] = k[u] >= 0 ? __ldg(pr + k[u]) : 0u;
+          for (int u = 0; u < 4; ++u) pv[u] = gg[u] >= 0 ? __ldg(p4 + gg[u]) : make_uint4(0, 0, 0, 0);
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (k[u] >= 0 && (v[u] < s_lo[warp][k[u]] || v[u] > s_hi[warp][k[u]])) alive = false;
+          for (int u = 0; u < 4; ++u) {
+            if (gg[u] < 0) continue;
+            const uint32_t pw[4] = {pv[u].x, pv[u].y, pv[u].z, pv[u].w};
+            const unsigned ub4 = (unsigned)(unc >> (4 * gg[u])) & 0xfu;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int k = 4 * gg[u] + i;
+              if (((ub4 >> i) & 1u) && (pw[i] < s_lo[warp][k] || pw[i] > s_hi[warp][k])) alive = false;
+            }
+          }
         }
-      }
-      if (alive) {
-        ++cnt;
-        const uint4* r4 = reinterpret_cast<const uint4*>(a.R + (int64_t)r * D);
-        uint32_t d = 0;
+        if (alive) {
+          ++cnt;
+          const uint4* r4 = reinterpret_cast<const uint4*>(a.R + (int64_t)r * D);
+          uint32_t d = 0;
 #pragma unroll
-        for (int v = 0; v < NW / 4; ++v) d = sq4(q + 4 * v, __ldg(r4 + v), d);
-        const unsigned long long key = ((unsigned long long)d << 32) | (unsigned)r;
-        best = key < best ? key : best;
+          for (int v = 0; v < NW / 4; ++v) d = sq4(q + 4 * v, __ldg(r4 + v), d);
+          const unsigned long long key = ((unsigned long long)d << 32) | (unsigned)r;
+          best = key < best ? key : best;
+        }
       }
     };
 
     const int ja = jlo & ~3;
-    uint4 cur = make_uint4(0, 0, 0, 0);
-    if (ja + 4 * lane < jhi) cur = __ldg(cw0 + (ja >> 2) + lane);
+    const uint4* c1 = reinterpret_cast<const uint4*>(cw1);
+    const uint4* c2 = reinterpret_cast<const uint4*>(cw2);
+    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, a2 = a0;
+    if (ja + 4 * lane < jhi) {
+      a0 = __ldg(cw0 + (ja >> 2) + lane);
+      if (ns1 > 1) a1 = __ldg(c1 + (ja >> 2) + lane);
+      if (ns1 > 2) a2 = __ldg(c2 + (ja >> 2) + lane);
+    }
     for (int base = ja;; base += 128) {
       const bool more = base < jhi;
       if (more) {
-        uint4 nxt = make_uint4(0, 0, 0, 0);
-        if (base + 128 + 4 * lane < jhi) nxt = __ldg(cw0 + ((base + 128) >> 2) + lane);
+        // prefetch the next chunk of all three groups, then test this one
+        uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0, b2 = b0;
+        if (base + 128 + 4 * lane < jhi) {
+          const int o = ((base + 128) >> 2) + lane;
+          b0 = __ldg(cw0 + o);
+          if (ns1 > 1) b1 = __ldg(c1 + o);
+          if (ns1 > 2) b2 = __ldg(c2 + o);
+        }
         const int j0 = base + 4 * lane;
-        const uint32_t wv[4] = {cur.x, cur.y, cur.z, cur.w};
+        const uint32_t v0[4] = {a0.x, a0.y, a0.z, a0.w};
+        const uint32_t v1[4] = {a1.x, a1.y, a1.z, a1.w};
+        const uint32_t v2[4] = {a2.x, a2.y, a2.z, a2.w};
         unsigned bits = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (j0 + u >= jlo && j0 + u < jhi && codes_pass(wv[u], lo0, hi0, any0)) bits |= 1u << u;
-        if (ns1 > 1 && __any_sync(kFull, bits != 0)) {
-          uint32_t w1[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) w1[u] = (bits >> u) & 1u ? __ldg(cw1 + j0 + u) : 0u;
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (((bits >> u) & 1u) && !codes_pass(w1[u], lo1, hi1, any1)) bits &= ~(1u << u);
-          if (ns1 > 2 && __any_sync(kFull, bits != 0)) {
-            uint32_t w2[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) w2[u] = (bits >> u) & 1u ? __ldg(cw2 + j0 + u) : 0u;
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (((bits >> u) & 1u) && !codes_pass(w2[u], lo2, hi2, any2)) bits &= ~(1u << u);
-          }
+        for (int u = 0; u < 4; ++u) {
+          const bool ok = j0 + u >= jlo && j0 + u < jhi && codes_pass(v0[u], lo0, hi0, any0) &&
+                          (ns1 < 2 || codes_pass(v1[u], lo1, hi1, any1)) &&
+                          (ns1 < 3 || codes_pass(v2[u], lo2, hi2, any2));
+          bits |= (ok ? 1u : 0u) << u;
         }
+        a0 = b0;
+        a1 = b1;
+        a2 = b2;
         // warp prefix sum of survivor counts -> append to the ring buffer
         const int c = __popc(bits);
         int pre = c;
@@ -519,7 +551,6 @@ __global__ void __launch_bounds__(kWarps * 32, C == 1 ? 4 : 2) k_sparse(SparseAr
         for (int u = 0; u < 4; ++u)
           if ((bits >> u) & 1u) queue[(slot++) & (kQueue - 1)] = j0 + u;
         qn += tot;
-        cur = nxt;
       }
       // drain full batches; after the last chunk also the remainder
       while (qn >= 32 || (!more && qn > 0)) {
