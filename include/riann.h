@@ -64,7 +64,7 @@ enum {
   RIANN_ERR_TIMEOUT = 5,      /* a bounded device wait gave up                    */
   RIANN_ERR_ADMISSION = 6,    /* server: the stream does not fit the budget       */
   RIANN_ERR_DEVICE = 7,       /* a kernel reported bad input (see riann_status)   */
-  RIANN_ERR_TOO_LARGE = 8     /* frame exceeds riann_exact_nn_noalloc's fixed scratch */
+  RIANN_ERR_TOO_LARGE = 8     /* more queries than a fixed scratch or batch context holds */
 };
 
 /* Bits of the device status word. */
@@ -81,8 +81,9 @@ typedef struct {
   /* A query whose smallest ring holds more than ring_limit references is
    * answered by brute force over all of R (count = n).  -1: never. */
   int32_t ring_limit;
-  /* Performance knob only (candidate-scan granularity threshold); results
-   * never depend on it.  0 = library default. */
+  /* Performance knob only; results never depend on it.  0 = the index's
+   * tuned setting; 1..3 = number of 4-ring code groups the candidate scan
+   * tests before it compacts survivors (see riann_autotune). */
   int32_t cap;
 } riann_params;
 
@@ -204,6 +205,120 @@ int riann_frame_stats(riann_index_t idx, riann_stream_t stream, riann_frame_stat
 #define RIANN_SLOT_PREP 2
 int riann_profile_enable(riann_index_t idx, int on);
 int riann_profile_read(riann_index_t idx, riann_stream_t stream, float* ms, int32_t nslots);
+
+/* ------------------------------------------------------------------------
+ * Sessions: one per video stream.  A session keeps the stream's previous ANN
+ * field on the device between frames (Alg. 1: r_i = ANNF^(t-1)(x, y)), double
+ * buffered, plus the scratch of one frame, so sessions on different CUDA
+ * streams run concurrently.  The first frame of a session (and the first
+ * after riann_session_reset, e.g. at a known scene cut) is answered by brute
+ * force (Alg. 1 "Initialize").  Results are identical to chaining
+ * riann_annf_frame calls by hand.
+ * ------------------------------------------------------------------------ */
+typedef struct riann_session_s* riann_session_t;
+
+typedef struct {
+  int32_t H, W;
+  int64_t frames;          /* frames processed so far                    */
+  int32_t has_field;       /* 1 when a previous field is held            */
+  size_t device_bytes;     /* device memory the session holds            */
+} riann_session_info_t;
+
+/* Allocates the session for frames of H x W x channels(idx).  The session
+ * keeps a pointer to idx, which must outlive it. */
+int riann_session_create(riann_index_t idx, int32_t H, int32_t W, riann_session_t* out);
+/* Synchronises the device and frees the session.  NULL is a no-op. */
+void riann_session_destroy(riann_session_t s);
+/* Drops the previous field: the next frame is answered by brute force. */
+int riann_session_reset(riann_session_t s);
+int riann_session_info(riann_session_t s, riann_session_info_t* out);
+/* Device bytes a session for H x W frames holds (the admission cost: two
+ * fields, distances, counts and a frame buffer; scratch excluded). */
+int64_t riann_session_state_bytes(riann_index_t idx, int32_t H, int32_t W);
+
+/* One frame from device memory.  The field, distances and counts stay in the
+ * session (riann_session_outputs); the d_out_* pointers (nullable) receive
+ * copies.  Asynchronous on `stream`. */
+int riann_session_frame(riann_session_t s, const riann_params* p, riann_stream_t stream,
+                        const uint8_t* d_frame, int32_t* d_out_annf, uint32_t* d_out_dist,
+                        uint32_t* d_out_count);
+/* One frame from host memory: copies h_frame [H][W][C] to the device, runs
+ * the step and copies the field (and, if not NULL, distances and counts) back
+ * into host buffers.  Asynchronous on `stream` when the host buffers are
+ * pinned; the caller synchronises the stream before reading them. */
+int riann_session_frame_host(riann_session_t s, const riann_params* p, riann_stream_t stream,
+                             const uint8_t* h_frame, int32_t* h_out_annf, uint32_t* h_out_dist,
+                             uint32_t* h_out_count);
+/* Checkpoint: copies the latest field (int32 [H-7][W-7]) to `out` (host or
+ * device); synchronous.  RIANN_ERR_INVALID_ARG when the session holds none. */
+int riann_session_field(riann_session_t s, riann_stream_t stream, int32_t* out);
+/* Resume: makes `field` (host or device, int32 [H-7][W-7]) the previous field
+ * of the next frame; synchronous. */
+int riann_session_restore(riann_session_t s, riann_stream_t stream, const int32_t* field);
+/* Device pointers of the latest field, distances and counts (owned by the
+ * session; valid until its next frame). */
+int riann_session_outputs(riann_session_t s, int32_t** d_annf, uint32_t** d_dist, uint32_t** d_count);
+/* The session's device frame buffer (H x W x C bytes), for callers that
+ * upload frames themselves. */
+uint8_t* riann_session_frame_buffer(riann_session_t s);
+/* Copies the latest field, distances and counts (each nullable; host or
+ * device destinations) on `stream`, asynchronously. */
+int riann_session_copy_outputs(riann_session_t s, riann_stream_t stream, int32_t* annf, uint32_t* dist,
+                               uint32_t* count);
+
+/* ------------------------------------------------------------------------
+ * Batched form: the frames of many sessions (of one index, of any sizes)
+ * answered by one persistent ring-intersection launch whose CTAs take query
+ * tiles of all frames from a device work counter, followed by one brute-force
+ * pass over the union of the queries it routed.  The launch sequence is
+ * captured once as a CUDA graph and replayed every call (unless created with
+ * RIANN_BATCH_NO_GRAPH); frame and field pointers travel in a pinned
+ * descriptor table the graph copies in.  Results are identical to running
+ * each session alone.
+ * ------------------------------------------------------------------------ */
+typedef struct riann_batch_s* riann_batch_t;
+#define RIANN_BATCH_NO_GRAPH 0x1
+
+typedef struct {
+  int32_t max_items;
+  int64_t max_queries;
+  int32_t uses_graph;
+  int64_t runs, graph_builds;
+  size_t device_bytes;
+} riann_batch_info_t;
+
+/* Scratch for up to max_items frames holding max_queries queries in total
+ * (< 2^31).  The context keeps a pointer to idx. */
+int riann_batch_create(riann_index_t idx, int32_t max_items, int64_t max_queries, int32_t flags,
+                       riann_batch_t* out);
+void riann_batch_destroy(riann_batch_t b);
+/* One step for n distinct sessions of the context's index; d_frames[i] is the
+ * device frame of sessions[i].  Asynchronous on `stream`; waits (host side)
+ * for the context's previous step before reusing its descriptor table.
+ * RIANN_ERR_TOO_LARGE when the frames exceed max_queries. */
+int riann_batch_run(riann_batch_t b, const riann_params* p, riann_stream_t stream,
+                    riann_session_t* sessions, const uint8_t* const* d_frames, int32_t n);
+/* Work counters of the context's last step (synchronises `stream`). */
+int riann_batch_stats(riann_batch_t b, riann_stream_t stream, riann_frame_stats_t* out);
+int riann_batch_info(riann_batch_t b, riann_batch_info_t* out);
+
+/* ------------------------------------------------------------------------
+ * Autotuner: times the ring kernel's variants (query tile 4x32 or 8x16;
+ * 1, 2 or 3 code groups tested before compaction) on a sample frame and its
+ * previous field, keeps the fastest in the index, and returns every timing.
+ * The variants compute identical results.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t tile_shape;   /* 0: 4 x 32 queries per CTA, 1: 8 x 16 */
+  int32_t depth;        /* 1..3 */
+  float ms;             /* mean time of one frame (riann_autotune), else -1 */
+} riann_tuning_t;
+
+int riann_autotune(riann_index_t idx, const riann_params* p, riann_stream_t stream,
+                   const uint8_t* d_frame, int32_t H, int32_t W, const int32_t* d_prev_annf,
+                   int32_t iters, riann_tuning_t* results, int32_t max_results, int32_t* n_results);
+int riann_set_tuning(riann_index_t idx, const riann_tuning_t* t);
+int riann_get_tuning(riann_index_t idx, riann_tuning_t* out);
 
 /* Synchronises `stream`, then returns RIANN_OK if the device status word is
  * clear, RIANN_ERR_DEVICE otherwise (and clears it); *bits (nullable) receives

@@ -1,13 +1,17 @@
 // api.cu -- the C ABI of include/riann.h: argument checks, device memory of
-// the index and its scratch, and the launch sequence of one frame.
+// the index, per-call workspaces, the launch sequence of a frame or a batch of
+// frames, per-stream sessions (the previous field kept on the device, Alg. 1
+// line "r_i = ANNF^(t-1)(x, y)"), batch contexts replayed as CUDA graphs, and
+// the ring-kernel autotuner.
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "common.cuh"
 
 namespace riann {
-
 
 int sm_count() {
   static int cached = 0;
@@ -18,10 +22,6 @@ int sm_count() {
     cached = v > 0 ? v : 1;
   }
   return cached;
-}
-
-cudaError_t launch_dense(const DenseArgs& a, Index& ix, cudaStream_t s) {
-  return launch_dense_tc(a, ix, s);
 }
 
 void prof_begin(Index& ix, int slot, cudaStream_t s) {
@@ -51,18 +51,103 @@ cudaError_t dalloc(T** p, size_t count, size_t& total) {
   return e;
 }
 
-void free_scratch(Index& ix) {
-  cudaFree(ix.dense_list);
-  cudaFree(ix.dense_count);
-  cudaFree(ix.best);
-  cudaFree(ix.Aq);
-  cudaFree(ix.qnorm);
-  ix.qnorm = nullptr;
-  ix.dense_list = nullptr;
-  ix.dense_count = nullptr;
-  ix.best = nullptr;
-  ix.Aq = nullptr;
-  ix.scratch_q = 0;
+bool params_ok(const riann_params* p) {
+  return p && p->alpha_den >= 1 && p->alpha_den <= 8 && p->alpha_num >= 0 &&
+         p->alpha_num <= 8 * p->alpha_den && p->ring_limit >= -1 && p->cap >= 0 && p->cap <= 3;
+}
+
+bool frame_ok(int32_t H, int32_t W) {
+  return H >= kPatch && W >= kPatch && (int64_t)(H - 7) * (int64_t)(W - 7) < (int64_t)INT32_MAX &&
+         (int64_t)H * W * 3 < ((int64_t)1 << 40);
+}
+
+FrameItem make_item(const uint8_t* frame, const int32_t* prev, int32_t* out, uint32_t* dist, uint32_t* count,
+                    int H, int W, int shape) {
+  FrameItem it;
+  it.frame = frame;
+  it.prev = prev;
+  it.out_annf = out;
+  it.out_dist = dist;
+  it.out_count = count;
+  it.H = H;
+  it.W = W;
+  it.Hq = H - 7;
+  it.Wq = W - 7;
+  it.tiles_x = (it.Wq + ring_tile_cols(shape) - 1) / ring_tile_cols(shape);
+  it.tile_begin = 0;
+  it.query_begin = 0;
+  return it;
+}
+
+int item_tiles(const FrameItem& it, int shape) {
+  return it.tiles_x * ((it.Hq + ring_tile_rows(shape) - 1) / ring_tile_rows(shape));
+}
+
+SparseArgs sparse_args(const Index& ix, const riann_params* p, Workspace& ws, unsigned long long* stats) {
+  SparseArgs sa;
+  std::memset(&sa, 0, sizeof(sa));
+  sa.R = ix.R;
+  sa.KP = ix.KP;
+  sa.P = ix.P;
+  sa.TA = ix.TA;
+  sa.Tid = ix.Tid;
+  sa.E = ix.E;
+  sa.RB = ix.RB;
+  sa.CW = ix.CW;
+  sa.CWE = ix.CWE;
+  sa.n = ix.n;
+  sa.K = ix.K;
+  sa.Kp = ix.Kp;
+  sa.G = ix.G;
+  sa.GP = ix.GP;
+  sa.nw = ix.nw;
+  sa.alpha_num = p->alpha_num;
+  sa.alpha_den = p->alpha_den;
+  sa.ring_limit = p->ring_limit;
+  sa.depth = p->cap ? p->cap : ix.depth;
+  sa.dense_list = ws.dense_list;
+  sa.counters = ws.counters;
+  sa.status = ix.status;
+  sa.stats = stats;
+  return sa;
+}
+
+DenseArgs dense_args(const Index& ix, unsigned long long* stats) {
+  DenseArgs da;
+  std::memset(&da, 0, sizeof(da));
+  da.R = ix.R;
+  da.n = ix.n;
+  da.stats = stats;
+  return da;
+}
+
+// One frame on a workspace: brute force when there is no previous field,
+// else the ring kernel followed by brute force for the queries it routed.
+cudaError_t run_frame(Index& ix, Workspace& ws, const riann_params* p, cudaStream_t s, const FrameItem& it,
+                      unsigned long long* stats) {
+  cudaError_t e = cudaSuccess;
+  if (stats) e = cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * kStats, s);
+  if (e != cudaSuccess) return e;
+  const int64_t Q = (int64_t)it.Hq * it.Wq;
+  DenseArgs da = dense_args(ix, stats);
+  da.one = it;
+  da.Q = Q;
+  if (!it.prev) {
+    da.list = nullptr;
+    da.list_count = nullptr;
+    return launch_dense_tc(da, ix, ws, s);
+  }
+  e = cudaMemsetAsync(ws.counters, 0, sizeof(uint32_t) * 4, s);
+  if (e != cudaSuccess) return e;
+  SparseArgs sa = sparse_args(ix, p, ws, stats);
+  sa.one = it;
+  prof_begin(ix, kSlotSparse, s);
+  e = launch_sparse(sa, ix.C, ix.tile_shape, s);
+  prof_end(ix, kSlotSparse, s);
+  if (e != cudaSuccess || p->ring_limit < 0) return e;
+  da.list = ws.dense_list;
+  da.list_count = ws.counters;
+  return launch_dense_tc(da, ix, ws, s);
 }
 
 void free_index(Index* ix) {
@@ -83,50 +168,150 @@ void free_index(Index* ix) {
   for (int k = 0; k < kSlots; ++k)
     for (int j = 0; j < 2; ++j)
       if (ix->prof_ev[k][j]) cudaEventDestroy(ix->prof_ev[k][j]);
-  free_scratch(*ix);
+  free_workspace(ix->ws);
   delete ix;
 }
 
-// Grow the index scratch to hold Q queries.  Allocation synchronises the device.
-int ensure_scratch(Index& ix, int64_t Q) {
-  if (ix.scratch_q >= Q) return RIANN_OK;
-  free_scratch(ix);
-  size_t dummy = 0;
+}  // namespace
+
+void free_workspace(Workspace& ws) {
+  cudaFree(ws.dense_list);
+  cudaFree(ws.counters);
+  cudaFree(ws.best);
+  cudaFree(ws.Aq);
+  cudaFree(ws.qnorm);
+  ws.dense_list = nullptr;
+  ws.counters = nullptr;
+  ws.best = nullptr;
+  ws.Aq = nullptr;
+  ws.qnorm = nullptr;
+  ws.cap_q = 0;
+  ws.bytes = 0;
+}
+
+int ensure_workspace(Workspace& ws, const Index& ix, int64_t Q) {
+  if (ws.cap_q >= Q) return RIANN_OK;
+  free_workspace(ws);
   const int64_t Qpad = (Q + kDenseTileM - 1) / kDenseTileM * kDenseTileM;
-  cudaError_t e = dalloc(&ix.dense_list, (size_t)Q, dummy);
-  if (e == cudaSuccess) e = dalloc(&ix.dense_count, 1, dummy);
-  if (e == cudaSuccess) e = dalloc(&ix.best, (size_t)Q, dummy);
-  if (e == cudaSuccess) e = dalloc(&ix.Aq, (size_t)Qpad * ix.D, dummy);
-  if (e == cudaSuccess) e = dalloc(&ix.qnorm, (size_t)Qpad, dummy);
+  size_t& b = ws.bytes;
+  cudaError_t e = dalloc(&ws.dense_list, (size_t)Q, b);
+  if (e == cudaSuccess) e = dalloc(&ws.counters, 4, b);
+  if (e == cudaSuccess) e = dalloc(&ws.best, (size_t)Q, b);
+  if (e == cudaSuccess) e = dalloc(&ws.Aq, (size_t)Qpad * ix.D, b);
+  if (e == cudaSuccess) e = dalloc(&ws.qnorm, (size_t)Qpad, b);
   if (e != cudaSuccess) {
-    free_scratch(ix);
+    free_workspace(ws);
     cudaGetLastError();
     return from_cuda(e);
   }
-  if (!make_row_map(&ix.tmAq, ix.Aq, (uint64_t)Qpad, ix.D, kDenseTileM)) {
-    free_scratch(ix);
+  if (!make_row_map(&ws.tmAq, ws.Aq, (uint64_t)Qpad, ix.D, kDenseTileM)) {
+    free_workspace(ws);
     return RIANN_ERR_UNSUPPORTED;
   }
-  ix.scratch_q = Q;
+  ws.cap_q = Q;
   return RIANN_OK;
 }
 
-bool params_ok(const riann_params* p) {
-  return p && p->alpha_den >= 1 && p->alpha_den <= 8 && p->alpha_num >= 0 &&
-         p->alpha_num <= 8 * p->alpha_den && p->ring_limit >= -1 && p->cap >= 0;
-}
-
-bool frame_ok(int32_t H, int32_t W) {
-  return H >= kPatch && W >= kPatch && (int64_t)(H - 7) * (int64_t)(W - 7) < (int64_t)INT32_MAX &&
-         (int64_t)H * W * 3 < ((int64_t)1 << 40);
-}
-
-}  // namespace
 }  // namespace riann
 
 using namespace riann;
 
 struct riann_index_s : public Index {};
+
+// Per-stream state (a video stream's previous field, kept on the device).
+struct riann_session_s {
+  Index* ix = nullptr;
+  int H = 0, W = 0;
+  int64_t Q = 0;
+  Workspace ws;                  // scratch of riann_session_frame
+  int32_t* field[2] = {nullptr, nullptr};
+  uint32_t* dist = nullptr;
+  uint32_t* count = nullptr;
+  uint8_t* dframe = nullptr;     // device copy of a frame given in host memory
+  int cur = 0;                   // field[cur] holds the latest field
+  bool have_prev = false;
+  int64_t frames = 0;
+  size_t bytes = 0;
+  std::mutex mu;
+};
+
+// A batch context: scratch for the union of its frames, pinned descriptor
+// staging, and the captured graph of one batched step.
+struct riann_batch_s {
+  Index* ix = nullptr;
+  int max_items = 0;
+  int64_t cap_q = 0;
+  bool use_graph = true;
+  Workspace ws;
+  FrameItem* h_items = nullptr;  // pinned [max_items]
+  BatchHeader* h_hdr = nullptr;  // pinned
+  FrameItem* d_items = nullptr;
+  BatchHeader* d_hdr = nullptr;
+  unsigned long long* stats = nullptr;   // [kStats] counters of the last run
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  riann_params gp{};             // parameters baked into the graph
+  int g_shape = -1, g_depth = -1;
+  cudaStream_t cap_stream = nullptr;   // private stream the graph is captured on
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+  int64_t runs = 0, graph_builds = 0;
+  size_t bytes = 0;
+  std::mutex mu;
+};
+
+namespace {
+
+void free_session(riann_session_s* s) {
+  if (!s) return;
+  cudaFree(s->field[0]);
+  cudaFree(s->field[1]);
+  cudaFree(s->dist);
+  cudaFree(s->count);
+  cudaFree(s->dframe);
+  free_workspace(s->ws);
+  delete s;
+}
+
+void free_batch(riann_batch_s* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  cudaFreeHost(b->h_items);
+  cudaFreeHost(b->h_hdr);
+  cudaFree(b->d_items);
+  cudaFree(b->d_hdr);
+  cudaFree(b->stats);
+  free_workspace(b->ws);
+  delete b;
+}
+
+// The launch sequence of one batched step (captured into the graph).
+cudaError_t enqueue_batch(riann_batch_s* b, const riann_params* p, cudaStream_t s) {
+  Index& ix = *b->ix;
+  cudaError_t e = cudaMemcpyAsync(b->d_items, b->h_items, sizeof(FrameItem) * b->max_items,
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_hdr, b->h_hdr, sizeof(BatchHeader), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->ws.counters, 0, sizeof(uint32_t) * 4, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->stats, 0, sizeof(unsigned long long) * kStats, s);
+  if (e != cudaSuccess) return e;
+  SparseArgs sa = sparse_args(ix, p, b->ws, b->stats);
+  sa.items = b->d_items;
+  sa.hdr = b->d_hdr;
+  e = launch_sparse_batch(sa, ix.C, ix.tile_shape, s);
+  if (e != cudaSuccess) return e;
+  DenseArgs da = dense_args(ix, b->stats);
+  da.items = b->d_items;
+  da.hdr = b->d_hdr;
+  da.Q = b->cap_q;
+  da.list = b->ws.dense_list;
+  da.list_count = b->ws.counters;
+  return launch_dense_tc(da, ix, b->ws, s);
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -149,7 +334,7 @@ const char* riann_strerror(int code) {
     case RIANN_ERR_TIMEOUT: return "bounded device wait timed out";
     case RIANN_ERR_ADMISSION: return "admission rejected: budget exceeded";
     case RIANN_ERR_DEVICE: return "kernel reported invalid input (see status bits)";
-    case RIANN_ERR_TOO_LARGE: return "frame has more queries than the fixed scratch of riann_exact_nn_noalloc holds";
+    case RIANN_ERR_TOO_LARGE: return "more queries than the fixed scratch or the batch context holds";
     default: return "unknown error";
   }
 }
@@ -203,19 +388,18 @@ int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t cha
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ix->KP, d_keypoints, (size_t)K * D, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = launch_index_build(*ix, s);
-  if (e == cudaSuccess &&
-      !make_row_map(&ix->tmRbf, ix->Rbf, (uint64_t)ix->n_pad, D, dense_ref_rows_per_tile(channels))) {
-    cudaStreamSynchronize(s);
-    free_index(ix);
-    return RIANN_ERR_UNSUPPORTED;
-  }
-  ix->tm_ready = true;
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaStreamSynchronize(s);
     free_index(ix);
     return from_cuda(e);
   }
+  if (!make_row_map(&ix->tmRbf, ix->Rbf, (uint64_t)ix->n_pad, D, dense_ref_rows_per_tile(channels))) {
+    cudaStreamSynchronize(s);
+    free_index(ix);
+    return RIANN_ERR_UNSUPPORTED;
+  }
+  ix->tm_ready = true;
   *out = ix;
   return RIANN_OK;
 }
@@ -259,102 +443,25 @@ int riann_annf_frame(riann_index_t idx, const riann_params* p, riann_stream_t st
     return RIANN_ERR_INVALID_ARG;
   Index& ix = *idx;
   std::lock_guard<std::mutex> lock(ix.mu);
-  const int Hq = H - 7, Wq = W - 7;
-  const int64_t Q = (int64_t)Hq * Wq;
-  int rc = ensure_scratch(ix, Q);
+  const int64_t Q = (int64_t)(H - 7) * (W - 7);
+  int rc = ensure_workspace(ix.ws, ix, Q);
   if (rc) return rc;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e0 = cudaMemsetAsync(ix.stats, 0, sizeof(unsigned long long) * kStats, s);
-  if (e0 != cudaSuccess) return from_cuda(e0);
-
-  DenseArgs da;
-  da.frame = d_frame;
-  da.H = H;
-  da.W = W;
-  da.Hq = Hq;
-  da.Wq = Wq;
-  da.Q = Q;
-  da.out_annf = d_out_annf;
-  da.out_dist = d_out_dist;
-  da.out_count = d_out_count;
-  da.R = ix.R;
-  da.n = ix.n;
-  da.stats = ix.stats;
-  if (!d_prev_annf) {
-    da.list = nullptr;
-    da.list_count = nullptr;
-    return from_cuda(launch_dense(da, ix, s));
-  }
-  cudaError_t e = cudaMemsetAsync(ix.dense_count, 0, sizeof(uint32_t), s);
-  if (e != cudaSuccess) return from_cuda(e);
-  SparseArgs sa;
-  sa.frame = d_frame;
-  sa.H = H;
-  sa.W = W;
-  sa.Hq = Hq;
-  sa.Wq = Wq;
-  sa.prev = d_prev_annf;
-  sa.out_annf = d_out_annf;
-  sa.out_dist = d_out_dist;
-  sa.out_count = d_out_count;
-  sa.R = ix.R;
-  sa.KP = ix.KP;
-  sa.P = ix.P;
-  sa.TA = ix.TA;
-  sa.Tid = ix.Tid;
-  sa.E = ix.E;
-  sa.RB = ix.RB;
-  sa.CW = ix.CW;
-  sa.CWE = ix.CWE;
-  sa.GP = ix.GP;
-  sa.nw = ix.nw;
-  sa.n = ix.n;
-  sa.K = ix.K;
-  sa.Kp = ix.Kp;
-  sa.G = ix.G;
-  sa.alpha_num = p->alpha_num;
-  sa.alpha_den = p->alpha_den;
-  sa.ring_limit = p->ring_limit;
-  sa.dense_list = ix.dense_list;
-  sa.dense_count = ix.dense_count;
-  sa.status = ix.status;
-  sa.stats = ix.stats;
-  prof_begin(ix, kSlotSparse, s);
-  e = launch_sparse(sa, ix.C, s);
-  prof_end(ix, kSlotSparse, s);
-  if (e != cudaSuccess) return from_cuda(e);
-  if (p->ring_limit >= 0) {
-    da.list = ix.dense_list;
-    da.list_count = ix.dense_count;
-    e = launch_dense(da, ix, s);
-  }
-  return from_cuda(e);
+  const FrameItem it = make_item(d_frame, d_prev_annf, d_out_annf, d_out_dist, d_out_count, H, W, ix.tile_shape);
+  return from_cuda(run_frame(ix, ix.ws, p, reinterpret_cast<cudaStream_t>(stream), it, ix.stats));
 }
 
-int riann_exact_nn(riann_index_t idx, riann_stream_t stream, const uint8_t* d_frame, int32_t H,
-                   int32_t W, int32_t* d_out_annf, uint32_t* d_out_dist) {
+int riann_exact_nn(riann_index_t idx, riann_stream_t stream, const uint8_t* d_frame, int32_t H, int32_t W,
+                   int32_t* d_out_annf, uint32_t* d_out_dist) {
   if (!idx || !d_frame || !d_out_annf || !frame_ok(H, W)) return RIANN_ERR_INVALID_ARG;
   Index& ix = *idx;
   std::lock_guard<std::mutex> lock(ix.mu);
   const int64_t Q = (int64_t)(H - 7) * (W - 7);
-  int rc = ensure_scratch(ix, Q);
+  int rc = ensure_workspace(ix.ws, ix, Q);
   if (rc) return rc;
-  DenseArgs da;
-  da.frame = d_frame;
-  da.H = H;
-  da.W = W;
-  da.Hq = H - 7;
-  da.Wq = W - 7;
+  DenseArgs da = dense_args(ix, nullptr);
+  da.one = make_item(d_frame, nullptr, d_out_annf, d_out_dist, nullptr, H, W, ix.tile_shape);
   da.Q = Q;
-  da.list = nullptr;
-  da.list_count = nullptr;
-  da.out_annf = d_out_annf;
-  da.out_dist = d_out_dist;
-  da.out_count = nullptr;
-  da.R = ix.R;
-  da.n = ix.n;
-  da.stats = nullptr;
-  return from_cuda(launch_dense(da, ix, reinterpret_cast<cudaStream_t>(stream)));
+  return from_cuda(launch_dense_tc(da, ix, ix.ws, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 int riann_frame_stats(riann_index_t idx, riann_stream_t stream, riann_frame_stats_t* out) {
@@ -416,21 +523,9 @@ int riann_exact_nn_noalloc(riann_index_t idx, riann_stream_t stream, const uint8
   if (dev != idx->device) return RIANN_ERR_INVALID_ARG;
   const int64_t Q = (int64_t)(H - 7) * (W - 7);
   if (Q > noalloc_max_queries(idx->C)) return RIANN_ERR_TOO_LARGE;
-  DenseArgs da;
-  da.frame = d_frame;
-  da.H = H;
-  da.W = W;
-  da.Hq = H - 7;
-  da.Wq = W - 7;
+  DenseArgs da = dense_args(*idx, nullptr);
+  da.one = make_item(d_frame, nullptr, d_out_annf, d_out_dist, nullptr, H, W, idx->tile_shape);
   da.Q = Q;
-  da.list = nullptr;
-  da.list_count = nullptr;
-  da.out_annf = d_out_annf;
-  da.out_dist = d_out_dist;
-  da.out_count = nullptr;
-  da.R = idx->R;
-  da.n = idx->n;
-  da.stats = nullptr;
   cudaError_t e = launch_exact_nn_noalloc(da, *idx, reinterpret_cast<cudaStream_t>(stream));
   if (e == cudaErrorInvalidValue) return RIANN_ERR_TOO_LARGE;
   if (e == cudaErrorNotSupported) return RIANN_ERR_UNSUPPORTED;
@@ -447,6 +542,379 @@ int riann_status(riann_index_t idx, riann_stream_t stream, uint32_t* bits) {
   if (bits) *bits = v;
   if (e != cudaSuccess) return from_cuda(e);
   return v ? RIANN_ERR_DEVICE : RIANN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sessions
+// ---------------------------------------------------------------------------
+int riann_session_create(riann_index_t idx, int32_t H, int32_t W, riann_session_t* out) {
+  if (!out) return RIANN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!idx || !frame_ok(H, W)) return RIANN_ERR_INVALID_ARG;
+  riann_session_s* s = new (std::nothrow) riann_session_s();
+  if (!s) return RIANN_ERR_OOM;
+  s->ix = idx;
+  s->H = H;
+  s->W = W;
+  s->Q = (int64_t)(H - 7) * (W - 7);
+  cudaError_t e = dalloc(&s->field[0], (size_t)s->Q, s->bytes);
+  if (e == cudaSuccess) e = dalloc(&s->field[1], (size_t)s->Q, s->bytes);
+  if (e == cudaSuccess) e = dalloc(&s->dist, (size_t)s->Q, s->bytes);
+  if (e == cudaSuccess) e = dalloc(&s->count, (size_t)s->Q, s->bytes);
+  if (e == cudaSuccess) e = dalloc(&s->dframe, (size_t)H * W * idx->C, s->bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_session(s);
+    return from_cuda(e);
+  }
+  *out = s;
+  return RIANN_OK;
+}
+
+void riann_session_destroy(riann_session_t s) {
+  if (!s) return;
+  cudaDeviceSynchronize();
+  free_session(s);
+}
+
+int riann_session_reset(riann_session_t s) {
+  if (!s) return RIANN_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->have_prev = false;
+  return RIANN_OK;
+}
+
+int riann_session_info(riann_session_t s, riann_session_info_t* out) {
+  if (!s || !out) return RIANN_ERR_INVALID_ARG;
+  out->H = s->H;
+  out->W = s->W;
+  out->frames = s->frames;
+  out->has_field = s->have_prev ? 1 : 0;
+  out->device_bytes = s->bytes + s->ws.bytes;
+  return RIANN_OK;
+}
+
+int64_t riann_session_state_bytes(riann_index_t idx, int32_t H, int32_t W) {
+  if (!idx || !frame_ok(H, W)) return 0;
+  const int64_t Q = (int64_t)(H - 7) * (W - 7);
+  return Q * 16 + (int64_t)H * W * idx->C;
+}
+
+int riann_session_frame(riann_session_t s, const riann_params* p, riann_stream_t stream, const uint8_t* d_frame,
+                        int32_t* d_out_annf, uint32_t* d_out_dist, uint32_t* d_out_count) {
+  if (!s || !params_ok(p) || !d_frame) return RIANN_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  Index& ix = *s->ix;
+  int rc = ensure_workspace(s->ws, ix, s->Q);
+  if (rc) return rc;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const int nxt = s->cur ^ 1;
+  const FrameItem it = make_item(d_frame, s->have_prev ? s->field[s->cur] : nullptr, s->field[nxt], s->dist,
+                                 s->count, s->H, s->W, ix.tile_shape);
+  cudaError_t e = run_frame(ix, s->ws, p, cs, it, nullptr);
+  const size_t fb = sizeof(int32_t) * (size_t)s->Q;
+  if (e == cudaSuccess && d_out_annf) e = cudaMemcpyAsync(d_out_annf, s->field[nxt], fb, cudaMemcpyDeviceToDevice, cs);
+  if (e == cudaSuccess && d_out_dist) e = cudaMemcpyAsync(d_out_dist, s->dist, fb, cudaMemcpyDeviceToDevice, cs);
+  if (e == cudaSuccess && d_out_count) e = cudaMemcpyAsync(d_out_count, s->count, fb, cudaMemcpyDeviceToDevice, cs);
+  if (e != cudaSuccess) return from_cuda(e);
+  s->cur = nxt;
+  s->have_prev = true;
+  ++s->frames;
+  return RIANN_OK;
+}
+
+int riann_session_frame_host(riann_session_t s, const riann_params* p, riann_stream_t stream, const uint8_t* h_frame,
+                             int32_t* h_out_annf, uint32_t* h_out_dist, uint32_t* h_out_count) {
+  if (!s || !params_ok(p) || !h_frame || !h_out_annf) return RIANN_ERR_INVALID_ARG;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(s->dframe, h_frame, (size_t)s->H * s->W * s->ix->C, cudaMemcpyHostToDevice, cs);
+  if (e != cudaSuccess) return from_cuda(e);
+  int rc = riann_session_frame(s, p, stream, s->dframe, nullptr, nullptr, nullptr);
+  if (rc) return rc;
+  const size_t fb = sizeof(int32_t) * (size_t)s->Q;
+  e = cudaMemcpyAsync(h_out_annf, s->field[s->cur], fb, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess && h_out_dist) e = cudaMemcpyAsync(h_out_dist, s->dist, fb, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess && h_out_count) e = cudaMemcpyAsync(h_out_count, s->count, fb, cudaMemcpyDeviceToHost, cs);
+  return from_cuda(e);
+}
+
+int riann_session_field(riann_session_t s, riann_stream_t stream, int32_t* out) {
+  if (!s || !out) return RIANN_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (!s->have_prev) return RIANN_ERR_INVALID_ARG;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(out, s->field[s->cur], sizeof(int32_t) * (size_t)s->Q, cudaMemcpyDefault, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  return from_cuda(e);
+}
+
+int riann_session_restore(riann_session_t s, riann_stream_t stream, const int32_t* field) {
+  if (!s || !field) return RIANN_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(s->field[s->cur], field, sizeof(int32_t) * (size_t)s->Q, cudaMemcpyDefault, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  if (e != cudaSuccess) return from_cuda(e);
+  s->have_prev = true;
+  return RIANN_OK;
+}
+
+int riann_session_outputs(riann_session_t s, int32_t** d_annf, uint32_t** d_dist, uint32_t** d_count) {
+  if (!s) return RIANN_ERR_INVALID_ARG;
+  if (d_annf) *d_annf = s->field[s->cur];
+  if (d_dist) *d_dist = s->dist;
+  if (d_count) *d_count = s->count;
+  return RIANN_OK;
+}
+
+uint8_t* riann_session_frame_buffer(riann_session_t s) { return s ? s->dframe : nullptr; }
+
+int riann_session_copy_outputs(riann_session_t s, riann_stream_t stream, int32_t* annf, uint32_t* dist,
+                               uint32_t* count) {
+  if (!s) return RIANN_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(s->mu);
+  if (!s->have_prev) return RIANN_ERR_INVALID_ARG;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const size_t fb = sizeof(int32_t) * (size_t)s->Q;
+  cudaError_t e = cudaSuccess;
+  if (annf) e = cudaMemcpyAsync(annf, s->field[s->cur], fb, cudaMemcpyDefault, cs);
+  if (e == cudaSuccess && dist) e = cudaMemcpyAsync(dist, s->dist, fb, cudaMemcpyDefault, cs);
+  if (e == cudaSuccess && count) e = cudaMemcpyAsync(count, s->count, fb, cudaMemcpyDefault, cs);
+  return from_cuda(e);
+}
+
+// ---------------------------------------------------------------------------
+// batch contexts
+// ---------------------------------------------------------------------------
+int riann_batch_create(riann_index_t idx, int32_t max_items, int64_t max_queries, int32_t flags,
+                       riann_batch_t* out) {
+  if (!out) return RIANN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!idx || max_items < 1 || max_items > 4096 || max_queries < 1 || max_queries >= INT32_MAX)
+    return RIANN_ERR_INVALID_ARG;
+  riann_batch_s* b = new (std::nothrow) riann_batch_s();
+  if (!b) return RIANN_ERR_OOM;
+  b->ix = idx;
+  b->max_items = max_items;
+  b->cap_q = max_queries;
+  b->use_graph = (flags & RIANN_BATCH_NO_GRAPH) == 0;
+  int rc = ensure_workspace(b->ws, *idx, max_queries);
+  cudaError_t e = rc ? cudaErrorMemoryAllocation : cudaSuccess;
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_items, sizeof(FrameItem) * max_items);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_hdr, sizeof(BatchHeader));
+  if (e == cudaSuccess) e = dalloc(&b->d_items, (size_t)max_items, b->bytes);
+  if (e == cudaSuccess) e = dalloc(&b->d_hdr, 1, b->bytes);
+  if (e == cudaSuccess) e = dalloc(&b->stats, kStats, b->bytes);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e == cudaSuccess && b->use_graph) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    free_batch(b);
+    return rc ? rc : from_cuda(e);
+  }
+  std::memset(b->h_items, 0, sizeof(FrameItem) * max_items);
+  *out = b;
+  return RIANN_OK;
+}
+
+void riann_batch_destroy(riann_batch_t b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  free_batch(b);
+}
+
+int riann_batch_run(riann_batch_t b, const riann_params* p, riann_stream_t stream, riann_session_t* sessions,
+                    const uint8_t* const* d_frames, int32_t n) {
+  if (!b || !params_ok(p) || !sessions || !d_frames || n < 1 || n > b->max_items) return RIANN_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(b->mu);
+  Index& ix = *b->ix;
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  for (int i = 0; i < n; ++i) {
+    if (!sessions[i] || sessions[i]->ix != b->ix || !d_frames[i]) return RIANN_ERR_INVALID_ARG;
+    for (int j = 0; j < i; ++j)
+      if (sessions[j] == sessions[i]) return RIANN_ERR_INVALID_ARG;
+  }
+  // the previous step's graph has read the staging buffer once its event passed
+  if (b->pending) {
+    cudaError_t e = cudaEventSynchronize(b->done);
+    if (e != cudaSuccess) return from_cuda(e);
+    b->pending = false;
+  }
+  int tiles = 0;
+  int64_t queries = 0;
+  for (int i = 0; i < n; ++i) queries += sessions[i]->Q;
+  if (queries > b->cap_q) return RIANN_ERR_TOO_LARGE;
+  queries = 0;
+  for (int i = 0; i < n; ++i) {
+    riann_session_s* s = sessions[i];
+    FrameItem it = make_item(d_frames[i], s->have_prev ? s->field[s->cur] : nullptr, s->field[s->cur ^ 1], s->dist,
+                             s->count, s->H, s->W, ix.tile_shape);
+    it.tile_begin = tiles;
+    it.query_begin = queries;
+    tiles += item_tiles(it, ix.tile_shape);
+    queries += s->Q;
+    b->h_items[i] = it;
+  }
+  b->h_hdr->n_items = n;
+  b->h_hdr->total_tiles = tiles;
+  b->h_hdr->total_queries = queries;
+  cudaError_t e = cudaSuccess;
+  if (b->use_graph) {
+    const bool stale = !b->exec || b->gp.alpha_num != p->alpha_num || b->gp.alpha_den != p->alpha_den ||
+                       b->gp.ring_limit != p->ring_limit || b->gp.cap != p->cap || b->g_shape != ix.tile_shape ||
+                       b->g_depth != ix.depth;
+    if (stale) {
+      if (b->exec) cudaGraphExecDestroy(b->exec);
+      if (b->graph) cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+      const bool saved_prof = ix.profile;
+      ix.profile = false;   // no profiler events inside the graph
+      // capture on the context's own stream (the caller's may be the legacy
+      // default stream, which cannot be captured); the graph runs on `cs`
+      e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const cudaError_t e2 = enqueue_batch(b, p, b->cap_stream);
+        e = cudaStreamEndCapture(b->cap_stream, &b->graph);
+        if (e == cudaSuccess) e = e2;
+      }
+      ix.profile = saved_prof;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return from_cuda(e);
+      }
+      b->gp = *p;
+      b->g_shape = ix.tile_shape;
+      b->g_depth = ix.depth;
+      ++b->graph_builds;
+    }
+    e = cudaGraphLaunch(b->exec, cs);
+  } else {
+    const bool saved_prof = ix.profile;
+    ix.profile = false;
+    e = enqueue_batch(b, p, cs);
+    ix.profile = saved_prof;
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(b->done, cs);
+  if (e != cudaSuccess) return from_cuda(e);
+  b->pending = true;
+  ++b->runs;
+  for (int i = 0; i < n; ++i) {
+    riann_session_s* s = sessions[i];
+    s->cur ^= 1;
+    s->have_prev = true;
+    ++s->frames;
+  }
+  return RIANN_OK;
+}
+
+int riann_batch_stats(riann_batch_t b, riann_stream_t stream, riann_frame_stats_t* out) {
+  if (!b || !out) return RIANN_ERR_INVALID_ARG;
+  unsigned long long v[kStats];
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(v, b->stats, sizeof(v), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return from_cuda(e);
+  out->ring_queries = v[kStatRingQueries];
+  out->dense_queries = v[kStatDenseQueries];
+  out->sum_seed = v[kStatSumSeed];
+  out->sum_candidates = v[kStatSumS];
+  return RIANN_OK;
+}
+
+int riann_batch_info(riann_batch_t b, riann_batch_info_t* out) {
+  if (!b || !out) return RIANN_ERR_INVALID_ARG;
+  out->max_items = b->max_items;
+  out->max_queries = b->cap_q;
+  out->uses_graph = b->use_graph ? 1 : 0;
+  out->runs = b->runs;
+  out->graph_builds = b->graph_builds;
+  out->device_bytes = b->bytes + b->ws.bytes;
+  return RIANN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+int riann_set_tuning(riann_index_t idx, const riann_tuning_t* t) {
+  if (!idx || !t || t->tile_shape < 0 || t->tile_shape >= kTileShapes || t->depth < 1 || t->depth > 3)
+    return RIANN_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(idx->mu);
+  idx->tile_shape = t->tile_shape;
+  idx->depth = t->depth;
+  return RIANN_OK;
+}
+
+int riann_get_tuning(riann_index_t idx, riann_tuning_t* out) {
+  if (!idx || !out) return RIANN_ERR_INVALID_ARG;
+  out->tile_shape = idx->tile_shape;
+  out->depth = idx->depth;
+  out->ms = -1.f;
+  return RIANN_OK;
+}
+
+int riann_autotune(riann_index_t idx, const riann_params* p, riann_stream_t stream, const uint8_t* d_frame,
+                   int32_t H, int32_t W, const int32_t* d_prev_annf, int32_t iters, riann_tuning_t* results,
+                   int32_t max_results, int32_t* n_results) {
+  if (!idx || !params_ok(p) || !d_frame || !d_prev_annf || !frame_ok(H, W) || iters < 1) return RIANN_ERR_INVALID_ARG;
+  Index& ix = *idx;
+  std::lock_guard<std::mutex> lock(ix.mu);
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t Q = (int64_t)(H - 7) * (W - 7);
+  int rc = ensure_workspace(ix.ws, ix, Q);
+  if (rc) return rc;
+  int32_t* out = nullptr;
+  size_t dummy = 0;
+  cudaError_t e = dalloc(&out, (size_t)Q, dummy);
+  if (e != cudaSuccess) return from_cuda(e);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  riann_params q = *p;
+  q.cap = 0;
+  std::vector<riann_tuning_t> all;
+  const bool saved_prof = ix.profile;
+  ix.profile = false;
+  const int saved_shape = ix.tile_shape, saved_depth = ix.depth;
+  for (int shape = 0; shape < kTileShapes && e == cudaSuccess; ++shape) {
+    for (int depth = 1; depth <= 3 && e == cudaSuccess; ++depth) {
+      ix.tile_shape = shape;
+      ix.depth = depth;
+      const FrameItem it = make_item(d_frame, d_prev_annf, out, nullptr, nullptr, H, W, shape);
+      e = run_frame(ix, ix.ws, &q, cs, it, nullptr);   // warm-up
+      if (e == cudaSuccess) e = cudaEventRecord(e0, cs);
+      for (int k = 0; k < iters && e == cudaSuccess; ++k) e = run_frame(ix, ix.ws, &q, cs, it, nullptr);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, cs);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      riann_tuning_t t;
+      t.tile_shape = shape;
+      t.depth = depth;
+      t.ms = ms / (float)iters;
+      all.push_back(t);
+    }
+  }
+  ix.profile = saved_prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(out);
+  if (e != cudaSuccess || all.empty()) {
+    ix.tile_shape = saved_shape;
+    ix.depth = saved_depth;
+    return from_cuda(e);
+  }
+  const riann_tuning_t best = *std::min_element(all.begin(), all.end(), [](const riann_tuning_t& a,
+                                                                             const riann_tuning_t& b) {
+    return a.ms < b.ms;
+  });
+  ix.tile_shape = best.tile_shape;
+  ix.depth = best.depth;
+  if (results)
+    for (int i = 0; i < (int)all.size() && i < max_results; ++i) results[i] = all[i];
+  if (n_results) *n_results = (int32_t)all.size();
+  return RIANN_OK;
 }
 
 }  // extern "C"

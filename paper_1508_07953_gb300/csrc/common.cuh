@@ -20,14 +20,52 @@ constexpr int kDenseTileN = 256;   // reference rows per tensor-core tile
 constexpr int kDenseTileM = 128;   // query rows per tensor-core tile
 constexpr int kBuckets = 256;      // quantile buckets per key point (8-bit codes)
 
-// Work counters of the last frame (riann_frame_stats).
+// Work counters of the last frame or batch (riann_frame_stats).
 enum StatSlot { kStatRingQueries = 0, kStatDenseQueries, kStatSumSeed, kStatSumS, kStats = 8 };
 
 // Kernel slots of the per-kernel event profiler (riann_profile_*).
 enum KernelSlot { kSlotSparse = 0, kSlotDense = 1, kSlotPrep = 2, kSlots = 4 };
 
+// Ring-kernel variants the autotuner chooses between: query tile shape.
+enum TileShape { kTile4x32 = 0, kTile8x16 = 1, kTileShapes = 2 };
+
 // Largest possible squared distance between two patches of `dim` bytes.
 __host__ __device__ constexpr uint32_t max_sqdist(int dim) { return (uint32_t)dim * 255u * 255u; }
+
+// One frame of a launch: its pixels, its previous field (nullptr: every query
+// is answered by brute force, Alg. 1 "Initialize"), its outputs, and its place
+// in the launch's tile and query numbering (a single-frame launch has one item
+// with both offsets 0).  Global query id = query_begin + y * Wq + x.
+struct FrameItem {
+  const uint8_t* frame;
+  const int32_t* prev;
+  int32_t* out_annf;
+  uint32_t* out_dist;     // nullable
+  uint32_t* out_count;    // nullable
+  int32_t H, W, Hq, Wq;
+  int32_t tiles_x;        // ring-kernel tiles per row of queries
+  int32_t tile_begin;     // first tile of this item in the launch
+  int64_t query_begin;    // first global query id of this item
+};
+
+// Device header of a batched launch.
+struct BatchHeader {
+  int32_t n_items;
+  int32_t total_tiles;
+  int64_t total_queries;
+};
+
+// Scratch of one launch in flight (one frame or one batch).
+struct Workspace {
+  int64_t cap_q = 0;                    // queries it can hold
+  int32_t* dense_list = nullptr;        // [cap_q] global query ids routed to brute force
+  uint32_t* counters = nullptr;         // [4]: 0 brute-force list length, 1 tile counter
+  unsigned long long* best = nullptr;   // [cap_q] packed (dist << 32 | index)
+  __nv_bfloat16* Aq = nullptr;          // [cap_q padded to 128][D] bf16 query rows
+  uint32_t* qnorm = nullptr;            // [cap_q padded] ||q||^2
+  CUtensorMap tmAq;                     // Aq rows, box 64 x 128
+  size_t bytes = 0;
+};
 
 // Device-resident index (Sec. 3.3 pre-processing restricted to K key points).
 struct Index {
@@ -57,34 +95,28 @@ struct Index {
   unsigned long long* stats = nullptr;  // [kStats] counters of the last frame
   size_t device_bytes = 0;
 
+  // ring-kernel tuning (riann_autotune sets them; these are the defaults)
+  int tile_shape = kTile4x32;
+  int depth = 3;                  // stage-1 filter depth (groups tested before compaction)
+
   // optional per-kernel timing with CUDA events recorded on the launch stream
   bool profile = false;
   bool prof_recorded[kSlots] = {};
   cudaEvent_t prof_ev[kSlots][2] = {};
 
-  // scratch for riann_annf_frame / riann_exact_nn, sized in queries
-  std::mutex mu;
-  int64_t scratch_q = 0;
-  int32_t* dense_list = nullptr;  // [scratch_q] queries routed to brute force
-  uint32_t* dense_count = nullptr;
-  unsigned long long* best = nullptr;   // [scratch_q] packed (dist << 32 | index)
-  __nv_bfloat16* Aq = nullptr;    // [scratch_q padded to 128][D] bf16 query rows
-  uint32_t* qnorm = nullptr;      // [scratch_q padded] ||q||^2
+  std::mutex mu;                  // guards ws and the profiler
+  Workspace ws;                   // scratch of riann_annf_frame / riann_exact_nn
 
-  // TMA descriptors of the brute-force operands
+  // TMA descriptor of the brute-force B operand
   CUtensorMap tmRbf;              // Rbf rows, box 64 x (reference rows per tile)
-  CUtensorMap tmAq;               // Aq rows, box 64 x 128
-  bool tm_ready = false;          // both maps encoded
+  bool tm_ready = false;
 };
 
-// Arguments of the fused sparse query kernel (a1-a4).
+// Arguments of the fused ring-intersection kernel (a1-a4).
 struct SparseArgs {
-  const uint8_t* frame;
-  int H, W, Hq, Wq;
-  const int32_t* prev;
-  int32_t* out_annf;
-  uint32_t* out_dist;
-  uint32_t* out_count;
+  FrameItem one;                  // the frame of a single-frame launch
+  const FrameItem* items;         // batched launch: device item array
+  const BatchHeader* hdr;         // batched launch: device header
   const uint8_t* R;
   const uint8_t* KP;
   const uint32_t* P;
@@ -96,22 +128,21 @@ struct SparseArgs {
   const uint32_t* CWE;
   int n, K, Kp, G, GP, nw;
   int alpha_num, alpha_den, ring_limit;
+  int depth;                      // stage-1 filter depth (1..3)
   int32_t* dense_list;
-  uint32_t* dense_count;
+  uint32_t* counters;             // [0] brute-force list length, [1] tile counter
   uint32_t* status;
   unsigned long long* stats;      // nullable
 };
 
 // Arguments of the brute-force path (a5).
 struct DenseArgs {
-  const uint8_t* frame;
-  int H, W, Hq, Wq;
-  int64_t Q;                      // queries in the frame
-  const int32_t* list;            // nullptr: all queries in order
-  const uint32_t* list_count;     // device count of `list` (nullptr: Q)
-  int32_t* out_annf;
-  uint32_t* out_dist;
-  uint32_t* out_count;
+  FrameItem one;                  // single frame (items == nullptr)
+  const FrameItem* items;         // batched launch: device item array
+  const BatchHeader* hdr;
+  int64_t Q;                      // queries of the single frame, or the list capacity
+  const int32_t* list;            // nullptr: every query of `one` in order
+  const uint32_t* list_count;     // device count of `list`
   const uint8_t* R;
   int n;
   unsigned long long* stats;      // nullable; a whole-frame launch records Q brute-force queries
@@ -124,14 +155,21 @@ void prof_end(Index& ix, int slot, cudaStream_t s);
 // 2-D SWIZZLE_128B tensor map over bf16 rows of D elements.
 bool make_row_map(CUtensorMap* m, const void* base, uint64_t rows, int D, int box_rows);
 int dense_ref_rows_per_tile(int C);
-cudaError_t launch_dense_tc(const DenseArgs& a, Index& ix, cudaStream_t s);
+cudaError_t launch_dense_tc(const DenseArgs& a, Index& ix, Workspace& ws, cudaStream_t s);
 int64_t noalloc_max_queries(int C);
 cudaError_t launch_exact_nn_noalloc(const DenseArgs& a, Index& ix, cudaStream_t s);
 
-// launchers (return cudaGetLastError())
+// ring kernel: one frame (grid = its tiles), or a persistent batched launch
+int ring_tile_rows(int shape);
+int ring_tile_cols(int shape);
+cudaError_t launch_sparse(const SparseArgs& a, int C, int shape, cudaStream_t s);
+cudaError_t launch_sparse_batch(const SparseArgs& a, int C, int shape, cudaStream_t s);
+
 cudaError_t launch_index_build(Index& ix, cudaStream_t s);
-cudaError_t launch_sparse(const SparseArgs& a, int C, cudaStream_t s);
-cudaError_t launch_dense(const DenseArgs& a, Index& ix, cudaStream_t s);
+
+// Workspace management (allocation synchronises the device).
+int ensure_workspace(Workspace& ws, const Index& ix, int64_t Q);
+void free_workspace(Workspace& ws);
 
 int sm_count();
 

@@ -394,8 +394,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
 // query rows in, results out
 // ---------------------------------------------------------------------------
 struct PrepArgs {
-  const uint8_t* frame;
-  int W, Wq;
+  FrameItem one;                  // single frame (items == nullptr)
+  const FrameItem* items;         // batched launch
+  const BatchHeader* hdr;
   int64_t Q;
   const int32_t* list;
   const uint32_t* list_count;
@@ -404,6 +405,16 @@ struct PrepArgs {
   unsigned long long* best;
 };
 
+// The item holding global query id gid (items sorted by query_begin).
+__device__ __forceinline__ const FrameItem& item_of(const FrameItem* items, const BatchHeader* hdr, int64_t gid) {
+  int lo = 0, hi = hdr->n_items - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (items[mid].query_begin <= gid) lo = mid; else hi = mid - 1;
+  }
+  return items[lo];
+}
+
 // Row i of Aq = bf16 bytes of the i-th query patch ((dy, dx, c) order), its
 // squared norm, and a reset best slot.  One thread per query.
 template <int C>
@@ -411,14 +422,16 @@ __global__ void k_dense_prep(PrepArgs a) {
   constexpr int NW = 16 * C;
   const int64_t nq = a.list ? (int64_t)*a.list_count : a.Q;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t qi = a.list ? (int64_t)a.list[i] : i;
-    const int y = (int)(qi / a.Wq), x = (int)(qi % a.Wq);
+    const int64_t gid = a.list ? (int64_t)a.list[i] : i;
+    const FrameItem& it = a.items ? item_of(a.items, a.hdr, gid) : a.one;
+    const int64_t qi = gid - it.query_begin;
+    const int y = (int)(qi / it.Wq), x = (int)(qi % it.Wq);
     uint2* dst = reinterpret_cast<uint2*>(a.Aq + i * (64 * C));
     uint32_t nrm = 0;
 #pragma unroll 4
     for (int w = 0; w < NW; ++w) {
       const int dy = w / (2 * C), j = w % (2 * C);
-      const uint8_t* p = a.frame + ((int64_t)(y + dy) * a.W + x) * C + 4 * j;
+      const uint8_t* p = it.frame + ((int64_t)(y + dy) * it.W + x) * C + 4 * j;
       const uint32_t b0 = p[0], b1 = p[1], b2 = p[2], b3 = p[3];
       nrm += b0 * b0 + b1 * b1 + b2 * b2 + b3 * b3;
       // bf16 of an integer 0..255: exact; pack two per 32-bit word
@@ -434,13 +447,13 @@ __global__ void k_dense_prep(PrepArgs a) {
 }
 
 struct FinishArgs {
+  FrameItem one;
+  const FrameItem* items;
+  const BatchHeader* hdr;
   const int32_t* list;
   const uint32_t* list_count;
   int64_t Q;
   const unsigned long long* best;
-  int32_t* out_annf;
-  uint32_t* out_dist;
-  uint32_t* out_count;
   int n;
   unsigned long long* stats;
 };
@@ -449,11 +462,13 @@ __global__ void k_dense_finish(FinishArgs a) {
   const int64_t nq = a.list ? (int64_t)*a.list_count : a.Q;
   if (!a.list && a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[kStatDenseQueries] = (unsigned long long)nq;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t qi = a.list ? (int64_t)a.list[i] : i;
+    const int64_t gid = a.list ? (int64_t)a.list[i] : i;
+    const FrameItem& it = a.items ? item_of(a.items, a.hdr, gid) : a.one;
+    const int64_t qi = gid - it.query_begin;
     const unsigned long long k = a.best[i];
-    a.out_annf[qi] = (int32_t)(k & 0xffffffffu);
-    if (a.out_dist) a.out_dist[qi] = (uint32_t)(k >> 32);
-    if (a.out_count) a.out_count[qi] = (uint32_t)a.n;
+    it.out_annf[qi] = (int32_t)(k & 0xffffffffu);
+    if (it.out_dist) it.out_dist[qi] = (uint32_t)(k >> 32);
+    if (it.out_count) it.out_count[qi] = (uint32_t)a.n;
   }
 }
 
@@ -489,19 +504,19 @@ bool make_row_map(CUtensorMap* m, const void* base, uint64_t rows, int D, int bo
 
 int dense_ref_rows_per_tile(int C) { return C == 1 ? Cfg<1>::BN : Cfg<3>::BN; }
 
-cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, cudaStream_t s) {
+cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, Workspace& ws, cudaStream_t s) {
   if (!ix.tm_ready) return cudaErrorNotSupported;
   const int C = ix.C;
   PrepArgs p;
-  p.frame = d.frame;
-  p.W = d.W;
-  p.Wq = d.Wq;
+  p.one = d.one;
+  p.items = d.items;
+  p.hdr = d.hdr;
   p.Q = d.Q;
   p.list = d.list;
   p.list_count = d.list_count;
-  p.Aq = ix.Aq;
-  p.qnorm = ix.qnorm;
-  p.best = ix.best;
+  p.Aq = ws.Aq;
+  p.qnorm = ws.qnorm;
+  p.best = ws.best;
   int64_t blocks = (d.Q + 255) / 256;
   const int64_t cap = (int64_t)sm_count() * 16;
   if (blocks > cap) blocks = cap;
@@ -512,14 +527,14 @@ cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, cudaStream_t s) {
   prof_end(ix, kSlotPrep, s);
 
   TcArgs t;
-  t.tmA = ix.tmAq;
+  t.tmA = ws.tmAq;
   t.tmB = ix.tmRbf;
   t.rnorm = ix.rnorm;
-  t.qnorm = ix.qnorm;
+  t.qnorm = ws.qnorm;
   t.count = d.list ? d.list_count : nullptr;
   t.Qfix = d.Q;
   t.n_pad = ix.n_pad;
-  t.best = ix.best;
+  t.best = ws.best;
   t.status = ix.status;
   const int grid = sm_count();
   prof_begin(ix, kSlotDense, s);
@@ -541,13 +556,13 @@ cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, cudaStream_t s) {
   prof_end(ix, kSlotDense, s);
 
   FinishArgs f;
+  f.one = d.one;
+  f.items = d.items;
+  f.hdr = d.hdr;
   f.list = d.list;
   f.list_count = d.list_count;
   f.Q = d.Q;
-  f.best = ix.best;
-  f.out_annf = d.out_annf;
-  f.out_dist = d.out_dist;
-  f.out_count = d.out_count;
+  f.best = ws.best;
   f.n = ix.n;
   f.stats = d.stats;
   k_dense_finish<<<(unsigned)blocks, 256, 0, s>>>(f);
@@ -640,9 +655,9 @@ cudaError_t launch_exact_nn_noalloc(const DenseArgs& d, Index& ix, cudaStream_t 
   unsigned long long* best = reinterpret_cast<unsigned long long*>(nd.base + L.best_off);
 
   PrepArgs p;
-  p.frame = d.frame;
-  p.W = d.W;
-  p.Wq = d.Wq;
+  p.one = d.one;
+  p.items = nullptr;
+  p.hdr = nullptr;
   p.Q = d.Q;
   p.list = nullptr;
   p.list_count = nullptr;
@@ -678,13 +693,13 @@ cudaError_t launch_exact_nn_noalloc(const DenseArgs& d, Index& ix, cudaStream_t 
   }
 
   FinishArgs f;
+  f.one = d.one;
+  f.items = nullptr;
+  f.hdr = nullptr;
   f.list = nullptr;
   f.list_count = nullptr;
   f.Q = d.Q;
   f.best = best;
-  f.out_annf = d.out_annf;
-  f.out_dist = d.out_dist;
-  f.out_count = nullptr;
   f.n = ix.n;
   f.stats = nullptr;
   k_dense_finish<<<(unsigned)blocks, 256, 0, s>>>(f);

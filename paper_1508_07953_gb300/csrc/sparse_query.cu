@@ -17,7 +17,6 @@
 namespace riann {
 namespace {
 
-constexpr int TY = 4, TX = 32;
 constexpr int kWarps = 8;
 constexpr unsigned kFull = 0xffffffffu;
 
@@ -190,8 +189,14 @@ __device__ __forceinline__ unsigned long long boundary_bits(uint32_t w, uint32_t
 
 constexpr int kQueue = 256;   // per-warp ring buffer of stage-1 survivors
 
-template <int C>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(SparseArgs a) {
+// One CTA per tile of TY x TX query positions.  Single-frame launch
+// (BATCH = false): the grid is the frame's tiles.  Batched launch: a
+// persistent grid whose CTAs take tiles of all the batch's frames from an
+// atomic counter, in the order of the items.
+template <int C, int SHAPE, bool BATCH>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(const SparseArgs a) {
+  constexpr int TY = SHAPE == kTile4x32 ? 4 : 8;
+  constexpr int TX = SHAPE == kTile4x32 ? 32 : 16;
   constexpr int D = 64 * C, NW = D / 4;
   constexpr int TROW = (TX + 7) * C;              // tile row bytes
   constexpr int TROWP = ((TROW + 8) + 3) & ~3;    // + room for the 8-byte funnel reads
@@ -212,34 +217,56 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(SparseArgs a) {
   __shared__ int32_t s_queue[kWarps][kQueue];     // stage-1 survivors (seed-run positions)
   __shared__ __align__(16) uint32_t s_q[kWarps][NW];   // the warp's query patch
   __shared__ int32_t s_dense[TY * TX];
-  __shared__ int s_next, s_ndense, s_dense_base;
+  __shared__ int s_next, s_ndense, s_dense_base, s_tile_id;
   __shared__ unsigned long long s_stat[3];        // ring-answered queries, scanned entries, sum of |S|
 
   const int K = a.K, n = a.n, G = a.G;
-  const int tiles_x = (a.Wq + TX - 1) / TX;
-  const int ty0 = (blockIdx.x / tiles_x) * TY;
-  const int tx0 = (blockIdx.x % tiles_x) * TX;
-
   {
     const uint32_t* kp = reinterpret_cast<const uint32_t*>(a.KP);
     for (int i = threadIdx.x; i < K * NW; i += blockDim.x) s_kp[(i / NW) * KPW + (i % NW)] = kp[i];
     for (int i = threadIdx.x; i < K * 16; i += blockDim.x) s_coarse[i >> 4][i & 15] = __ldg(a.E + (i >> 4) * kBuckets + 16 * (i & 15));
-    const int64_t rowb = (int64_t)a.W * C;
-    for (int i = threadIdx.x; i < (TY + 7) * TROWP; i += blockDim.x) {
-      const int r = i / TROWP, c = i % TROWP;
-      const int y = ty0 + r;
-      const int64_t xb = (int64_t)tx0 * C + c;
-      s_tile[i] = (c < TROW && y < a.H && xb < rowb) ? a.frame[(int64_t)y * rowb + xb] : (uint8_t)0;
-    }
-    if (threadIdx.x == 0) { s_next = 0; s_ndense = 0; s_stat[0] = s_stat[1] = s_stat[2] = 0; }
   }
-  __syncthreads();
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t p2 = (uint32_t)(a.alpha_num * a.alpha_num);
   const uint32_t q2 = (uint32_t)(a.alpha_den * a.alpha_den);
   const float alpha = (float)a.alpha_num / (float)a.alpha_den;
   const uint32_t Amax = max_sqdist(D);
+
+  for (int round = 0;; ++round) {
+  // ---- the next tile and its frame ----
+  FrameItem it;
+  int tile;
+  if (BATCH) {
+    __syncthreads();   // the previous tile's shared state is no longer read
+    if (threadIdx.x == 0) s_tile_id = (int)atomicAdd(a.counters + 1, 1u);
+    __syncthreads();
+    const int tg = s_tile_id;
+    if (tg >= a.hdr->total_tiles) break;
+    int lo = 0, hi = a.hdr->n_items - 1;   // last item with tile_begin <= tg
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (a.items[mid].tile_begin <= tg) lo = mid; else hi = mid - 1;
+    }
+    it = a.items[lo];
+    tile = tg - it.tile_begin;
+  } else {
+    if (round > 0) break;
+    it = a.one;
+    tile = blockIdx.x;
+  }
+  const int ty0 = (tile / it.tiles_x) * TY;
+  const int tx0 = (tile % it.tiles_x) * TX;
+  {
+    const int64_t rowb = (int64_t)it.W * C;
+    for (int i = threadIdx.x; i < (TY + 7) * TROWP; i += blockDim.x) {
+      const int r = i / TROWP, c = i % TROWP;
+      const int y = ty0 + r;
+      const int64_t xb = (int64_t)tx0 * C + c;
+      s_tile[i] = (c < TROW && y < it.H && xb < rowb) ? it.frame[(int64_t)y * rowb + xb] : (uint8_t)0;
+    }
+    if (threadIdx.x == 0) { s_next = 0; s_ndense = 0; s_stat[0] = s_stat[1] = s_stat[2] = 0; }
+  }
+  __syncthreads();
 
   for (;;) {
     int t = 0;
@@ -248,8 +275,12 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(SparseArgs a) {
     if (t >= TY * TX) break;
     const int ly = t / TX, lx = t % TX;
     const int y = ty0 + ly, x = tx0 + lx;
-    if (y >= a.Hq || x >= a.Wq) continue;
-    const int64_t qi = (int64_t)y * a.Wq + x;
+    if (y >= it.Hq || x >= it.Wq) continue;
+    const int64_t qi = (int64_t)y * it.Wq + x;
+    if (!it.prev) {   // no previous field: brute force (Alg. 1 "Initialize")
+      if (lane == 0) s_dense[atomicAdd(&s_ndense, 1)] = (int32_t)(it.query_begin + qi);
+      continue;
+    }
 
     // a1: the query patch, 4 bytes per word, (dy, dx, c) order, kept in shared
     // memory for the whole query (registers go to the scan)
@@ -265,13 +296,13 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(SparseArgs a) {
     __syncwarp();
 
     // previous match r_p and temporal change C = ||q - r_p||^2 (Alg. 1: r_i, d_i)
-    const int rp = __ldg(a.prev + qi);
+    const int rp = __ldg(it.prev + qi);
     if ((unsigned)rp >= (unsigned)n) {
       if (lane == 0) {
         atomicOr(a.status, RIANN_DEV_BAD_PREV);
-        a.out_annf[qi] = -1;
-        if (a.out_dist) a.out_dist[qi] = 0xffffffffu;
-        if (a.out_count) a.out_count[qi] = 0u;
+        it.out_annf[qi] = -1;
+        if (it.out_dist) it.out_dist[qi] = 0xffffffffu;
+        if (it.out_count) it.out_count[qi] = 0u;
       }
       continue;
     }
@@ -355,7 +386,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(SparseArgs a) {
         }
       }
       if (!found) {
-        if (lane == 0) s_dense[atomicAdd(&s_ndense, 1)] = (int32_t)qi;
+        if (lane == 0) s_dense[atomicAdd(&s_ndense, 1)] = (int32_t)(it.query_begin + qi);
         continue;
       }
     }
@@ -412,7 +443,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(SparseArgs a) {
     uint32_t cnt = 0;
     const uint32_t* cw = a.CW + (int64_t)ms * G * a.nw;
     const int32_t* tid = a.Tid + (int64_t)ms * n;
-    const int ns1 = G < 3 ? G : 3;
+    const int ns1 = G < a.depth ? G : a.depth;
     const int g0 = s_ord[warp][0];
     const int g1 = s_ord[warp][ns1 > 1 ? 1 : 0];
     const int g2 = s_ord[warp][ns1 > 2 ? 2 : 0];
@@ -569,9 +600,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(SparseArgs a) {
       cnt += __shfl_xor_sync(kFull, cnt, o);
     }
     if (lane == 0) {
-      a.out_annf[qi] = (int32_t)(best & 0xffffffffu);
-      if (a.out_dist) a.out_dist[qi] = (uint32_t)(best >> 32);
-      if (a.out_count) a.out_count[qi] = cnt;
+      it.out_annf[qi] = (int32_t)(best & 0xffffffffu);
+      if (it.out_dist) it.out_dist[qi] = (uint32_t)(best >> 32);
+      if (it.out_count) it.out_count[qi] = cnt;
       if (a.stats) {
         atomicAdd(&s_stat[0], 1ull);
         atomicAdd(&s_stat[1], (unsigned long long)(jhi - jlo));
@@ -583,7 +614,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(SparseArgs a) {
 
   // hand the brute-force queries of this tile to the dense path
   __syncthreads();
-  if (threadIdx.x == 0 && s_ndense > 0) s_dense_base = (int)atomicAdd(a.dense_count, (uint32_t)s_ndense);
+  if (threadIdx.x == 0 && s_ndense > 0) s_dense_base = (int)atomicAdd(a.counters, (uint32_t)s_ndense);
   if (threadIdx.x == 0 && a.stats) {
     atomicAdd(&a.stats[kStatRingQueries], s_stat[0]);
     atomicAdd(&a.stats[kStatDenseQueries], (unsigned long long)s_ndense);
@@ -592,15 +623,37 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(SparseArgs a) {
   }
   __syncthreads();
   for (int i = threadIdx.x; i < s_ndense; i += blockDim.x) a.dense_list[s_dense_base + i] = s_dense[i];
+  }   // tiles
+}
+
+template <int C, int SHAPE>
+cudaError_t launch_ring(const SparseArgs& a, bool batch, int grid, cudaStream_t s) {
+  if (batch) k_sparse<C, SHAPE, true><<<grid, kWarps * 32, 0, s>>>(a);
+  else k_sparse<C, SHAPE, false><<<grid, kWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_any(const SparseArgs& a, int C, int shape, bool batch, int grid, cudaStream_t s) {
+  if (C == 1) return shape == kTile8x16 ? launch_ring<1, kTile8x16>(a, batch, grid, s)
+                                        : launch_ring<1, kTile4x32>(a, batch, grid, s);
+  return shape == kTile8x16 ? launch_ring<3, kTile8x16>(a, batch, grid, s)
+                            : launch_ring<3, kTile4x32>(a, batch, grid, s);
 }
 
 }  // namespace
 
-cudaError_t launch_sparse(const SparseArgs& a, int C, cudaStream_t s) {
-  const int tiles = ((a.Hq + TY - 1) / TY) * ((a.Wq + TX - 1) / TX);
-  if (C == 1) k_sparse<1><<<tiles, kWarps * 32, 0, s>>>(a);
-  else k_sparse<3><<<tiles, kWarps * 32, 0, s>>>(a);
-  return cudaGetLastError();
+int ring_tile_rows(int shape) { return shape == kTile8x16 ? 8 : 4; }
+int ring_tile_cols(int shape) { return shape == kTile8x16 ? 16 : 32; }
+
+cudaError_t launch_sparse(const SparseArgs& a, int C, int shape, cudaStream_t s) {
+  const int tiles = a.one.tiles_x * ((a.one.Hq + ring_tile_rows(shape) - 1) / ring_tile_rows(shape));
+  if (tiles <= 0) return cudaSuccess;
+  return launch_any(a, C, shape, false, tiles, s);
+}
+
+// Persistent batched launch: as many CTAs as stay resident (2 per SM).
+cudaError_t launch_sparse_batch(const SparseArgs& a, int C, int shape, cudaStream_t s) {
+  return launch_any(a, C, shape, true, 2 * sm_count(), s);
 }
 
 }  // namespace riann

@@ -58,8 +58,27 @@ class riann_frame_stats_t(ctypes.Structure):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
+class riann_session_info_t(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("frames", ctypes.c_int64),
+                ("has_field", ctypes.c_int32), ("device_bytes", ctypes.c_size_t)]
+
+
+class riann_batch_info_t(ctypes.Structure):
+    _fields_ = [("max_items", ctypes.c_int32), ("max_queries", ctypes.c_int64),
+                ("uses_graph", ctypes.c_int32), ("runs", ctypes.c_int64),
+                ("graph_builds", ctypes.c_int64), ("device_bytes", ctypes.c_size_t)]
+
+
+class riann_tuning_t(ctypes.Structure):
+    _fields_ = [("tile_shape", ctypes.c_int32), ("depth", ctypes.c_int32), ("ms", ctypes.c_float)]
+
+    def as_dict(self):
+        return {"tile_shape": int(self.tile_shape), "depth": int(self.depth), "ms": float(self.ms)}
+
+
 _P = ctypes.c_void_p
 _i32 = ctypes.c_int32
+_i64 = ctypes.c_int64
 _lib.riann_default_params.argtypes = [_i32]
 _lib.riann_default_params.restype = riann_params
 _lib.riann_strerror.argtypes = [ctypes.c_int]
@@ -77,6 +96,31 @@ _lib.riann_profile_read.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_float), _i32
 _lib.riann_exact_nn_noalloc.argtypes = [_P, _P, _P, _i32, _i32, _P, _P]
 _lib.riann_exact_nn_noalloc_max_queries.argtypes = [_i32]
 _lib.riann_exact_nn_noalloc_max_queries.restype = ctypes.c_int64
+_lib.riann_session_create.argtypes = [_P, _i32, _i32, ctypes.POINTER(_P)]
+_lib.riann_session_destroy.argtypes = [_P]
+_lib.riann_session_destroy.restype = None
+_lib.riann_session_reset.argtypes = [_P]
+_lib.riann_session_info.argtypes = [_P, ctypes.POINTER(riann_session_info_t)]
+_lib.riann_session_state_bytes.argtypes = [_P, _i32, _i32]
+_lib.riann_session_state_bytes.restype = _i64
+_lib.riann_session_frame.argtypes = [_P, ctypes.POINTER(riann_params), _P, _P, _P, _P, _P]
+_lib.riann_session_frame_host.argtypes = [_P, ctypes.POINTER(riann_params), _P, _P, _P, _P, _P]
+_lib.riann_session_field.argtypes = [_P, _P, _P]
+_lib.riann_session_restore.argtypes = [_P, _P, _P]
+_lib.riann_session_outputs.argtypes = [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]
+_lib.riann_session_copy_outputs.argtypes = [_P, _P, _P, _P, _P]
+_lib.riann_session_frame_buffer.argtypes = [_P]
+_lib.riann_session_frame_buffer.restype = _P
+_lib.riann_batch_create.argtypes = [_P, _i32, _i64, _i32, ctypes.POINTER(_P)]
+_lib.riann_batch_destroy.argtypes = [_P]
+_lib.riann_batch_destroy.restype = None
+_lib.riann_batch_run.argtypes = [_P, ctypes.POINTER(riann_params), _P, ctypes.POINTER(_P), ctypes.POINTER(_P), _i32]
+_lib.riann_batch_stats.argtypes = [_P, _P, ctypes.POINTER(riann_frame_stats_t)]
+_lib.riann_batch_info.argtypes = [_P, ctypes.POINTER(riann_batch_info_t)]
+_lib.riann_autotune.argtypes = [_P, ctypes.POINTER(riann_params), _P, _P, _i32, _i32, _P, _i32,
+                                ctypes.POINTER(riann_tuning_t), _i32, ctypes.POINTER(_i32)]
+_lib.riann_set_tuning.argtypes = [_P, ctypes.POINTER(riann_tuning_t)]
+_lib.riann_get_tuning.argtypes = [_P, ctypes.POINTER(riann_tuning_t)]
 _lib.riann_status.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_uint32)]
 
 
@@ -282,3 +326,194 @@ def annf(index: RiannIndex, frame: torch.Tensor, prev: Optional[torch.Tensor],
     riann_annf_frame(index, params if params is not None else riann_default_params(index.n),
                      frame, prev, out, dist, cnt, stream)
     return out, dist, cnt
+
+
+# ---------------------------------------------------------------------------
+# sessions (per-stream state)
+# ---------------------------------------------------------------------------
+RIANN_BATCH_NO_GRAPH = 0x1
+
+
+class RiannSession:
+    """Owns a ``riann_session_t``: one video stream's resident previous field."""
+
+    def __init__(self, index: RiannIndex, H: int, W: int):
+        h = ctypes.c_void_p(0)
+        _check(_lib.riann_session_create(index.handle, int(H), int(W), ctypes.byref(h)), "riann_session_create")
+        self.handle = h
+        self.index = index          # keeps the index alive
+        self.H, self.W = int(H), int(W)
+        self.shape = (self.H - 7, self.W - 7)
+
+    def info(self) -> riann_session_info_t:
+        out = riann_session_info_t()
+        _check(_lib.riann_session_info(self.handle, ctypes.byref(out)), "riann_session_info")
+        return out
+
+    def close(self):
+        if self.handle and self.handle.value:
+            _lib.riann_session_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def riann_session_create(index: RiannIndex, H: int, W: int) -> RiannSession:
+    return RiannSession(index, H, W)
+
+
+def riann_session_reset(session: RiannSession) -> None:
+    _check(_lib.riann_session_reset(session.handle), "riann_session_reset")
+
+
+def riann_session_state_bytes(index: RiannIndex, H: int, W: int) -> int:
+    return int(_lib.riann_session_state_bytes(index.handle, int(H), int(W)))
+
+
+def riann_session_frame(session: RiannSession, params: riann_params, frame: torch.Tensor,
+                        out_annf: Optional[torch.Tensor] = None, out_dist: Optional[torch.Tensor] = None,
+                        out_count: Optional[torch.Tensor] = None,
+                        stream: Optional[torch.cuda.Stream] = None) -> None:
+    Q = session.shape[0] * session.shape[1]
+    _frame_dims(frame, session.index.C)
+    _check(_lib.riann_session_frame(session.handle, ctypes.byref(params), _stream(stream),
+                                    _dev(frame, (torch.uint8,), "frame"),
+                                    _dev(out_annf, _I32, "out_annf", Q), _dev(out_dist, _U32, "out_dist", Q),
+                                    _dev(out_count, _U32, "out_count", Q)), "riann_session_frame")
+
+
+def _host(t: Optional[torch.Tensor], dtypes, name: str, numel: int):
+    if t is None:
+        return None
+    if t.is_cuda or t.dtype not in dtypes or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{name} must be a contiguous CPU tensor of {numel} elements in {dtypes}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def riann_session_frame_host(session: RiannSession, params: riann_params, frame: torch.Tensor,
+                             out_annf: torch.Tensor, out_dist: Optional[torch.Tensor] = None,
+                             out_count: Optional[torch.Tensor] = None,
+                             stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Host frame in, host field out (pinned host tensors keep it asynchronous)."""
+    Q = session.shape[0] * session.shape[1]
+    _check(_lib.riann_session_frame_host(session.handle, ctypes.byref(params), _stream(stream),
+                                         _host(frame, (torch.uint8,), "frame", session.H * session.W * session.index.C),
+                                         _host(out_annf, _I32, "out_annf", Q), _host(out_dist, _U32, "out_dist", Q),
+                                         _host(out_count, _U32, "out_count", Q)), "riann_session_frame_host")
+
+
+def riann_session_field(session: RiannSession, out: torch.Tensor, stream=None) -> None:
+    Q = session.shape[0] * session.shape[1]
+    if out.dtype != torch.int32 or not out.is_contiguous() or out.numel() != Q:
+        raise ValueError("out must be a contiguous int32 tensor of the field's size")
+    _check(_lib.riann_session_field(session.handle, _stream(stream), ctypes.c_void_p(out.data_ptr())),
+           "riann_session_field")
+
+
+def riann_session_restore(session: RiannSession, field: torch.Tensor, stream=None) -> None:
+    Q = session.shape[0] * session.shape[1]
+    if field.dtype != torch.int32 or not field.is_contiguous() or field.numel() != Q:
+        raise ValueError("field must be a contiguous int32 tensor of the field's size")
+    _check(_lib.riann_session_restore(session.handle, _stream(stream), ctypes.c_void_p(field.data_ptr())),
+           "riann_session_restore")
+
+
+def riann_session_outputs(session: RiannSession):
+    """(annf, dist, count) device pointers of the latest frame, as ints."""
+    a, d, c = ctypes.c_void_p(0), ctypes.c_void_p(0), ctypes.c_void_p(0)
+    _check(_lib.riann_session_outputs(session.handle, ctypes.byref(a), ctypes.byref(d), ctypes.byref(c)),
+           "riann_session_outputs")
+    return a.value, d.value, c.value
+
+
+def session_result(session: RiannSession, stream=None):
+    """Copies of the latest (annf, dist, count) as int32 CUDA tensors."""
+    outs = [torch.empty(session.shape, dtype=torch.int32, device="cuda") for _ in range(3)]
+    _check(_lib.riann_session_copy_outputs(session.handle, _stream(stream),
+                                           *[ctypes.c_void_p(t.data_ptr()) for t in outs]),
+           "riann_session_copy_outputs")
+    return tuple(outs)
+
+
+# ---------------------------------------------------------------------------
+# batched form
+# ---------------------------------------------------------------------------
+class RiannBatch:
+    def __init__(self, index: RiannIndex, max_items: int, max_queries: int, use_graph: bool = True):
+        h = ctypes.c_void_p(0)
+        flags = 0 if use_graph else RIANN_BATCH_NO_GRAPH
+        _check(_lib.riann_batch_create(index.handle, int(max_items), int(max_queries), flags, ctypes.byref(h)),
+               "riann_batch_create")
+        self.handle = h
+        self.index = index
+        self.max_items = int(max_items)
+
+    def info(self) -> riann_batch_info_t:
+        out = riann_batch_info_t()
+        _check(_lib.riann_batch_info(self.handle, ctypes.byref(out)), "riann_batch_info")
+        return out
+
+    def close(self):
+        if self.handle and self.handle.value:
+            _lib.riann_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def riann_batch_create(index: RiannIndex, max_items: int, max_queries: int, use_graph: bool = True) -> RiannBatch:
+    return RiannBatch(index, max_items, max_queries, use_graph)
+
+
+def riann_batch_run(batch: RiannBatch, params: riann_params, sessions, frames, stream=None) -> None:
+    """One batched step: frames[i] (CUDA uint8 tensor) is the next frame of sessions[i]."""
+    n = len(sessions)
+    if n != len(frames):
+        raise ValueError("one frame per session")
+    hs = (ctypes.c_void_p * n)(*[s.handle.value for s in sessions])
+    fs = (ctypes.c_void_p * n)(*[_dev(f, (torch.uint8,), "frame").value for f in frames])
+    for s, f in zip(sessions, frames):
+        if _frame_dims(f, s.index.C) != (s.H, s.W):
+            raise ValueError("frame size differs from its session's")
+    _check(_lib.riann_batch_run(batch.handle, ctypes.byref(params), _stream(stream), hs, fs, n), "riann_batch_run")
+
+
+def riann_batch_stats(batch: RiannBatch, stream=None) -> dict:
+    out = riann_frame_stats_t()
+    _check(_lib.riann_batch_stats(batch.handle, _stream(stream), ctypes.byref(out)), "riann_batch_stats")
+    return out.as_dict()
+
+
+# ---------------------------------------------------------------------------
+# autotuner
+# ---------------------------------------------------------------------------
+def riann_autotune(index: RiannIndex, params: riann_params, frame: torch.Tensor, prev_annf: torch.Tensor,
+                   iters: int = 3, stream=None):
+    """Times every ring-kernel variant on one frame; keeps the fastest. Returns all timings."""
+    H, W = _frame_dims(frame, index.C)
+    res = (riann_tuning_t * 16)()
+    nres = ctypes.c_int32(0)
+    _check(_lib.riann_autotune(index.handle, ctypes.byref(params), _stream(stream),
+                               _dev(frame, (torch.uint8,), "frame"), H, W,
+                               _dev(prev_annf, _I32, "prev_annf", (H - 7) * (W - 7)), int(iters),
+                               res, 16, ctypes.byref(nres)), "riann_autotune")
+    return [res[i].as_dict() for i in range(nres.value)]
+
+
+def riann_set_tuning(index: RiannIndex, tile_shape: int, depth: int) -> None:
+    t = riann_tuning_t(int(tile_shape), int(depth), -1.0)
+    _check(_lib.riann_set_tuning(index.handle, ctypes.byref(t)), "riann_set_tuning")
+
+
+def riann_get_tuning(index: RiannIndex) -> dict:
+    t = riann_tuning_t()
+    _check(_lib.riann_get_tuning(index.handle, ctypes.byref(t)), "riann_get_tuning")
+    return t.as_dict()

@@ -1,0 +1,207 @@
+"""Sessions (per-stream resident state), the batched persistent form with its
+CUDA graph, and the ring-kernel variants: all must give exactly the results of
+plain per-frame calls, which tests/test_gpu_parity.py pins to the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1508_07953_gb300 import riann
+    return riann
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    w = synth.WORKLOADS["tiny"]
+    R = synth.workload_reference(w)
+    KP = synth.workload_keypoints(w, R)
+    frames = synth.Video(w.video).frames(0, w.frames)
+    return R, KP, frames
+
+
+def plain_chain(rt, idx, frames, params, resets=()):
+    outs, prev = [], None
+    for t, f in enumerate(frames):
+        if t in resets:
+            prev = None
+        a, d, c = rt.annf(idx, _dev(f), prev, params)
+        outs.append(tuple(x.cpu().numpy() for x in (a, d, c)))
+        prev = a
+    return outs
+
+
+def test_session_equals_plain_chain_and_oracle(rt, tiny):
+    R, KP, frames = tiny
+    idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
+    params = rt.riann_default_params(len(R))
+    ref = plain_chain(rt, idx, frames, params)
+    s = rt.riann_session_create(idx, 128, 128)
+    for t, f in enumerate(frames):
+        rt.riann_session_frame(s, params, _dev(f))
+        got = [x.cpu().numpy() for x in rt.session_result(s)]
+        for k in range(3):
+            assert np.array_equal(got[k], ref[t][k]), (t, k)
+    info = s.info()
+    assert info.frames == len(frames) and info.has_field == 1
+    # the oracle chain agrees too (sessions only move state around)
+    oix = oracle.Index(R, KP)
+    oa, _, _, _ = oracle.riann_frame(oix, frames[0], None, ring_limit=params.ring_limit)
+    oa1, _, _, _ = oracle.riann_frame(oix, frames[1], oa, ring_limit=params.ring_limit)
+    assert np.array_equal(ref[1][0], oa1)
+    s.close()
+    idx.close()
+
+
+def test_session_host_buffers(rt, tiny):
+    import torch
+    R, KP, frames = tiny
+    idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
+    params = rt.riann_default_params(len(R))
+    ref = plain_chain(rt, idx, frames[:4], params)
+    s = rt.riann_session_create(idx, 128, 128)
+    out = torch.empty((121, 121), dtype=torch.int32).pin_memory()
+    dist = torch.empty((121, 121), dtype=torch.int32).pin_memory()
+    cnt = torch.empty((121, 121), dtype=torch.int32).pin_memory()
+    for t in range(4):
+        rt.riann_session_frame_host(s, params, torch.from_numpy(frames[t]).pin_memory(), out, dist, cnt)
+        torch.cuda.current_stream().synchronize()
+        assert np.array_equal(out.numpy(), ref[t][0])
+        assert np.array_equal(dist.numpy(), ref[t][1])
+        assert np.array_equal(cnt.numpy(), ref[t][2])
+    s.close()
+    idx.close()
+
+
+def test_session_checkpoint_resume(rt, tiny):
+    import torch
+    R, KP, frames = tiny
+    idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
+    params = rt.riann_default_params(len(R))
+    ref = plain_chain(rt, idx, frames, params)
+    s = rt.riann_session_create(idx, 128, 128)
+    for t in range(4):
+        rt.riann_session_frame(s, params, _dev(frames[t]))
+    ckpt = torch.empty((121, 121), dtype=torch.int32)
+    rt.riann_session_field(s, ckpt)                      # to host memory
+    s.close()
+    s2 = rt.riann_session_create(idx, 128, 128)          # a fresh session resumes
+    rt.riann_session_restore(s2, ckpt)
+    for t in range(4, len(frames)):
+        rt.riann_session_frame(s2, params, _dev(frames[t]))
+        got = rt.session_result(s2)
+        assert np.array_equal(got[0].cpu().numpy(), ref[t][0]), t
+        assert np.array_equal(got[2].cpu().numpy(), ref[t][2]), t
+    s2.close()
+    idx.close()
+
+
+def test_session_reset_brute_forces_next_frame(rt, tiny):
+    R, KP, frames = tiny
+    idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
+    params = rt.riann_default_params(len(R))
+    ref = plain_chain(rt, idx, frames[:5], params, resets=(3,))
+    s = rt.riann_session_create(idx, 128, 128)
+    for t in range(5):
+        if t == 3:
+            rt.riann_session_reset(s)
+        rt.riann_session_frame(s, params, _dev(frames[t]))
+        got = rt.session_result(s)
+        assert np.array_equal(got[0].cpu().numpy(), ref[t][0]), t
+    assert (rt.session_result(s)[2].cpu().numpy() >= 0).all()
+    s.close()
+    idx.close()
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_each_stream_alone(rt, use_graph):
+    # uneven streams sharing one index: 4 sizes, with region motion
+    w = synth.WORKLOADS["tiny"]
+    R = synth.workload_reference(w)
+    KP = synth.workload_keypoints(w, R)
+    idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
+    params = rt.riann_default_params(len(R))
+    sizes = [(40, 56), (72, 130), (128, 128), (19, 300), (64, 64)]
+    vids = [synth.Video(synth.VideoSpec(H, W, 1, 50 + i, speeds=(0.5, 2.0))) for i, (H, W) in enumerate(sizes)]
+    T = 5
+    frames = [[v.frame(t) for t in range(T)] for v in vids]
+    resets = {2: (3,)}                                        # stream 2 restarts at t = 3
+    refs = [plain_chain(rt, idx, frames[i], params, resets.get(i, ())) for i in range(len(sizes))]
+    sess = [rt.riann_session_create(idx, H, W) for (H, W) in sizes]
+    total_q = sum((H - 7) * (W - 7) for H, W in sizes)
+    b = rt.riann_batch_create(idx, 8, total_q, use_graph=use_graph)
+    for t in range(T):
+        for i in resets:
+            if t in resets[i]:
+                rt.riann_session_reset(sess[i])
+        rt.riann_batch_run(b, params, sess, [_dev(frames[i][t]) for i in range(len(sizes))])
+        for i in range(len(sizes)):
+            got = rt.session_result(sess[i])
+            for k in range(3):
+                assert np.array_equal(got[k].cpu().numpy(), refs[i][t][k]), (use_graph, t, i, k)
+    info = b.info()
+    assert info.runs == T
+    assert info.graph_builds == (1 if use_graph else 0)
+    assert rt.riann_status(idx) == 0
+    # subsets of the sessions in a step (continuous batching) keep exact results
+    sub = [sess[0], sess[3]]
+    rt.riann_batch_run(b, params, sub, [_dev(vids[0].frame(T)), _dev(vids[3].frame(T))])
+    for i, s in ((0, sess[0]), (3, sess[3])):
+        a, _, _ = rt.annf(idx, _dev(vids[i].frame(T)), _dev(refs[i][T - 1][0]), params)
+        assert np.array_equal(rt.session_result(s)[0].cpu().numpy(), a.cpu().numpy())
+    b.close()
+    for s in sess:
+        s.close()
+    idx.close()
+
+
+def test_batch_rejects_oversize_and_duplicates(rt, tiny):
+    R, KP, frames = tiny
+    idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
+    params = rt.riann_default_params(len(R))
+    s = rt.riann_session_create(idx, 128, 128)
+    b = rt.riann_batch_create(idx, 2, 1000)
+    with pytest.raises(rt.RiannError) as e:
+        rt.riann_batch_run(b, params, [s], [_dev(frames[0])])
+    assert e.value.code == rt.RIANN_ERR_TOO_LARGE
+    b2 = rt.riann_batch_create(idx, 2, 40000)
+    with pytest.raises(rt.RiannError):
+        rt.riann_batch_run(b2, params, [s, s], [_dev(frames[0]), _dev(frames[0])])
+    b.close()
+    b2.close()
+    s.close()
+    idx.close()
+
+
+def test_tuning_variants_identical_and_autotune(rt, tiny):
+    R, KP, frames = tiny
+    idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
+    params = rt.riann_default_params(len(R))
+    a0, _, _ = rt.annf(idx, _dev(frames[0]), None, params)
+    outs = []
+    for shape in (0, 1):
+        for depth in (1, 2, 3):
+            rt.riann_set_tuning(idx, shape, depth)
+            outs.append([x.cpu().numpy() for x in rt.annf(idx, _dev(frames[1]), a0, params)])
+    for o in outs[1:]:
+        for k in range(3):
+            assert np.array_equal(o[k], outs[0][k])
+    res = rt.riann_autotune(idx, params, _dev(frames[1]), a0, iters=2)
+    assert len(res) == 6 and all(r["ms"] > 0 for r in res)
+    best = min(res, key=lambda r: r["ms"])
+    t = rt.riann_get_tuning(idx)
+    assert (t["tile_shape"], t["depth"]) == (best["tile_shape"], best["depth"])
+    idx.close()
