@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--start", type=int, default=21, help="first timed frame")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-ticks", type=int, default=6, help="timed ticks of the 32-stream batched form")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=12.0)
     ap.add_argument("--crop", default=None,
                     help="HxW: run on the top-left crop of each frame (small cases for profiler captures)")
     return ap.parse_args()
@@ -221,6 +225,116 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------
+# batched form: 32 uneven streams, one persistent launch (CUDA graph) per tick
+# ---------------------------------------------------------------------------
+def run_batched(riann, dev, ticks: int, warm: int = 2, flush=None):
+    """Streams sharing a 16384-patch, 32-key gray index: 8 each at 320x240,
+    640x480, 1280x720 and 1920x1080, per-stream speed from {0.25, 1, 4}
+    px/frame.  Tick 0 initialises every stream by brute force (not timed).
+    Timed: `ticks` ticks of (a) the batched form and (b) the same streams one
+    by one with the per-frame form, each from the same state."""
+    import torch
+    w = synth.BATCH_INDEX
+    R = synth.workload_reference(w)
+    KP = synth.workload_keypoints(w, R)
+    idx = riann.riann_build_reference_index(torch.from_numpy(R).to(dev), torch.from_numpy(KP).to(dev))
+    params = riann.riann_default_params(w.n)
+    specs = [synth.batch_stream_spec(i) for i in range(len(synth.BATCH_SIZES))]
+    T = 1 + warm + ticks
+    frames = [[torch.from_numpy(synth.Video(sp).frame(t)).to(dev) for t in range(T)] for sp in specs]
+    qpt = sum((sp.H - 7) * (sp.W - 7) for sp in specs)
+    stream = torch.cuda.Stream(device=dev)
+
+    def make_sessions():
+        return [riann.riann_session_create(idx, sp.H, sp.W) for sp in specs]
+
+    # (a) batched
+    sess_b = make_sessions()
+    batch = riann.riann_batch_create(idx, len(specs), qpt, use_graph=True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ticks)]
+    with torch.cuda.stream(stream):
+        for t in range(1 + warm):
+            riann.riann_batch_run(batch, params, sess_b, [f[t] for f in frames], stream=stream)
+        for k in range(ticks):
+            t = 1 + warm + k
+            if flush is not None:
+                flush.fill_(k & 0xff)
+            ev[k][0].record(stream)
+            riann.riann_batch_run(batch, params, sess_b, [f[t] for f in frames], stream=stream)
+            ev[k][1].record(stream)
+    stream.synchronize()
+    ms_b = sum(a.elapsed_time(b) for a, b in ev) / ticks
+    st = riann.riann_batch_stats(batch, stream)
+    # (b) the same streams one by one
+    sess_p = make_sessions()
+    with torch.cuda.stream(stream):
+        for t in range(1 + warm):
+            for s, f in zip(sess_p, frames):
+                riann.riann_session_frame(s, params, f[t], stream=stream)
+        for k in range(ticks):
+            t = 1 + warm + k
+            if flush is not None:
+                flush.fill_(k & 0xff)
+            ev[k][0].record(stream)
+            for s, f in zip(sess_p, frames):
+                riann.riann_session_frame(s, params, f[t], stream=stream)
+            ev[k][1].record(stream)
+    stream.synchronize()
+    ms_p = sum(a.elapsed_time(b) for a, b in ev) / ticks
+    equal = all(torch.equal(x, y) for sb, sp_ in zip(sess_b, sess_p)
+                for x, y in zip(riann.session_result(sb, stream), riann.session_result(sp_, stream)))
+    stream.synchronize()
+    info = batch.info()
+    out = {"workload": "32 gray streams (8 each 320x240, 640x480, 1280x720, 1920x1080), n=16384, K=32",
+           "queries_per_tick": qpt, "ticks": ticks,
+           "batched_ms_per_tick": ms_b, "plain_ms_per_tick": ms_p,
+           "batched_queries_per_s": qpt / (ms_b / 1e3), "plain_queries_per_s": qpt / (ms_p / 1e3),
+           "speedup": ms_p / ms_b, "equal_to_plain": bool(equal), "graph_builds": int(info.graph_builds),
+           "last_tick_work": st}
+    batch.close()
+    for s in sess_b + sess_p:
+        s.close()
+    idx.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# served form: Poisson arrivals of 480p/720p/1080p gray and RGB streams
+# ---------------------------------------------------------------------------
+def run_served(riann, dev, gray_idx, seconds: float):
+    """Same arrival trace through (a) the continuous-batching server and (b) a
+    server that runs each frame by itself; then (a) at a light load."""
+    import torch
+    from paper_1508_07953_gb300 import serve
+    w = synth.SERVE_RGB_INDEX
+    R = synth.workload_reference(w)
+    KP = synth.workload_keypoints(w, R)
+    rgb_idx = riann.riann_build_reference_index(torch.from_numpy(R).to(dev), torch.from_numpy(KP).to(dev))
+    pools = {fmt: [torch.from_numpy(f).pin_memory() for f in synth.serve_frame_pool(fmt, 12, 2000 + i)]
+             for i, fmt in enumerate(synth.SERVE_FORMATS)}
+    params = riann.riann_default_params(65536)
+    out = {"workload": "Poisson arrivals (rate 4/s, life U[5,20] s), 30 fps, 480p/720p/1080p x gray/RGB, "
+                       "n=65536 refs and K=64 key points per index",
+           "budget_bytes": 4 << 30, "max_tick_queries": 48 << 20}
+
+    def one(rate, plain):
+        spec = serve.ServeSpec(rate=rate, duration=seconds, seed=7)
+        srv = riann.RiannServer(gray_idx, rgb_idx, budget_bytes=4 << 30, max_tick_queries=48 << 20,
+                                max_streams=256, params=params, plain=plain)
+        try:
+            return serve.run(srv, pools, spec)
+        finally:
+            srv.close()
+
+    out["batched"] = one(4.0, False)
+    out["plain"] = one(4.0, True)
+    out["batched_light_load"] = one(0.25, False)
+    out["light_load_rate"] = 0.25
+    rgb_idx.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_ours(args, rank, world, local):
@@ -366,6 +480,12 @@ def run_ours(args, rank, world, local):
     line["clocks"] = clocks
     if e2e:
         line["e2e"] = e2e
+    if not args.no_batch:
+        line["batched"] = run_batched(riann, dev, args.batch_ticks, flush=flush)
+    if not args.no_serve:
+        del flush
+        torch.cuda.empty_cache()
+        line["served"] = run_served(riann, dev, idx, args.serve_seconds)
     if world == 1 and not args.no_cpu_baseline:
         pd = {"alpha_num": params.alpha_num, "alpha_den": params.alpha_den, "ring_limit": params.ring_limit}
         line["cpu_baseline"] = cpu_baseline(R, KP, frames_np, pd)

@@ -320,6 +320,60 @@ int riann_autotune(riann_index_t idx, const riann_params* p, riann_stream_t stre
 int riann_set_tuning(riann_index_t idx, const riann_tuning_t* t);
 int riann_get_tuning(riann_index_t idx, riann_tuning_t* out);
 
+/* ------------------------------------------------------------------------
+ * Served form: continuous batching of many streams of different sizes and
+ * channel counts.  Streams are admitted while their resident state
+ * (riann_session_state_bytes) fits `budget_bytes` and their queries fit
+ * `max_tick_queries` per index; otherwise riann_server_open returns
+ * RIANN_ERR_ADMISSION (the caller may retry when streams close).  A
+ * submitted frame is copied into one of the stream's two pinned input slots;
+ * a newer frame replaces one not yet dispatched (counted as dropped).
+ * riann_server_step completes the tick in flight (blocking only if `wait`)
+ * and launches the next over every stream with a pending frame: copies in,
+ * one batched step per index, fields copied back to pinned host memory.
+ * Frames arriving while a tick runs join the next tick.  Results equal those
+ * of each stream run alone.  All times are riann_server_clock() seconds.
+ * ------------------------------------------------------------------------ */
+typedef struct riann_server_s* riann_server_t;
+
+typedef struct {
+  int32_t stream_id;
+  int64_t frame_id;
+  double t_arrival;   /* as given to riann_server_submit            */
+  double t_done;      /* when the host saw the frame's tick complete */
+} riann_server_result_t;
+
+typedef struct {
+  int32_t open_streams;
+  size_t budget_bytes, used_bytes;
+  int64_t ticks, frames_done, queries_done, rejected, submitted, dropped;
+} riann_server_info_t;
+
+#define RIANN_SERVER_PLAIN 0x1   /* run each frame of a tick by itself (comparison mode) */
+
+double riann_server_clock(void);
+/* gray / rgb: indexes for 1- and 3-channel streams (either may be NULL).
+ * The server keeps pointers to them; they must outlive it. */
+int riann_server_create(riann_index_t gray, riann_index_t rgb, size_t budget_bytes, int64_t max_tick_queries,
+                        int32_t max_streams, const riann_params* p, int32_t flags, riann_server_t* out);
+void riann_server_destroy(riann_server_t s);
+int riann_server_open(riann_server_t s, int32_t H, int32_t W, int32_t C, int32_t* stream_id);
+int riann_server_close(riann_server_t s, int32_t stream_id);
+/* h_frame: host uint8 [H][W][C]; copied before the call returns. */
+int riann_server_submit(riann_server_t s, int32_t stream_id, const uint8_t* h_frame, int64_t frame_id,
+                        double t_arrival);
+/* *launched = number of frames in the newly launched tick (0: none, or the
+ * previous tick is still running and wait == 0). */
+int riann_server_step(riann_server_t s, riann_stream_t stream, int32_t wait, int32_t* launched);
+/* Pops up to `max` completed frames. */
+int riann_server_poll(riann_server_t s, riann_server_result_t* out, int32_t max, int32_t* n);
+/* Latest completed field of a stream (int32 [H-7][W-7] host copy); valid
+ * while the stream has no frame in flight. */
+int riann_server_field(riann_server_t s, int32_t stream_id, int32_t* out);
+int riann_server_info(riann_server_t s, riann_server_info_t* out);
+int riann_server_stream_counts(riann_server_t s, int32_t stream_id, int64_t* submitted, int64_t* dropped,
+                               int64_t* completed);
+
 /* Synchronises `stream`, then returns RIANN_OK if the device status word is
  * clear, RIANN_ERR_DEVICE otherwise (and clears it); *bits (nullable) receives
  * the word. */

@@ -121,6 +121,18 @@ _lib.riann_autotune.argtypes = [_P, ctypes.POINTER(riann_params), _P, _P, _i32, 
                                 ctypes.POINTER(riann_tuning_t), _i32, ctypes.POINTER(_i32)]
 _lib.riann_set_tuning.argtypes = [_P, ctypes.POINTER(riann_tuning_t)]
 _lib.riann_get_tuning.argtypes = [_P, ctypes.POINTER(riann_tuning_t)]
+_lib.riann_server_clock.restype = ctypes.c_double
+_lib.riann_server_create.argtypes = [_P, _P, ctypes.c_size_t, _i64, _i32, ctypes.POINTER(riann_params), _i32,
+                                     ctypes.POINTER(_P)]
+_lib.riann_server_destroy.argtypes = [_P]
+_lib.riann_server_destroy.restype = None
+_lib.riann_server_open.argtypes = [_P, _i32, _i32, _i32, ctypes.POINTER(_i32)]
+_lib.riann_server_close.argtypes = [_P, _i32]
+_lib.riann_server_submit.argtypes = [_P, _i32, _P, _i64, ctypes.c_double]
+_lib.riann_server_step.argtypes = [_P, _P, _i32, ctypes.POINTER(_i32)]
+_lib.riann_server_field.argtypes = [_P, _i32, _P]
+_lib.riann_server_stream_counts.argtypes = [_P, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                            ctypes.POINTER(_i64)]
 _lib.riann_status.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_uint32)]
 
 
@@ -517,3 +529,102 @@ def riann_get_tuning(index: RiannIndex) -> dict:
     t = riann_tuning_t()
     _check(_lib.riann_get_tuning(index.handle, ctypes.byref(t)), "riann_get_tuning")
     return t.as_dict()
+
+
+# ---------------------------------------------------------------------------
+# served form
+# ---------------------------------------------------------------------------
+RIANN_SERVER_PLAIN = 0x1
+
+
+class riann_server_result_t(ctypes.Structure):
+    _fields_ = [("stream_id", ctypes.c_int32), ("frame_id", ctypes.c_int64),
+                ("t_arrival", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class riann_server_info_t(ctypes.Structure):
+    _fields_ = [("open_streams", ctypes.c_int32), ("budget_bytes", ctypes.c_size_t),
+                ("used_bytes", ctypes.c_size_t), ("ticks", ctypes.c_int64), ("frames_done", ctypes.c_int64),
+                ("queries_done", ctypes.c_int64), ("rejected", ctypes.c_int64), ("submitted", ctypes.c_int64),
+                ("dropped", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib.riann_server_poll.argtypes = [_P, ctypes.POINTER(riann_server_result_t), _i32, ctypes.POINTER(_i32)]
+_lib.riann_server_info.argtypes = [_P, ctypes.POINTER(riann_server_info_t)]
+
+
+def riann_server_clock() -> float:
+    return float(_lib.riann_server_clock())
+
+
+class RiannServer:
+    def __init__(self, gray: Optional[RiannIndex], rgb: Optional[RiannIndex], budget_bytes: int,
+                 max_tick_queries: int, max_streams: int, params: riann_params, plain: bool = False):
+        h = ctypes.c_void_p(0)
+        _check(_lib.riann_server_create(gray.handle if gray else None, rgb.handle if rgb else None,
+                                        int(budget_bytes), int(max_tick_queries), int(max_streams),
+                                        ctypes.byref(params), RIANN_SERVER_PLAIN if plain else 0,
+                                        ctypes.byref(h)), "riann_server_create")
+        self.handle = h
+        self.indexes = (gray, rgb)
+        self._res = (riann_server_result_t * 1024)()
+
+    def open(self, H: int, W: int, C: int) -> Optional[int]:
+        """Admit a stream; None when the budget or the tick capacity is full."""
+        sid = ctypes.c_int32(-1)
+        rc = _lib.riann_server_open(self.handle, int(H), int(W), int(C), ctypes.byref(sid))
+        if rc == RIANN_ERR_ADMISSION:
+            return None
+        _check(rc, "riann_server_open")
+        return int(sid.value)
+
+    def close_stream(self, sid: int) -> None:
+        _check(_lib.riann_server_close(self.handle, int(sid)), "riann_server_close")
+
+    def submit(self, sid: int, frame, frame_id: int, t_arrival: float) -> None:
+        """frame: contiguous CPU uint8 tensor or numpy array [H][W][C]."""
+        ptr = frame.data_ptr() if isinstance(frame, torch.Tensor) else frame.ctypes.data
+        _check(_lib.riann_server_submit(self.handle, int(sid), ctypes.c_void_p(ptr), int(frame_id),
+                                        float(t_arrival)), "riann_server_submit")
+
+    def step(self, wait: bool = False, stream=None) -> int:
+        n = ctypes.c_int32(0)
+        _check(_lib.riann_server_step(self.handle, _stream(stream), int(bool(wait)), ctypes.byref(n)),
+               "riann_server_step")
+        return int(n.value)
+
+    def poll(self):
+        n = ctypes.c_int32(0)
+        _check(_lib.riann_server_poll(self.handle, self._res, 1024, ctypes.byref(n)), "riann_server_poll")
+        return [(self._res[i].stream_id, self._res[i].frame_id, self._res[i].t_arrival, self._res[i].t_done)
+                for i in range(n.value)]
+
+    def field(self, sid: int, out: torch.Tensor) -> None:
+        if out.is_cuda or out.dtype != torch.int32 or not out.is_contiguous():
+            raise ValueError("out must be a contiguous int32 CPU tensor")
+        _check(_lib.riann_server_field(self.handle, int(sid), ctypes.c_void_p(out.data_ptr())), "riann_server_field")
+
+    def counts(self, sid: int):
+        a, b, c = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(_lib.riann_server_stream_counts(self.handle, int(sid), ctypes.byref(a), ctypes.byref(b),
+                                               ctypes.byref(c)), "riann_server_stream_counts")
+        return int(a.value), int(b.value), int(c.value)
+
+    def info(self) -> dict:
+        out = riann_server_info_t()
+        _check(_lib.riann_server_info(self.handle, ctypes.byref(out)), "riann_server_info")
+        return out.as_dict()
+
+    def close(self):
+        if self.handle and self.handle.value:
+            _lib.riann_server_destroy(self.handle)
+            self.handle = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

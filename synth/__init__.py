@@ -187,25 +187,26 @@ class Video:
         s = self.spec
         shot, tt = (t // s.cut_every, t % s.cut_every) if s.cut_every else (0, t)
         tex, vel, aff = self._scene(shot)
-        Y = np.arange(s.H, dtype=np.float64)[:, None] * np.ones((1, s.W))
-        X = np.ones((s.H, 1)) * np.arange(s.W, dtype=np.float64)[None, :]
+        Y = np.arange(s.H, dtype=np.float32)[:, None]
+        X = np.arange(s.W, dtype=np.float32)[None, :]
         if s.motion == "global":
             dy, dx = self._drift(shot, tt)
-            Ys, Xs = Y - dy, X - dx
+            Ys, Xs = Y - np.float32(dy), X - np.float32(dx)
         else:
-            ry = (np.arange(s.H) // s.region)[:, None] * np.ones((1, s.W), np.int64)
-            rx = np.ones((s.H, 1), np.int64) * (np.arange(s.W) // s.region)[None, :]
-            cy = (ry + 0.5) * s.region
-            cx = (rx + 0.5) * s.region
-            v = vel[ry, rx]
-            A = aff[ry, rx]
+            ry = np.arange(s.H) // s.region
+            rx = np.arange(s.W) // s.region
+            cy = ((ry + 0.5) * s.region).astype(np.float32)[:, None]
+            cx = ((rx + 0.5) * s.region).astype(np.float32)[None, :]
+            v = vel.astype(np.float32)[ry][:, rx]            # [H][W][2]
+            A = aff.astype(np.float32)[ry][:, rx]            # [H][W][2][2]
             py, px = Y - cy, X - cx
-            dy = tt * (v[..., 0] + A[..., 0, 0] * py + A[..., 0, 1] * px)
-            dx = tt * (v[..., 1] + A[..., 1, 0] * py + A[..., 1, 1] * px)
+            f = np.float32(tt)
+            dy = f * (v[..., 0] + A[..., 0, 0] * py + A[..., 0, 1] * px)
+            dx = f * (v[..., 1] + A[..., 1, 0] * py + A[..., 1, 1] * px)
             Ys, Xs = Y - dy, X - dx
-        img = bilinear_wrap(tex, Ys, Xs)
-        noise = np.random.default_rng([s.seed, t, 13]).normal(0.0, s.noise_sigma, size=img.shape)
-        return quantise(img + noise.astype(np.float32))
+        img = bilinear_wrap(tex, np.broadcast_to(Ys, (s.H, s.W)), np.broadcast_to(Xs, (s.H, s.W)))
+        noise = np.random.default_rng([s.seed, t, 13]).standard_normal(size=img.shape, dtype=np.float32)
+        return quantise(img + np.float32(s.noise_sigma) * noise)
 
     def frames(self, t0: int, t1: int) -> np.ndarray:
         return np.stack([self.frame(t) for t in range(t0, t1)])
@@ -249,6 +250,20 @@ WORKLOADS = {
 BATCH_SIZES = [(240, 320)] * 8 + [(480, 640)] * 8 + [(720, 1280)] * 8 + [(1080, 1920)] * 8
 BATCH_INDEX = Workload("batch_index", 16384, 32, 1, 64, (720, 1280), 8,
                        VideoSpec(720, 1280, 1, 9), 60)
+
+
+# Served form: an RGB index (65536 patches, 64 key points) beside the 1080p gray
+# one; streams of 480p / 720p / 1080p, gray or RGB, region motion, N(0, 2^2).
+SERVE_RGB_INDEX = Workload("serve_rgb", 65536, 64, 3, 32, (720, 1280), 12,
+                           VideoSpec(720, 1280, 3, 13), 60)
+SERVE_FORMATS = ((480, 640, 1), (720, 1280, 1), (1080, 1920, 1), (480, 640, 3), (720, 1280, 3), (1080, 1920, 3))
+
+
+def serve_frame_pool(fmt, n_frames: int, seed: int) -> list:
+    """n_frames consecutive frames of one synthetic stream of format (H, W, C)."""
+    H, W, C = fmt
+    v = Video(VideoSpec(H, W, C, seed, speeds=(0.0, 0.5, 2.0, 6.0), noise_sigma=2.0))
+    return [v.frame(t) for t in range(n_frames)]
 
 
 def batch_stream_spec(s: int) -> VideoSpec:
