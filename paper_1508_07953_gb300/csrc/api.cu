@@ -53,7 +53,7 @@ cudaError_t dalloc(T** p, size_t count, size_t& total) {
 
 bool params_ok(const riann_params* p) {
   return p && p->alpha_den >= 1 && p->alpha_den <= 8 && p->alpha_num >= 0 &&
-         p->alpha_num <= 8 * p->alpha_den && p->ring_limit >= -1 && p->cap >= 0 && p->cap <= 3;
+         p->alpha_num <= 8 * p->alpha_den && p->ring_limit >= -1 && p->cap >= 0 && p->cap <= 5;
 }
 
 bool frame_ok(int32_t H, int32_t W) {
@@ -838,7 +838,7 @@ int riann_batch_info(riann_batch_t b, riann_batch_info_t* out) {
 // autotuner
 // ---------------------------------------------------------------------------
 int riann_set_tuning(riann_index_t idx, const riann_tuning_t* t) {
-  if (!idx || !t || t->tile_shape < 0 || t->tile_shape >= kTileShapes || t->depth < 1 || t->depth > 3)
+  if (!idx || !t || t->tile_shape < 0 || t->tile_shape >= kTileShapes || t->depth < 1 || t->depth > 5)
     return RIANN_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(idx->mu);
   idx->tile_shape = t->tile_shape;
@@ -878,7 +878,7 @@ int riann_autotune(riann_index_t idx, const riann_params* p, riann_stream_t stre
   ix.profile = false;
   const int saved_shape = ix.tile_shape, saved_depth = ix.depth;
   for (int shape = 0; shape < kTileShapes && e == cudaSuccess; ++shape) {
-    for (int depth = 1; depth <= 3 && e == cudaSuccess; ++depth) {
+    for (int depth = 1; depth <= 5 && e == cudaSuccess; ++depth) {
       ix.tile_shape = shape;
       ix.depth = depth;
       const FrameItem it = make_item(d_frame, d_prev_annf, out, nullptr, nullptr, H, W, shape);

@@ -564,6 +564,21 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(const SparseArgs a) {
                           (ns1 < 3 || codes_pass(v2[u], lo2, hi2, any2));
           bits |= (ok ? 1u : 0u) << u;
         }
+        // deeper stage 1 (depth 4..5): the next groups by estimated
+        // selectivity, one 16-byte load per lane for its four entries, only
+        // while some entry of the warp is still alive
+        for (int oi = 3; oi < ns1; ++oi) {
+          if (!__any_sync(kFull, bits != 0)) break;
+          if (bits) {
+            const int g = s_ord[warp][oi];
+            const uint4 wv4 = __ldg(reinterpret_cast<const uint4*>(cw + (int64_t)g * a.nw) + (j0 >> 2));
+            const uint32_t lo4 = s_lo4[warp][g], hi4 = s_hi4[warp][g], any4 = s_any4[warp][g];
+            const uint32_t vg[4] = {wv4.x, wv4.y, wv4.z, wv4.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (((bits >> u) & 1u) && !codes_pass(vg[u], lo4, hi4, any4)) bits &= ~(1u << u);
+          }
+        }
         a0 = b0;
         a1 = b1;
         a2 = b2;

@@ -147,7 +147,7 @@ def test_tiny_chain_all_queries(rt, tiny, alpha, limit):
 def test_cap_does_not_change_output(rt, tiny):
     R, KP, frames = tiny
     base = gpu_chain(rt, R, KP, frames[:3], make_params(rt, len(R)))
-    for cap in (1, 2, 3):
+    for cap in (1, 2, 3, 4, 5):
         other = gpu_chain(rt, R, KP, frames[:3], make_params(rt, len(R), cap=cap))
         for t in range(3):
             for k in range(3):
