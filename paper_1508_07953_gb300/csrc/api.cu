@@ -94,12 +94,10 @@ SparseArgs sparse_args(const Index& ix, const riann_params* p, Workspace& ws, un
   sa.E = ix.E;
   sa.RB = ix.RB;
   sa.CW = ix.CW;
-  sa.CWE = ix.CWE;
   sa.n = ix.n;
   sa.K = ix.K;
   sa.Kp = ix.Kp;
   sa.G = ix.G;
-  sa.GP = ix.GP;
   sa.nw = ix.nw;
   sa.alpha_num = p->alpha_num;
   sa.alpha_den = p->alpha_den;
@@ -162,7 +160,6 @@ void free_index(Index* ix) {
   cudaFree(ix->E);
   cudaFree(ix->RB);
   cudaFree(ix->CW);
-  cudaFree(ix->CWE);
   cudaFree(ix->status);
   cudaFree(ix->stats);
   for (int k = 0; k < kSlots; ++k)
@@ -363,7 +360,6 @@ int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t cha
   ix->n_pad = (n + kDenseTileN - 1) / kDenseTileN * kDenseTileN;
   ix->Kp = (K + 3) / 4 * 4;
   ix->G = (K + 3) / 4;
-  ix->GP = (ix->G + 3) / 4 * 4;
   ix->nw = (n + 3) / 4 * 4;
   const int D = ix->D;
   size_t& tot = ix->device_bytes;
@@ -377,7 +373,6 @@ int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t cha
   if (e == cudaSuccess) e = dalloc(&ix->E, (size_t)K * kBuckets, tot);
   if (e == cudaSuccess) e = dalloc(&ix->RB, (size_t)K * (kBuckets + 1), tot);
   if (e == cudaSuccess) e = dalloc(&ix->CW, (size_t)K * ix->G * ix->nw, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->CWE, (size_t)K * ix->GP * n, tot);
   if (e == cudaSuccess) e = dalloc(&ix->status, 1, tot);
   if (e == cudaSuccess) e = dalloc(&ix->stats, kStats, tot);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

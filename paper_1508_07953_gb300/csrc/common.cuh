@@ -87,9 +87,7 @@ struct Index {
   uint32_t* RB = nullptr;         // [K][kBuckets + 1] first rank of each bucket in TA[m]; RB[m][256] = n
   uint32_t* CW = nullptr;         // [K][G][nw] in key m's sorted order, codes of keys 4g..4g+3 (one byte
                                   // each); rows padded to nw = n rounded up to 4 (16-byte aligned rows)
-  uint32_t* CWE = nullptr;        // [K][n][GP] the same codes entry-major (GP = G rounded up to 4 words)
-  int G = 0;                      // ceil(K / 4)
-  int GP = 0;                     // ceil(G / 4) * 4
+  int G = 0;                      // ceil(K / 4) = Kp / 4
   int nw = 0;                     // n rounded up to 4
   uint32_t* status = nullptr;     // device status word (RIANN_DEV_* bits)
   unsigned long long* stats = nullptr;  // [kStats] counters of the last frame
@@ -125,10 +123,9 @@ struct SparseArgs {
   const uint32_t* E;
   const uint32_t* RB;
   const uint32_t* CW;
-  const uint32_t* CWE;
-  int n, K, Kp, G, GP, nw;
+  int n, K, Kp, G, nw;
   int alpha_num, alpha_den, ring_limit;
-  int depth;                      // stage-1 filter depth (1..3)
+  int depth;                      // stage-1 filter depth (1..5)
   int32_t* dense_list;
   uint32_t* counters;             // [0] brute-force list length, [1] tile counter
   uint32_t* status;

@@ -155,7 +155,7 @@ __global__ void k_codes(const uint32_t* __restrict__ P, const uint32_t* __restri
 // CW[m][g][j]: codes of keys 4g..4g+3 of reference Tid[m][j] (byte i = key 4g+i;
 // keys past K read as 0).
 __global__ void k_pack_codes(const int32_t* __restrict__ Tid, const uint8_t* __restrict__ code, int n, int K,
-                             int G, int GP, int nw, uint32_t* __restrict__ CW, uint32_t* __restrict__ CWE) {
+                             int G, int nw, uint32_t* __restrict__ CW) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int m = blockIdx.y;
   if (j >= n) return;
@@ -168,9 +168,7 @@ __global__ void k_pack_codes(const int32_t* __restrict__ Tid, const uint8_t* __r
       if (k < K) w |= (uint32_t)c[k] << (8 * i);
     }
     CW[((int64_t)m * G + g) * nw + j] = w;
-    CWE[((int64_t)m * n + j) * GP + g] = w;
   }
-  for (int g = G; g < GP; ++g) CWE[((int64_t)m * n + j) * GP + g] = 0;
 }
 
 }  // namespace
@@ -208,7 +206,7 @@ cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
   }
   e = cudaMemsetAsync(ix.CW, 0, sizeof(uint32_t) * (size_t)K * ix.G * ix.nw, s);
   if (e != cudaSuccess) return e;
-  k_pack_codes<<<dim3((n + 255) / 256, K), 256, 0, s>>>(ix.Tid, code, n, K, ix.G, ix.GP, ix.nw, ix.CW, ix.CWE);
+  k_pack_codes<<<dim3((n + 255) / 256, K), 256, 0, s>>>(ix.Tid, code, n, K, ix.G, ix.nw, ix.CW);
   e = cudaFreeAsync(code, s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

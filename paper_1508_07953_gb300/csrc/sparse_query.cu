@@ -8,16 +8,19 @@
 // and hands queries to its warps through a shared counter (candidate counts
 // vary by orders of magnitude between queries, Sec. 3.3 / Fig. 5).
 //
-// Ring sizes and the intersection work on 8-bit bucket codes (see common.cuh):
-// a reference whose code for key m lies strictly inside the code range of the
-// exact ring bounds is a member of ring m, one outside it is not, and one in a
-// boundary bucket is settled exactly from P.
+// Ring sizes and the first filter of the intersection work on 8-bit bucket
+// codes (see common.cuh): a reference whose code for key m lies outside the
+// code range of the exact ring bounds is not a member of ring m.  The
+// references that pass the filter are then tested exactly against every ring
+// from their row of key-point distances in P (16 MB for n = 65536, K = 64:
+// it stays in L2).
 #include "common.cuh"
 
 namespace riann {
 namespace {
 
 constexpr int kWarps = 8;
+constexpr int kCtasPerSm = 3;   // register budget 80 per thread
 constexpr unsigned kFull = 0xffffffffu;
 
 // Exact ring membership |sqrt(A) - sqrt(B)| <= (p/q) sqrt(C) for A, B <= 192*255^2:
@@ -169,32 +172,20 @@ __device__ __forceinline__ uint32_t bytes_ge(uint32_t x, uint32_t y) {   // 0x80
   return ((x & ~y) | (~(x ^ y) & t)) & kHi;
 }
 
-__device__ __forceinline__ uint32_t bytes_eq(uint32_t x, uint32_t y) {   // 0x80 where x == y
-  const uint32_t z = x ^ y;
-  return ~(((z & ~kHi) + ~kHi) | z) & kHi;
-}
-
 // every byte with lo <= code <= hi, or marked "always passes" in any4
 __device__ __forceinline__ bool codes_pass(uint32_t w, uint32_t lo4, uint32_t hi4, uint32_t any4) {
   return ((bytes_ge(w, lo4) & bytes_ge(hi4, w)) | (any4 & kHi)) == kHi;
 }
 
-// bit (4g + i) set where byte i of w sits on a boundary bucket of key 4g + i
-__device__ __forceinline__ unsigned long long boundary_bits(uint32_t w, uint32_t lo4, uint32_t hi4, uint32_t any4,
-                                                            int g) {
-  const uint32_t eq = (bytes_eq(w, lo4) | bytes_eq(w, hi4)) & ~any4;
-  const uint32_t b = (((eq >> 7) * 0x00204081u) >> 21) & 0xfu;   // bits 7, 15, 23, 31 -> 0..3
-  return (unsigned long long)b << (4 * g);
-}
-
 constexpr int kQueue = 256;   // per-warp ring buffer of stage-1 survivors
+constexpr int kRowBatch = 4;  // 16-byte words of a distance row loaded per round (4 keys each)
 
 // One CTA per tile of TY x TX query positions.  Single-frame launch
 // (BATCH = false): the grid is the frame's tiles.  Batched launch: a
 // persistent grid whose CTAs take tiles of all the batch's frames from an
 // atomic counter, in the order of the items.
 template <int C, int SHAPE, bool BATCH>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(const SparseArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const SparseArgs a) {
   constexpr int TY = SHAPE == kTile4x32 ? 4 : 8;
   constexpr int TX = SHAPE == kTile4x32 ? 32 : 16;
   constexpr int D = 64 * C, NW = D / 4;
@@ -205,8 +196,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(const SparseArgs a) {
   __shared__ __align__(16) uint8_t s_tile[(TY + 7) * TROWP];
   __shared__ uint32_t s_kp[kMaxK * KPW];
   __shared__ uint32_t s_coarse[kMaxK][16];        // every 16th bucket edge per key
-  __shared__ uint32_t s_lo[kWarps][kMaxK];        // exact ring bounds on A
-  __shared__ uint32_t s_hi[kWarps][kMaxK];
+  // exact ring bounds [lo, hi] on A as (lo, hi - lo) per key; padding keys (0, ~0)
+  __shared__ __align__(16) uint32_t s_lw[kWarps][2 * kMaxK];
   __shared__ int16_t s_clo[kWarps][kMaxK];        // their bucket codes (-1..255)
   __shared__ int16_t s_chi[kWarps][kMaxK];
   __shared__ uint32_t s_ub[kWarps][kMaxK];        // bucket-granular upper bound on |Ring_m|
@@ -340,8 +331,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(const SparseArgs a) {
         const int chi = bucket_code(s_coarse[m], e, hi);
         const uint32_t ub = __ldg(rb + chi + 1) - (clo < 0 ? 0u : __ldg(rb + clo));
         const uint32_t lb = chi > clo + 1 ? __ldg(rb + chi) - __ldg(rb + clo + 1) : 0u;
-        s_lo[warp][m] = lo;
-        s_hi[warp][m] = hi;
+        s_lw[warp][2 * m] = lo;
+        s_lw[warp][2 * m + 1] = hi - lo;
         s_clo[warp][m] = (int16_t)clo;
         s_chi[warp][m] = (int16_t)chi;
         s_ub[warp][m] = ub;
@@ -351,6 +342,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(const SparseArgs a) {
           if (ub <= (uint32_t)a.ring_limit) small = true;
           else if (lb <= (uint32_t)a.ring_limit) maybe = true;
         }
+      } else if (m < a.Kp) {   // padding key of a distance row: always passes
+        s_lw[warp][2 * m] = 0u;
+        s_lw[warp][2 * m + 1] = 0xffffffffu;
       }
     }
 #pragma unroll
@@ -381,7 +375,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(const SparseArgs a) {
           const int m = __ffs(todo) - 1 + 32 * h;
           todo &= todo - 1;
           const int2 run = ring_run(a.TA + (int64_t)m * n, a.RB + m * (kBuckets + 1), s_clo[warp][m],
-                                    s_chi[warp][m], s_lo[warp][m], s_hi[warp][m], lane);
+                                    s_chi[warp][m], s_lw[warp][2 * m], s_lw[warp][2 * m] + s_lw[warp][2 * m + 1], lane);
           if ((uint32_t)(run.y - run.x) <= (uint32_t)a.ring_limit) found = true;
         }
       }
@@ -393,7 +387,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(const SparseArgs a) {
 
     // exact run of the seed ring in its sorted list (the whole warp searches)
     const int2 run = ring_run(a.TA + (int64_t)ms * n, a.RB + ms * (kBuckets + 1), s_clo[warp][ms],
-                              s_chi[warp][ms], s_lo[warp][ms], s_hi[warp][ms], lane);
+                              s_chi[warp][ms], s_lw[warp][2 * ms],
+                              s_lw[warp][2 * ms] + s_lw[warp][2 * ms + 1], lane);
     const int jlo = run.x, jhi = run.y;
 
     // per group of 4 keys: packed code ranges, keys that always pass, and an
@@ -436,9 +431,10 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(const SparseArgs a) {
     // a3 + a4.  Stage 1: each lane tests 4 consecutive seed-run entries (one
     // 16-byte load of the most selective group's codes, next chunk prefetched)
     // and the survivors against the next two groups; survivors go to a
-    // per-warp ring buffer (warp prefix sum).  Stage 2: each batch of 32
-    // queued entries is tested against every group (entry-major codes),
-    // boundary buckets are settled exactly from P, members are verified.
+    // per-warp ring buffer (warp prefix sum).  Stage 2: each lane takes one
+    // queued entry and tests its distance row exactly against every ring,
+    // lo_m <= A_m <= hi_m as one unsigned compare (A_m - lo_m <= hi_m - lo_m);
+    // members are verified against the query.
     unsigned long long best = lane == 0 ? (((unsigned long long)Cd << 32) | (unsigned)rp) : ~0ull;
     uint32_t cnt = 0;
     const uint32_t* cw = a.CW + (int64_t)ms * G * a.nw;
@@ -453,82 +449,46 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_sparse(const SparseArgs a) {
     const uint4* cw0 = reinterpret_cast<const uint4*>(cw + (int64_t)g0 * a.nw);
     const uint32_t* cw1 = cw + (int64_t)g1 * a.nw;
     const uint32_t* cw2 = cw + (int64_t)g2 * a.nw;
-    constexpr int kMaxGl = kMaxK / 4;
-    (void)kMaxGl;
-    const uint4* cwe = reinterpret_cast<const uint4*>(a.CWE + (int64_t)ms * n * a.GP);
-    const int gq = a.GP / 4;                       // uint4 words per entry-major row
+    const uint4* prow = reinterpret_cast<const uint4*>(a.P);
+    const int kq = a.Kp >> 2;                      // 16-byte words per distance row
+    const uint4* lw4 = reinterpret_cast<const uint4*>(s_lw[warp]);
     int32_t* queue = s_queue[warp];
     int qhead = 0, qn = 0;                         // ring buffer: [qhead, qhead + qn)
 
     auto drain = [&](int take) {
-      // round 1: every group's codes (entry-major row) and the reference index
       bool alive = lane < take;
       const int j = alive ? queue[(qhead + lane) & (kQueue - 1)] : 0;
-      uint4 w4[4];
       int r = 0;
       if (alive) {
-#pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4)
-          if (c4 < gq) w4[c4] = __ldg(cwe + (int64_t)j * gq + c4);
         r = __ldg(tid + j);
-      }
-      unsigned long long unc = 0;
-      if (alive) {
+        const uint4* row = prow + (int64_t)r * kq;
+        // kRowBatch 4-key groups per round of loads; a lane stops at its
+        // first failed round
+#pragma unroll 1
+        for (int h = 0; h < kq && alive; h += kRowBatch) {
+          uint4 v[kRowBatch];
 #pragma unroll
-        for (int c4 = 0; c4 < 4; ++c4) {
-          if (c4 < gq) {
-            const uint32_t ws[4] = {w4[c4].x, w4[c4].y, w4[c4].z, w4[c4].w};
+          for (int c = 0; c < kRowBatch; ++c) v[c] = h + c < kq ? __ldg(row + h + c) : make_uint4(0, 0, 0, 0);
+          unsigned ok = 1u;
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int g = 4 * c4 + u;
-              if (g < G) {
-                const uint32_t lo4 = s_lo4[warp][g], hi4 = s_hi4[warp][g], any4 = s_any4[warp][g];
-                if (!codes_pass(ws[u], lo4, hi4, any4)) alive = false;
-                unc |= boundary_bits(ws[u], lo4, hi4, any4, g);
-              }
+          for (int c = 0; c < kRowBatch; ++c) {
+            if (h + c < kq) {
+              const uint4 l0 = lw4[2 * (h + c)], l1 = lw4[2 * (h + c) + 1];
+              ok &= (unsigned)(v[c].x - l0.x <= l0.y) & (unsigned)(v[c].y - l0.z <= l0.w) &
+                    (unsigned)(v[c].z - l1.x <= l1.y) & (unsigned)(v[c].w - l1.z <= l1.w);
             }
           }
+          alive = ok != 0u;
         }
       }
-      // round 2: the distances of the boundary-bucket keys, four keys per
-      // 16-byte load; round 3: the reference row of members
       if (alive) {
-        const uint4* p4 = reinterpret_cast<const uint4*>(a.P + (int64_t)r * a.Kp);
-        unsigned ug = 0;   // groups holding boundary-bucket keys
+        ++cnt;
+        const uint4* r4 = reinterpret_cast<const uint4*>(a.R + (int64_t)r * D);
+        uint32_t d = 0;
 #pragma unroll
-        for (int g = 0; g < kMaxG; ++g)
-          if ((unc >> (4 * g)) & 0xfull) ug |= 1u << g;
-        while (ug && alive) {
-          int gg[4];
-          uint4 pv[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            gg[u] = ug ? __ffs(ug) - 1 : -1;
-            ug &= ug - 1;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) pv[u] = gg[u] >= 0 ? __ldg(p4 + gg[u]) : make_uint4(0, 0, 0, 0);
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (gg[u] < 0) continue;
-            const uint32_t pw[4] = {pv[u].x, pv[u].y, pv[u].z, pv[u].w};
-            const unsigned ub4 = (unsigned)(unc >> (4 * gg[u])) & 0xfu;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-              const int k = 4 * gg[u] + i;
-              if (((ub4 >> i) & 1u) && (pw[i] < s_lo[warp][k] || pw[i] > s_hi[warp][k])) alive = false;
-            }
-          }
-        }
-        if (alive) {
-          ++cnt;
-          const uint4* r4 = reinterpret_cast<const uint4*>(a.R + (int64_t)r * D);
-          uint32_t d = 0;
-#pragma unroll
-          for (int v = 0; v < NW / 4; ++v) d = sq4(q + 4 * v, __ldg(r4 + v), d);
-          const unsigned long long key = ((unsigned long long)d << 32) | (unsigned)r;
-          best = key < best ? key : best;
-        }
+        for (int v = 0; v < NW / 4; ++v) d = sq4(q + 4 * v, __ldg(r4 + v), d);
+        const unsigned long long key = ((unsigned long long)d << 32) | (unsigned)r;
+        best = key < best ? key : best;
       }
     };
 
@@ -666,9 +626,9 @@ cudaError_t launch_sparse(const SparseArgs& a, int C, int shape, cudaStream_t s)
   return launch_any(a, C, shape, false, tiles, s);
 }
 
-// Persistent batched launch: as many CTAs as stay resident (2 per SM).
+// Persistent batched launch: as many CTAs as stay resident.
 cudaError_t launch_sparse_batch(const SparseArgs& a, int C, int shape, cudaStream_t s) {
-  return launch_any(a, C, shape, true, 2 * sm_count(), s);
+  return launch_any(a, C, shape, true, kCtasPerSm * sm_count(), s);
 }
 
 }  // namespace riann
