@@ -153,6 +153,7 @@ void free_index(Index* ix) {
   cudaFree(ix->R);
   cudaFree(ix->KP);
   cudaFree(ix->Rbf);
+  cudaFree(ix->RN);
   cudaFree(ix->rnorm);
   cudaFree(ix->P);
   cudaFree(ix->TA);
@@ -366,6 +367,7 @@ int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t cha
   cudaError_t e = dalloc(&ix->R, (size_t)n * D, tot);
   if (e == cudaSuccess) e = dalloc(&ix->KP, (size_t)K * D, tot);
   if (e == cudaSuccess) e = dalloc(&ix->Rbf, (size_t)ix->n_pad * D, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->RN, (size_t)ix->n_pad * 16, tot);
   if (e == cudaSuccess) e = dalloc(&ix->rnorm, (size_t)ix->n_pad, tot);
   if (e == cudaSuccess) e = dalloc(&ix->P, (size_t)n * ix->Kp, tot);
   if (e == cudaSuccess) e = dalloc(&ix->TA, (size_t)n * K, tot);

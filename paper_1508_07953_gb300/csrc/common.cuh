@@ -75,8 +75,15 @@ struct Index {
   int n_pad = 0;                  // n rounded up to kDenseTileN
   uint8_t* R = nullptr;           // [n][D] reference patches
   uint8_t* KP = nullptr;          // [K][D] key points
-  __nv_bfloat16* Rbf = nullptr;   // [n_pad][D] bf16 copy (exact: values 0..255); pad rows zero
-  float* rnorm = nullptr;         // [n_pad] ||r||^2 (exact integers in fp32); pad rows +inf
+  // Brute-force operands (exact in bf16 / fp32).  Gray: Rbf = -2r and RN =
+  // ||r||^2 = h 2^16 + m 2^8 + l as the three terms (h 2^16, m 2^8, l) in
+  // columns 0..2 of [n_pad][16] (pad rows 2^24), in the tensor core's
+  // no-swizzle K-major order (per 8-row group 256 B: the 8 x 16-byte core
+  // matrix of columns 0..7, then that of columns 8..15).  RGB: Rbf = r and
+  // rnorm = ||r||^2 (pad rows +inf).  Pad rows of Rbf are zero.
+  __nv_bfloat16* Rbf = nullptr;   // [n_pad][D]
+  __nv_bfloat16* RN = nullptr;    // [n_pad][16] (gray)
+  float* rnorm = nullptr;         // [n_pad] (RGB)
   uint32_t* P = nullptr;          // [n][Kp] ||k_m - r||^2 (rows padded to Kp = K rounded up to 4; pad 0)
   uint32_t* TA = nullptr;         // [K][n] per key: distances ascending
   int32_t* Tid = nullptr;         // [K][n] per key: reference index of each TA entry

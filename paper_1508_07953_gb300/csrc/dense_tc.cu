@@ -2,19 +2,25 @@
 // tensor cores (tcgen05 + TMEM + TMA, sm_103a).  Used for the frame-0
 // initialisation and for queries whose rings are too wide.
 //
-// argmin_r ||q - r||^2 = argmin_r (||r||^2 - 2 q.r).  The dot products q.r are
-// one GEMM  S = Aq * R^T  with Aq [queries][D] and R [refs][D] in bf16.  uint8
-// values 0..255 are exact in bf16, every product is exact in fp32 and every
-// partial sum is a non-negative integer below 192*255^2 < 2^24, so the fp32
-// accumulation is exact and the argmin is bit-identical to integer arithmetic.
-// (INT8 MMA, tcgen05 kind::i8, is not available on sm_103a.)
+// argmin_r ||q - r||^2 = argmin_r (||r||^2 - 2 q.r), over bf16 operands that
+// hold the uint8 values exactly, with exact fp32 accumulation: every product
+// and every partial sum is an integer below 2^24 in magnitude.
+//  * gray (D = 64): one GEMM with K = D + 16,
+//      S = [q | 1 1 1 0..] . [-2r | h 2^16, m 2^8, l, 0..]   (||r||^2 = h 2^16 + m 2^8 + l),
+//    every term exact in bf16 (-2r >= -510, h <= 63, m, l <= 255) and every
+//    partial sum in [-2 * 64 * 255^2, 64 * 255^2], inside (-2^23, 2^23); the
+//    epilogue only takes the minimum of the accumulator.
+//  * RGB (D = 192): -2 q.r would reach -2.5e7 > 2^24, so the GEMM is q . r
+//    (partial sums <= 192 * 255^2 < 2^24) and the epilogue forms ||r||^2 - 2 q.r.
+// The argmin is bit-identical to integer arithmetic.  (INT8 MMA, tcgen05
+// kind::i8, is not available on sm_103a.)
 //
 // Pipeline per CTA (persistent, one CTA per SM, 12 warps):
 //   warp 0      TMA producer: one query tile (128 rows) per work item, then a
 //               ring of reference tiles (BN rows), SWIZZLE_128B layout
 //   warp 1      TMEM allocator and MMA issuer (one thread): D/16 MMAs of
-//               128 x BN x 16 per reference tile into one of two TMEM
-//               accumulators
+//               128 x BN x 16 per reference tile (gray: + 1 for the norm
+//               terms) into one of two TMEM accumulators
 //   warps 4-11  epilogue: tcgen05.ld of the accumulator (2 warps per TMEM lane
 //               quadrant, each half the columns), fused ||r||^2 - 2 q.r and a
 //               running (value, index) minimum per query row; results merge
@@ -40,22 +46,32 @@ struct Cfg;
 template <>
 struct Cfg<1> {
   static constexpr int D = 64, ATOMS = 1, BN = 256, STAGES = 4, TMEM_COLS = 512;
+  static constexpr bool FOLD = true;    // ||r||^2 added by the tensor cores
 };
 template <>
 struct Cfg<3> {
   static constexpr int D = 192, ATOMS = 3, BN = 128, STAGES = 3, TMEM_COLS = 256;
+  static constexpr bool FOLD = false;   // ||r||^2 - 2 q.r formed in the epilogue
 };
 
+// bytes of one stage's norm-term tile (BN rows x 32 B) and of the ones tile
 template <int C>
-constexpr int smem_bytes() {
+__host__ __device__ constexpr int norm_bytes() { return Cfg<C>::FOLD ? Cfg<C>::BN * 32 : 0; }
+template <int C>
+__host__ __device__ constexpr int ones_bytes() { return Cfg<C>::FOLD ? kM * 32 : 0; }
+
+template <int C>
+__host__ __device__ constexpr int smem_bytes() {
   using G = Cfg<C>;
-  return 1024 /* alignment slack */ + G::ATOMS * kM * 128 + G::STAGES * G::ATOMS * G::BN * 128 + 256;
+  return 1024 /* alignment slack */ + G::ATOMS * kM * 128 + G::STAGES * G::ATOMS * G::BN * 128 +
+         G::STAGES * norm_bytes<C>() + ones_bytes<C>() + 256;
 }
 
 struct TcArgs {
   CUtensorMap tmA;                // Aq  [rows][D] bf16, box 64 x 128
   CUtensorMap tmB;                // Rbf [n_pad][D] bf16, box 64 x BN
-  const float* rnorm;             // [n_pad]
+  const float* rnorm;             // [n_pad] ||r||^2 (RGB)
+  const __nv_bfloat16* rn;        // [n_pad][16] norm terms in core-matrix order (gray)
   const uint32_t* qnorm;          // [rows]
   const uint32_t* count;          // device count of query rows (nullptr: Qfix)
   int64_t Qfix;
@@ -139,6 +155,26 @@ __device__ __forceinline__ uint64_t sw128_desc(const void* p) {
   return d;
 }
 
+// Shared-memory matrix descriptor, no swizzle, K-major, K = 16: 8-row x
+// 16-byte core matrices, the two along K 128 B apart (leading byte offset),
+// consecutive 8-row groups 256 B apart (stride byte offset).
+__device__ __forceinline__ uint64_t plain_desc(const void* p) {
+  const uint32_t addr = smem_u32(p);
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(256 >> 4) << 32;
+  d |= (uint64_t)1 << 46;                           // descriptor version for sm_100 family
+  return d;                                         // layout 0: no swizzle
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // Instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, M x N.
 __host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
@@ -159,7 +195,13 @@ __device__ __forceinline__ void tc_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+// tcgen05.ld of N = 32 or 64 consecutive accumulator columns of this warp's
+// 32 TMEM lanes (one column per register), then wait for it.
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -171,6 +213,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<64>(uint32_t taddr, uint32_t (&v)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, "
+      "%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, "
+      "%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]), "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]), "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]), "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), "=r"(v[56]), "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Two fp32 FMAs in one instruction (sm_100 family): d = a * b + c per lane.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " mov.b64 rc, {%6, %7};\n fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
 }
 
 __device__ __forceinline__ float min3(float a, float b, float c) {
@@ -190,7 +255,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;                                        // [ATOMS][128][128 B]
   uint8_t* sB = sA + G::ATOMS * kM * 128;                    // [STAGES][ATOMS][BN][128 B]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sB + G::STAGES * G::ATOMS * G::BN * 128);
+  uint8_t* sN = sB + G::STAGES * G::ATOMS * G::BN * 128;     // gray: [STAGES][BN x 32 B] norm terms
+  uint8_t* sOnes = sN + G::STAGES * norm_bytes<C>();         // gray: [128 x 32 B] ones in columns 0..2
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sOnes + ones_bytes<C>());
   uint64_t* full = bars;
   uint64_t* empty = full + G::STAGES;
   uint64_t* tfull = empty + G::STAGES;
@@ -213,6 +280,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
   const int64_t n_items = n_qt * nsplit;
   if ((int64_t)blockIdx.x >= n_items) return;   // uniform for the whole CTA
 
+  if (G::FOLD) {
+    // A operand of the norm MMA: every query row [1 1 1 0 .. 0] (core-matrix order)
+    __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(sOnes);
+    for (int e = threadIdx.x; e < kM * 16; e += blockDim.x) {
+      const int k = ((e >> 6) & 1) * 8 + (e & 7);
+      o[e] = __float2bfloat16_rn(k < 3 ? 1.f : 0.f);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor cores
+  }
   if (threadIdx.x == 0) {
     for (int s = 0; s < G::STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -256,9 +332,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
         for (int at = 0; at < G::ATOMS; ++at) tma_load_2d(sA + at * kM * 128, &a.tmA, afull, 64 * at, qt * kM);
         for (int rt = rt0; rt < rt1; ++rt) {
           if (!(ok = mbar_wait(&empty[stage], phase ^ 1, s_abort))) break;
-          mbar_expect_tx(&full[stage], G::ATOMS * G::BN * 128);
+          mbar_expect_tx(&full[stage], G::ATOMS * G::BN * 128 + norm_bytes<C>());
           for (int at = 0; at < G::ATOMS; ++at)
             tma_load_2d(sB + (stage * G::ATOMS + at) * G::BN * 128, &a.tmB, &full[stage], 64 * at, rt * G::BN);
+          if (G::FOLD)
+            bulk_load(sN + stage * norm_bytes<C>(), a.rn + (int64_t)rt * G::BN * 16, norm_bytes<C>(), &full[stage]);
           if (++stage == G::STAGES) {
             stage = 0;
             phase ^= 1;
@@ -297,6 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
             tc_mma(d, sw128_desc(sA + at * kM * 128 + ko),
                    sw128_desc(sB + (stage * G::ATOMS + at) * G::BN * 128 + ko), IDESC, kk > 0 ? 1u : 0u);
           }
+          if (G::FOLD) tc_mma(d, plain_desc(sOnes), plain_desc(sN + stage * norm_bytes<C>()), IDESC, 1u);
           tc_commit(&empty[stage]);
           tc_commit(&tfull[acc]);
           if (++stage == G::STAGES) {
@@ -320,12 +399,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
     int acc = 0;
     uint32_t acc_phase = 0;
     bool ok = true;
+    const float2 m2 = make_float2(-2.f, -2.f);
+    constexpr int CH = HALF < 64 ? HALF : 64;   // columns per TMEM load
     for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
       const int qt = (int)(it / nsplit), part = (int)(it % nsplit);
       const int rt0 = part * per, rt1 = min(n_rt, rt0 + per);
       float bv = __int_as_float(0x7f800000);
       int bi = 0;
       for (int rt = rt0; rt < rt1; ++rt) {
+        const int colt = rt * G::BN + half * HALF;
+        // RGB: ||r||^2 of this tile's first 32 columns, fetched while the MMA runs
+        float4 rn[8];
+        if (!G::FOLD) {
+#pragma unroll
+          for (int j = 0; j < 8; ++j) rn[j] = __ldg(reinterpret_cast<const float4*>(a.rnorm + colt) + j);
+        }
         ok = mbar_wait(&tfull[acc], acc_phase, s_abort);
         if (!__all_sync(kFull, ok)) {
           ok = false;
@@ -334,34 +422,52 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
         tc_fence_after();
         const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(acc * G::BN + half * HALF);
 #pragma unroll 1
-        for (int c = 0; c < HALF; c += 32) {
-          uint32_t v[32];
-          tmem_ld32(tb + (uint32_t)c, v);
-          const int col0 = rt * G::BN + half * HALF + c;
-          const float4* rn4 = reinterpret_cast<const float4*>(a.rnorm + col0);
-          float x[32];
+        for (int c = 0; c < HALF; c += CH) {
+          uint32_t v[CH];
+          tmem_ld<CH>(tb + (uint32_t)c, v);
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float4 r = __ldg(rn4 + j);
-            x[4 * j + 0] = fmaf(-2.f, __uint_as_float(v[4 * j + 0]), r.x);
-            x[4 * j + 1] = fmaf(-2.f, __uint_as_float(v[4 * j + 1]), r.y);
-            x[4 * j + 2] = fmaf(-2.f, __uint_as_float(v[4 * j + 2]), r.z);
-            x[4 * j + 3] = fmaf(-2.f, __uint_as_float(v[4 * j + 3]), r.w);
-          }
-          float m[11];
+          for (int h32 = 0; h32 < CH / 32; ++h32) {
+            const int col0 = colt + c + 32 * h32;
+            float x[32];
+            if (G::FOLD) {
 #pragma unroll
-          for (int j = 0; j < 10; ++j) m[j] = min3(x[3 * j], x[3 * j + 1], x[3 * j + 2]);
-          m[10] = fminf(x[30], x[31]);
-          const float m0 = min3(m[0], m[1], m[2]), m1 = min3(m[3], m[4], m[5]);
-          const float m2 = min3(m[6], m[7], m[8]), m3 = fminf(m[9], m[10]);
-          const float cmin = fminf(min3(m0, m1, m2), m3);
-          if (cmin < bv) {       // rare after the first tiles: locate the lowest column
-            int jj = 31;
+              for (int j = 0; j < 32; ++j) x[j] = __uint_as_float(v[32 * h32 + j]);
+            } else {
+              // next 32 columns' norms in flight during this chunk's arithmetic
+              float4 rx[8];
+              const int cn = c + 32 * h32 + 32 < HALF ? col0 + 32 : col0;
 #pragma unroll
-            for (int j = 31; j >= 0; --j)
-              if (x[j] == cmin) jj = j;
-            bv = cmin;
-            bi = col0 + jj;
+              for (int j = 0; j < 8; ++j) rx[j] = __ldg(reinterpret_cast<const float4*>(a.rnorm + cn) + j);
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const uint32_t* w = v + 32 * h32 + 4 * j;
+                const float2 lo = fma2(make_float2(__uint_as_float(w[0]), __uint_as_float(w[1])), m2,
+                                       make_float2(rn[j].x, rn[j].y));
+                const float2 hi = fma2(make_float2(__uint_as_float(w[2]), __uint_as_float(w[3])), m2,
+                                       make_float2(rn[j].z, rn[j].w));
+                x[4 * j + 0] = lo.x;
+                x[4 * j + 1] = lo.y;
+                x[4 * j + 2] = hi.x;
+                x[4 * j + 3] = hi.y;
+              }
+#pragma unroll
+              for (int j = 0; j < 8; ++j) rn[j] = rx[j];
+            }
+            float m[11];
+#pragma unroll
+            for (int j = 0; j < 10; ++j) m[j] = min3(x[3 * j], x[3 * j + 1], x[3 * j + 2]);
+            m[10] = fminf(x[30], x[31]);
+            const float m0 = min3(m[0], m[1], m[2]), m1 = min3(m[3], m[4], m[5]);
+            const float mm2 = min3(m[6], m[7], m[8]), m3 = fminf(m[9], m[10]);
+            const float cmin = fminf(min3(m0, m1, mm2), m3);
+            if (cmin < bv) {       // rare after the first tiles: locate the lowest column
+              int jj = 31;
+#pragma unroll
+              for (int j = 31; j >= 0; --j)
+                if (x[j] == cmin) jj = j;
+              bv = cmin;
+              bi = col0 + jj;
+            }
           }
         }
         tc_fence_before();
@@ -373,7 +479,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
         }
       }
       const int64_t i = (int64_t)qt * kM + row;
-      if (ok && i < Qd && bv < __int_as_float(0x7f800000)) {
+      // padding columns score +inf (RGB) or 2^24 (gray), above every real score
+      if (ok && i < Qd && bv < 16777216.f) {
         const uint32_t dist = (uint32_t)((float)a.qnorm[i] + bv);   // exact: integer < 2^24
         atomicMin(a.best + i, ((unsigned long long)dist << 32) | (unsigned)bi);
       }
@@ -530,6 +637,7 @@ cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, Workspace& ws, cudaSt
   t.tmA = ws.tmAq;
   t.tmB = ix.tmRbf;
   t.rnorm = ix.rnorm;
+  t.rn = ix.RN;
   t.qnorm = ws.qnorm;
   t.count = d.list ? d.list_count : nullptr;
   t.Qfix = d.Q;
@@ -675,6 +783,7 @@ cudaError_t launch_exact_nn_noalloc(const DenseArgs& d, Index& ix, cudaStream_t 
   t.tmA = nd.map[k];
   t.tmB = ix.tmRbf;
   t.rnorm = ix.rnorm;
+  t.rn = ix.RN;
   t.qnorm = qnorm;
   t.count = nullptr;
   t.Qfix = d.Q;

@@ -28,26 +28,41 @@ __global__ void k_key_distances(const uint8_t* __restrict__ R, const uint8_t* __
   P[t] = s;
 }
 
-// bf16 copy of R (0..255 are exact in bf16) and ||r||^2 (exact in fp32: < 2^24).
-// Rows n..n_pad-1 are zero with norm +inf so padded columns never win an argmin.
+// Brute-force operands (layouts in common.cuh).  Gray (D = 64): Rbf = -2r
+// (even integers -510..0, exact in bf16) and RN = ||r||^2 split into three
+// terms exact in bf16 (h 2^16 with h <= 63, m 2^8 and l with m, l <= 255), so
+// one extra K = 16 MMA against a ones row adds ||r||^2 to -2 q.r in the fp32
+// accumulator.  RGB: Rbf = r and rnorm = ||r||^2 (exact in fp32: < 2^24).
+// Rows n..n_pad-1: zero vector, norm term 2^24 (gray) or +inf (RGB), above
+// every real score.
 __global__ void k_prep_refs(const uint8_t* __restrict__ R, int n, int n_pad, int D,
-                            __nv_bfloat16* __restrict__ Rbf, float* __restrict__ rnorm) {
+                            __nv_bfloat16* __restrict__ Rbf, __nv_bfloat16* __restrict__ RN,
+                            float* __restrict__ rnorm) {
   int r = blockIdx.x;
   if (r >= n_pad) return;
+  const bool fold = D == 64;
   uint32_t s = 0;
   for (int i = threadIdx.x; i < D; i += blockDim.x) {
     uint32_t v = r < n ? R[(int64_t)r * D + i] : 0u;
-    Rbf[(int64_t)r * D + i] = __float2bfloat16_rn((float)v);
+    Rbf[(int64_t)r * D + i] = __float2bfloat16_rn(fold ? -2.f * (float)v : (float)v);
     s += v * v;
   }
   __shared__ uint32_t red[32];
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 16) {
     uint32_t tot = 0;
     for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) tot += red[w];
-    rnorm[r] = r < n ? (float)tot : __int_as_float(0x7f800000);
+    const int k = threadIdx.x;
+    float t = 0.f;
+    if (r >= n) t = k == 0 ? 16777216.f : 0.f;
+    else if (k == 0) t = (float)((tot >> 16) << 16);
+    else if (k == 1) t = (float)(((tot >> 8) & 255u) << 8);
+    else if (k == 2) t = (float)(tot & 255u);
+    // core-matrix order: group r / 8 (256 B), column half k / 8 (128 B), row r % 8 (16 B)
+    RN[(int64_t)(r >> 3) * 128 + (k >> 3) * 64 + (r & 7) * 8 + (k & 7)] = __float2bfloat16_rn(t);
+    if (k == 0) rnorm[r] = r < n ? (float)tot : __int_as_float(0x7f800000);
   }
 }
 
@@ -179,7 +194,7 @@ cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
     int64_t tot = (int64_t)n * ix.Kp;
     k_key_distances<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ix.R, ix.KP, n, K, ix.Kp, D, ix.P);
   }
-  k_prep_refs<<<ix.n_pad, 64, 0, s>>>(ix.R, n, ix.n_pad, D, ix.Rbf, ix.rnorm);
+  k_prep_refs<<<ix.n_pad, 64, 0, s>>>(ix.R, n, ix.n_pad, D, ix.Rbf, ix.RN, ix.rnorm);
   int NP = kChunk;
   while (NP < n) NP <<= 1;
   unsigned long long* keys = nullptr;
