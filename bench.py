@@ -322,8 +322,11 @@ def run_batched(riann, dev, ticks: int, warm: int = 2, flush=None):
 # served form: Poisson arrivals of 480p/720p/1080p gray and RGB streams
 # ---------------------------------------------------------------------------
 def run_served(riann, dev, gray_idx, seconds: float):
-    """Same arrival trace through (a) the continuous-batching server and (b) a
-    server that runs each frame by itself; then (a) at a light load."""
+    """One arrival trace through (a) the continuous-batching server and (b) a
+    server that runs each frame by itself, both admitting streams by memory
+    and by GPU time (load limit 0.85 of measured GPU time per query); then (c)
+    the batching server admitting by memory alone, which at this arrival rate
+    is overloaded."""
     import torch
     from paper_1508_07953_gb300 import serve
     w = synth.SERVE_RGB_INDEX
@@ -333,23 +336,23 @@ def run_served(riann, dev, gray_idx, seconds: float):
     pools = {fmt: [torch.from_numpy(f).pin_memory() for f in synth.serve_frame_pool(fmt, 12, 2000 + i)]
              for i, fmt in enumerate(synth.SERVE_FORMATS)}
     params = riann.riann_default_params(65536)
+    load_limit = 0.85
     out = {"workload": "Poisson arrivals (rate 4/s, life U[5,20] s), 30 fps, 480p/720p/1080p x gray/RGB, "
                        "n=65536 refs and K=64 key points per index",
-           "budget_bytes": 4 << 30, "max_tick_queries": 48 << 20}
+           "budget_bytes": 4 << 30, "max_tick_queries": 48 << 20, "load_limit": load_limit}
 
-    def one(rate, plain):
-        spec = serve.ServeSpec(rate=rate, duration=seconds, seed=7)
+    def one(plain, limit):
+        spec = serve.ServeSpec(rate=4.0, duration=seconds, seed=7)
         srv = riann.RiannServer(gray_idx, rgb_idx, budget_bytes=4 << 30, max_tick_queries=48 << 20,
-                                max_streams=256, params=params, plain=plain)
+                                max_streams=256, params=params, plain=plain, load_limit=limit)
         try:
             return serve.run(srv, pools, spec)
         finally:
             srv.close()
 
-    out["batched"] = one(4.0, False)
-    out["plain"] = one(4.0, True)
-    out["batched_light_load"] = one(0.25, False)
-    out["light_load_rate"] = 0.25
+    out["batched"] = one(False, load_limit)
+    out["plain"] = one(True, load_limit)
+    out["batched_memory_admission_only"] = one(False, 0.0)
     rgb_idx.close()
     return out
 

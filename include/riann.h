@@ -323,9 +323,15 @@ int riann_get_tuning(riann_index_t idx, riann_tuning_t* out);
 /* ------------------------------------------------------------------------
  * Served form: continuous batching of many streams of different sizes and
  * channel counts.  Streams are admitted while their resident state
- * (riann_session_state_bytes) fits `budget_bytes` and their queries fit
- * `max_tick_queries` per index; otherwise riann_server_open returns
- * RIANN_ERR_ADMISSION (the caller may retry when streams close).  A
+ * (riann_session_state_bytes) fits `budget_bytes`, their queries fit
+ * `max_tick_queries` per index and, when `load_limit` > 0, the GPU time they
+ * claim fits: every open stream with a declared frame rate claims
+ * fps * (H-7) * (W-7) * t_q GPU seconds per second, t_q being the GPU time
+ * per query measured on its index (CUDA events around each index's part of
+ * every tick, exponentially averaged), and the claims may sum to at most
+ * `load_limit` (e.g. 0.85).  Until an index has a measurement only one
+ * rate-declaring stream of it is admitted.  Otherwise riann_server_open
+ * returns RIANN_ERR_ADMISSION (the caller may retry later).  A
  * submitted frame is copied into one of the stream's two pinned input slots;
  * a newer frame replaces one not yet dispatched (counted as dropped).
  * riann_server_step completes the tick in flight (blocking only if `wait`)
@@ -347,17 +353,22 @@ typedef struct {
   int32_t open_streams;
   size_t budget_bytes, used_bytes;
   int64_t ticks, frames_done, queries_done, rejected, submitted, dropped;
+  double load;              /* GPU seconds per second claimed by the open streams */
+  double ns_per_query[2];   /* measured GPU time per query, [0] gray, [1] RGB; 0: none yet */
 } riann_server_info_t;
 
 #define RIANN_SERVER_PLAIN 0x1   /* run each frame of a tick by itself (comparison mode) */
 
 double riann_server_clock(void);
 /* gray / rgb: indexes for 1- and 3-channel streams (either may be NULL).
- * The server keeps pointers to them; they must outlive it. */
+ * The server keeps pointers to them; they must outlive it.  load_limit <= 0:
+ * no rate admission. */
 int riann_server_create(riann_index_t gray, riann_index_t rgb, size_t budget_bytes, int64_t max_tick_queries,
-                        int32_t max_streams, const riann_params* p, int32_t flags, riann_server_t* out);
+                        int32_t max_streams, const riann_params* p, int32_t flags, double load_limit,
+                        riann_server_t* out);
 void riann_server_destroy(riann_server_t s);
-int riann_server_open(riann_server_t s, int32_t H, int32_t W, int32_t C, int32_t* stream_id);
+/* fps: the stream's declared frame rate (<= 0: claims no GPU time). */
+int riann_server_open(riann_server_t s, int32_t H, int32_t W, int32_t C, double fps, int32_t* stream_id);
 int riann_server_close(riann_server_t s, int32_t stream_id);
 /* h_frame: host uint8 [H][W][C]; copied before the call returns. */
 int riann_server_submit(riann_server_t s, int32_t stream_id, const uint8_t* h_frame, int64_t frame_id,

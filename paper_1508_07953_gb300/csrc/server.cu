@@ -2,8 +2,10 @@
 //
 // Host-side scheduler around the batched step.  Streams are admitted while
 // their resident state (two ANN fields, distances, counts and a frame buffer,
-// riann_session_state_bytes) fits a device-memory budget and their queries fit
-// the per-tick capacity of the batch contexts.  Frames are submitted into a
+// riann_session_state_bytes) fits a device-memory budget, their queries fit
+// the per-tick capacity of the batch contexts and (rate admission) the GPU
+// time they claim at their declared frame rate, priced at the measured GPU
+// time per query of their index, fits a load limit.  Frames are submitted into a
 // stream's pinned input slots (two per stream, so a frame can arrive while the
 // previous one is being copied); a newer frame replaces an undispatched older
 // one (counted as dropped).  riann_server_step completes the tick in flight
@@ -40,6 +42,7 @@ struct ServerStream {
   int64_t busy_id = -1;
   int64_t submitted = 0, dropped = 0, completed = 0;
   size_t state_bytes = 0;
+  double fps = 0;                          // declared frame rate (rate admission)
 };
 
 }  // namespace
@@ -59,6 +62,12 @@ struct riann_server_s {
   int64_t ticks = 0, frames_done = 0, queries_done = 0, rejected = 0;
   int64_t submitted = 0, dropped = 0;            // over all streams, open or closed
   bool plain = false;                            // per-frame path instead of the batched step
+  // rate admission: GPU time per query per index, measured with events
+  // around each index's part of a tick and averaged (weight 0.2 per tick)
+  double load_limit = 0;
+  double ns_q[2] = {0, 0};
+  cudaEvent_t ev[2][2] = {};
+  int64_t tick_q[2] = {0, 0};                    // queries per index in the tick in flight
   std::mutex mu;
 };
 
@@ -101,9 +110,27 @@ bool finish_tick(riann_server_s* s, bool wait) {
     ++s->frames_done;
     s->queries_done += st.Q;
   }
+  for (int k = 0; k < 2; ++k) {
+    if (s->tick_q[k] <= 0) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, s->ev[k][0], s->ev[k][1]) == cudaSuccess && ms > 0.f) {
+      const double ns = 1e6 * (double)ms / (double)s->tick_q[k];
+      s->ns_q[k] = s->ns_q[k] > 0 ? 0.8 * s->ns_q[k] + 0.2 * ns : ns;
+    }
+    cudaGetLastError();
+    s->tick_q[k] = 0;
+  }
   s->members.clear();
   s->inflight = false;
   return true;
+}
+
+// GPU seconds per second claimed by the open streams at the current estimates.
+double claimed_load(const riann_server_s* s) {
+  double l = 0;
+  for (const auto& st : s->streams)
+    if (st.open && st.fps > 0) l += st.fps * (double)st.Q * s->ns_q[chan_slot(st.C)] * 1e-9;
+  return l;
 }
 
 }  // namespace
@@ -113,7 +140,8 @@ extern "C" {
 double riann_server_clock(void) { return now_s(); }
 
 int riann_server_create(riann_index_t gray, riann_index_t rgb, size_t budget_bytes, int64_t max_tick_queries,
-                        int32_t max_streams, const riann_params* p, int32_t flags, riann_server_t* out) {
+                        int32_t max_streams, const riann_params* p, int32_t flags, double load_limit,
+                        riann_server_t* out) {
   if (!out) return RIANN_ERR_INVALID_ARG;
   *out = nullptr;
   if ((!gray && !rgb) || !p || max_streams < 1 || max_streams > 4096 || max_tick_queries < 1)
@@ -128,6 +156,7 @@ int riann_server_create(riann_index_t gray, riann_index_t rgb, size_t budget_byt
   s->budget = budget_bytes;
   s->params = *p;
   s->plain = (flags & RIANN_SERVER_PLAIN) != 0;
+  s->load_limit = load_limit;
   s->streams.resize((size_t)max_streams);
   int rc = RIANN_OK;
   for (int k = 0; k < 2 && rc == RIANN_OK; ++k) {
@@ -137,9 +166,15 @@ int riann_server_create(riann_index_t gray, riann_index_t rgb, size_t budget_byt
   }
   if (rc == RIANN_OK && cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming) != cudaSuccess)
     rc = RIANN_ERR_CUDA;
+  for (int k = 0; k < 2 && rc == RIANN_OK; ++k)
+    for (int j = 0; j < 2 && rc == RIANN_OK; ++j)
+      if (cudaEventCreate(&s->ev[k][j]) != cudaSuccess) rc = RIANN_ERR_CUDA;
   if (rc != RIANN_OK) {
     for (int k = 0; k < 2; ++k) riann_batch_destroy(s->batch[k]);
     if (s->done) cudaEventDestroy(s->done);
+    for (int k = 0; k < 2; ++k)
+      for (int j = 0; j < 2; ++j)
+        if (s->ev[k][j]) cudaEventDestroy(s->ev[k][j]);
     delete s;
     return rc;
   }
@@ -153,10 +188,13 @@ void riann_server_destroy(riann_server_t s) {
   for (auto& st : s->streams) close_stream(s, st);
   for (int k = 0; k < 2; ++k) riann_batch_destroy(s->batch[k]);
   if (s->done) cudaEventDestroy(s->done);
+  for (int k = 0; k < 2; ++k)
+    for (int j = 0; j < 2; ++j)
+      if (s->ev[k][j]) cudaEventDestroy(s->ev[k][j]);
   delete s;
 }
 
-int riann_server_open(riann_server_t s, int32_t H, int32_t W, int32_t C, int32_t* stream_id) {
+int riann_server_open(riann_server_t s, int32_t H, int32_t W, int32_t C, double fps, int32_t* stream_id) {
   if (!s || !stream_id || (C != 1 && C != 3)) return RIANN_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(s->mu);
   *stream_id = -1;
@@ -170,7 +208,16 @@ int riann_server_open(riann_server_t s, int32_t H, int32_t W, int32_t C, int32_t
       slot = (int)i;
       break;
     }
-  if (slot < 0 || s->used + (size_t)bytes > s->budget || s->open_q[k] + Q > s->cap_q[k]) {
+  bool fits = slot >= 0 && s->used + (size_t)bytes <= s->budget && s->open_q[k] + Q <= s->cap_q[k];
+  if (fits && s->load_limit > 0 && fps > 0) {
+    if (s->ns_q[k] > 0) {
+      fits = claimed_load(s) + fps * (double)Q * s->ns_q[k] * 1e-9 <= s->load_limit;
+    } else {   // no measurement yet: one rate-declaring stream per index until there is
+      for (const auto& o : s->streams)
+        if (o.open && o.fps > 0 && chan_slot(o.C) == k) fits = false;
+    }
+  }
+  if (!fits) {
     ++s->rejected;
     return RIANN_ERR_ADMISSION;
   }
@@ -194,6 +241,7 @@ int riann_server_open(riann_server_t s, int32_t H, int32_t W, int32_t C, int32_t
     return rc;
   }
   st.open = true;
+  st.fps = fps;
   st.state_bytes = (size_t)bytes;
   s->used += st.state_bytes;
   s->open_q[k] += Q;
@@ -259,16 +307,22 @@ int riann_server_step(riann_server_t s, riann_stream_t stream, int32_t wait, int
   if (s->members.empty()) return RIANN_OK;
   for (int k = 0; k < 2; ++k) {
     if (sess[k].empty()) continue;
+    int64_t q = 0;
+    for (int id : s->members)
+      if (chan_slot(s->streams[id].C) == k) q += s->streams[id].Q;
+    s->tick_q[k] = q;
+    if (cudaEventRecord(s->ev[k][0], cs) != cudaSuccess) return RIANN_ERR_CUDA;
     if (s->plain) {
       for (size_t i = 0; i < sess[k].size(); ++i) {
         const int rc = riann_session_frame(sess[k][i], &s->params, stream, frames[k][i], nullptr, nullptr, nullptr);
         if (rc) return rc;
       }
-      continue;
+    } else {
+      const int rc = riann_batch_run(s->batch[k], &s->params, stream, sess[k].data(), frames[k].data(),
+                                     (int32_t)sess[k].size());
+      if (rc) return rc;
     }
-    const int rc = riann_batch_run(s->batch[k], &s->params, stream, sess[k].data(), frames[k].data(),
-                                   (int32_t)sess[k].size());
-    if (rc) return rc;
+    if (cudaEventRecord(s->ev[k][1], cs) != cudaSuccess) return RIANN_ERR_CUDA;
   }
   for (int id : s->members) {
     ServerStream& st = s->streams[id];
@@ -319,6 +373,9 @@ int riann_server_info(riann_server_t s, riann_server_info_t* out) {
   out->frames_done = s->frames_done;
   out->queries_done = s->queries_done;
   out->rejected = s->rejected;
+  out->load = claimed_load(s);
+  out->ns_per_query[0] = s->ns_q[0];
+  out->ns_per_query[1] = s->ns_q[1];
   return RIANN_OK;
 }
 

@@ -123,10 +123,10 @@ _lib.riann_set_tuning.argtypes = [_P, ctypes.POINTER(riann_tuning_t)]
 _lib.riann_get_tuning.argtypes = [_P, ctypes.POINTER(riann_tuning_t)]
 _lib.riann_server_clock.restype = ctypes.c_double
 _lib.riann_server_create.argtypes = [_P, _P, ctypes.c_size_t, _i64, _i32, ctypes.POINTER(riann_params), _i32,
-                                     ctypes.POINTER(_P)]
+                                     ctypes.c_double, ctypes.POINTER(_P)]
 _lib.riann_server_destroy.argtypes = [_P]
 _lib.riann_server_destroy.restype = None
-_lib.riann_server_open.argtypes = [_P, _i32, _i32, _i32, ctypes.POINTER(_i32)]
+_lib.riann_server_open.argtypes = [_P, _i32, _i32, _i32, ctypes.c_double, ctypes.POINTER(_i32)]
 _lib.riann_server_close.argtypes = [_P, _i32]
 _lib.riann_server_submit.argtypes = [_P, _i32, _P, _i64, ctypes.c_double]
 _lib.riann_server_step.argtypes = [_P, _P, _i32, ctypes.POINTER(_i32)]
@@ -546,10 +546,13 @@ class riann_server_info_t(ctypes.Structure):
     _fields_ = [("open_streams", ctypes.c_int32), ("budget_bytes", ctypes.c_size_t),
                 ("used_bytes", ctypes.c_size_t), ("ticks", ctypes.c_int64), ("frames_done", ctypes.c_int64),
                 ("queries_done", ctypes.c_int64), ("rejected", ctypes.c_int64), ("submitted", ctypes.c_int64),
-                ("dropped", ctypes.c_int64)]
+                ("dropped", ctypes.c_int64), ("load", ctypes.c_double), ("ns_per_query", ctypes.c_double * 2)]
 
     def as_dict(self):
-        return {k: int(getattr(self, k)) for k, _ in self._fields_}
+        d = {k: int(getattr(self, k)) for k, _ in self._fields_[:9]}
+        d["load"] = float(self.load)
+        d["ns_per_query"] = [float(x) for x in self.ns_per_query]
+        return d
 
 
 _lib.riann_server_poll.argtypes = [_P, ctypes.POINTER(riann_server_result_t), _i32, ctypes.POINTER(_i32)]
@@ -562,20 +565,22 @@ def riann_server_clock() -> float:
 
 class RiannServer:
     def __init__(self, gray: Optional[RiannIndex], rgb: Optional[RiannIndex], budget_bytes: int,
-                 max_tick_queries: int, max_streams: int, params: riann_params, plain: bool = False):
+                 max_tick_queries: int, max_streams: int, params: riann_params, plain: bool = False,
+                 load_limit: float = 0.0):
         h = ctypes.c_void_p(0)
         _check(_lib.riann_server_create(gray.handle if gray else None, rgb.handle if rgb else None,
                                         int(budget_bytes), int(max_tick_queries), int(max_streams),
                                         ctypes.byref(params), RIANN_SERVER_PLAIN if plain else 0,
-                                        ctypes.byref(h)), "riann_server_create")
+                                        float(load_limit), ctypes.byref(h)), "riann_server_create")
         self.handle = h
         self.indexes = (gray, rgb)
         self._res = (riann_server_result_t * 1024)()
 
-    def open(self, H: int, W: int, C: int) -> Optional[int]:
-        """Admit a stream; None when the budget or the tick capacity is full."""
+    def open(self, H: int, W: int, C: int, fps: float = 0.0) -> Optional[int]:
+        """Admit a stream; None when the memory budget, the tick capacity or
+        (with a load limit and fps > 0) the GPU-time budget is full."""
         sid = ctypes.c_int32(-1)
-        rc = _lib.riann_server_open(self.handle, int(H), int(W), int(C), ctypes.byref(sid))
+        rc = _lib.riann_server_open(self.handle, int(H), int(W), int(C), float(fps), ctypes.byref(sid))
         if rc == RIANN_ERR_ADMISSION:
             return None
         _check(rc, "riann_server_open")

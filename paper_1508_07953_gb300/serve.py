@@ -3,7 +3,9 @@
 Streams arrive as a Poisson process, live for a uniformly drawn time and send
 frames at a fixed rate; each frame's arrival time is its nominal capture time.
 The server (C++ core, ``riann_server_*``) admits streams while their resident
-state fits its device-memory budget; every step completes the tick in flight
+state fits its device-memory budget and, when it has a load limit, while the
+GPU time they claim at their frame rate fits it (a rejected stream retries
+until its lifetime would have ended); every step completes the tick in flight
 and batches every stream's newest pending frame into the next one.  Frames
 that a stream sends faster than the GPU finishes them are replaced by newer
 ones (counted as dropped), as a live pipeline would do.  Frame latency =
@@ -82,7 +84,7 @@ def run(server, pools: Dict[Tuple[int, int, int], list], spec: ServeSpec, trace:
             ai += 1
         keep = []
         for a in waiting:
-            sid = server.open(*a.fmt)
+            sid = server.open(*a.fmt, fps=spec.fps)
             if sid is None:
                 if now < a.t + a.life:
                     keep.append(a)          # retry while the stream would still be alive
@@ -123,6 +125,7 @@ def run(server, pools: Dict[Tuple[int, int, int], list], spec: ServeSpec, trace:
         "latency_ms_p50": 1e3 * percentile(lat, 50), "latency_ms_p99": 1e3 * percentile(lat, 99),
         "latency_ms_p50_by_format": {k: 1e3 * percentile(v, 50) for k, v in sorted(per_fmt_lat.items())},
         "queries_per_s": info["queries_done"] / max(wall, 1e-9), "wall_s": wall,
+        "ns_per_query_measured": info["ns_per_query"],
         "ticks": info["ticks"], "stream_seconds": stream_seconds,
         "fps_per_stream": frames / max(stream_seconds, 1e-9),
     }

@@ -108,3 +108,33 @@ def test_admission_budget_and_replacement(rt, indexes):
     info = srv.info()
     assert info["dropped"] == 1 and info["rejected"] == 1
     srv.close()
+
+
+def test_rate_admission(rt, indexes):
+    """With a load limit, a stream that declares a frame rate claims
+    fps * queries * (measured GPU time per query); claims must fit the limit."""
+    params = rt.riann_default_params(3000)
+    idx = indexes[1][0]
+    srv = rt.RiannServer(idx, None, budget_bytes=1 << 30, max_tick_queries=1 << 20, max_streams=8,
+                         params=params, load_limit=0.5)
+    a = srv.open(64, 64, 1, fps=30.0)
+    assert a is not None                                    # no measurement yet: the first one enters
+    assert srv.open(64, 64, 1, fps=30.0) is None            # ... and only the first
+    free = srv.open(64, 64, 1)                              # declares no rate: memory budget only
+    assert free is not None
+    v = synth.Video(synth.VideoSpec(64, 64, 1, 91))
+    for t in range(3):
+        srv.submit(a, v.frame(t), t, 0.0)
+        srv.step(wait=True)
+        srv.step(wait=True)
+    info = srv.info()
+    ns = info["ns_per_query"][0]
+    assert ns > 0 and info["ns_per_query"][1] == 0
+    q = 57 * 57
+    assert abs(info["load"] - 30.0 * q * ns * 1e-9) <= 1e-9 + 1e-6 * info["load"]
+    # a stream whose claim alone exceeds the limit is rejected, a small one fits
+    huge_fps = 2.0 * 0.5 / (q * ns * 1e-9)
+    assert srv.open(64, 64, 1, fps=huge_fps) is None
+    assert srv.open(64, 64, 1, fps=1.0) is not None
+    assert srv.info()["rejected"] == 2
+    srv.close()
