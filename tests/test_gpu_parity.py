@@ -164,6 +164,7 @@ def test_cap_does_not_change_output(rt, tiny):
     (257, 17, 3, 15, 100),    # RGB, odd K
     (2049, 5, 1, 8, 300),     # one query row
     (3000, 32, 3, 70, 9),     # one query column pair
+    (6001, 64, 1, 24, 90),    # n not a multiple of 4 with K = 64: long seed runs, many drains
 ])
 @pytest.mark.parametrize("alpha,limit", [((1, 4), -1), ((1, 2), 40), ((8, 1), -1)])
 def test_random_cases(rt, n, K, C, H, W, alpha, limit):
