@@ -185,7 +185,7 @@ constexpr int kRowBatch = 4;  // 16-byte words of a distance row loaded per roun
 // persistent grid whose CTAs take tiles of all the batch's frames from an
 // atomic counter, in the order of the items.
 template <int C, int SHAPE, bool BATCH>
-__global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const SparseArgs a) {
+__global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid_constant__ SparseArgs a) {
   constexpr int TY = SHAPE == kTile4x32 ? 4 : 8;
   constexpr int TX = SHAPE == kTile4x32 ? 32 : 16;
   constexpr int D = 64 * C, NW = D / 4;
@@ -209,6 +209,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const Sparse
   __shared__ __align__(16) uint32_t s_q[kWarps][NW];   // the warp's query patch
   __shared__ int32_t s_dense[TY * TX];
   __shared__ int s_next, s_ndense, s_dense_base, s_tile_id;
+  __shared__ FrameItem s_item;                    // batched launch: the current tile's frame
   __shared__ unsigned long long s_stat[3];        // ring-answered queries, scanned entries, sum of |S|
 
   const int K = a.K, n = a.n, G = a.G;
@@ -224,27 +225,31 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const Sparse
   const uint32_t Amax = max_sqdist(D);
 
   for (int round = 0;; ++round) {
-  // ---- the next tile and its frame ----
-  FrameItem it;
-  int tile;
+  // ---- the next tile and its frame (kept in shared memory or read from the
+  // kernel parameters, not copied into registers) ----
   if (BATCH) {
     __syncthreads();   // the previous tile's shared state is no longer read
-    if (threadIdx.x == 0) s_tile_id = (int)atomicAdd(a.counters + 1, 1u);
-    __syncthreads();
-    const int tg = s_tile_id;
-    if (tg >= a.hdr->total_tiles) break;
-    int lo = 0, hi = a.hdr->n_items - 1;   // last item with tile_begin <= tg
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (a.items[mid].tile_begin <= tg) lo = mid; else hi = mid - 1;
+    if (threadIdx.x == 0) {
+      const int tg = (int)atomicAdd(a.counters + 1, 1u);
+      int t = -1;
+      if (tg < a.hdr->total_tiles) {
+        int lo = 0, hi = a.hdr->n_items - 1;   // last item with tile_begin <= tg
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (a.items[mid].tile_begin <= tg) lo = mid; else hi = mid - 1;
+        }
+        s_item = a.items[lo];
+        t = tg - s_item.tile_begin;
+      }
+      s_tile_id = t;
     }
-    it = a.items[lo];
-    tile = tg - it.tile_begin;
-  } else {
-    if (round > 0) break;
-    it = a.one;
-    tile = blockIdx.x;
+    __syncthreads();
+    if (s_tile_id < 0) break;
+  } else if (round > 0) {
+    break;
   }
+  const FrameItem& it = BATCH ? s_item : a.one;
+  const int tile = BATCH ? s_tile_id : (int)blockIdx.x;
   const int ty0 = (tile / it.tiles_x) * TY;
   const int tx0 = (tile % it.tiles_x) * TX;
   {
