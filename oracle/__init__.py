@@ -58,6 +58,7 @@ def _load():
                                                       i32, i32, i32, P, i64, P, P, P, P]
             lib.oracle_riann_indexed.argtypes = [P, i32, i32, i32, P, i32, P, i32, P, P, P, P,
                                                  i32, i32, i32, P, i64, P, P, P, P]
+            lib.oracle_reconstruct.argtypes = [P, i32, i32, P, i32, i32, P, P, P]
             lib.oracle_num_threads.restype = ctypes.c_int
             lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -77,7 +78,7 @@ class use_library:
         self._saved = _lib
         lib = ctypes.CDLL(self.path)
         for name in ("oracle_ring_member", "oracle_key_distances", "oracle_sort_tables", "oracle_exact_nn",
-                     "oracle_riann_definitional", "oracle_riann_indexed", "oracle_num_threads",
+                     "oracle_riann_definitional", "oracle_riann_indexed", "oracle_reconstruct", "oracle_num_threads",
                      "oracle_set_num_threads"):
             f, g = getattr(self._saved, name), getattr(lib, name)
             g.argtypes, g.restype = f.argtypes, f.restype
@@ -184,3 +185,23 @@ def riann_frame(index: Index, frame: np.ndarray, prev: Optional[np.ndarray],
     else:
         raise ValueError(mode)
     return annf, dist, count, nseed
+
+
+def reconstruct(R: np.ndarray, annf: np.ndarray, frame: Optional[np.ndarray] = None):
+    """Sec. 4 reconstruction of a frame from its field: (out uint8 [H][W][C],
+    err2 = (sum (f_GT - f_R)^2, sum f_GT^2) or None).  R: [n][8][8][C] or
+    [n][D]; annf: [H-7][W-7]; frame: [H][W] or [H][W][C] (its shape gives H, W)."""
+    lib = _load()
+    Rr = _c(R, np.uint8).reshape(R.shape[0], -1)
+    n, D = Rr.shape
+    C = D // 64
+    a = _c(annf, np.int32)
+    H, W = a.shape[0] + 7, a.shape[1] + 7
+    f = None if frame is None else _frame3(frame)
+    if f is not None:
+        assert f.shape == (H, W, C)
+    out = np.empty((H, W, C), np.uint8)
+    err2 = np.zeros(2, np.uint64) if f is not None else None
+    lib.oracle_reconstruct(_ptr(Rr), n, C, _ptr(a), H, W, _ptr(f), _ptr(out), _ptr(err2))
+    return out, (None if err2 is None else (int(err2[0]), int(err2[1])))
+

@@ -334,3 +334,39 @@ void oracle_riann_indexed(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
     free(B); free(lo); free(hi);
   }
 }
+
+/* Sec. 4 reconstruction, written as its definition: for every output pixel,
+ * the query patches that cover it are those with top-left corner
+ * y-7 <= py <= y and x-7 <= px <= x inside the query grid. */
+void oracle_reconstruct(const uint8_t* R, int32_t n, int32_t C, const int32_t* annf, int32_t H, int32_t W,
+                        const uint8_t* frame, uint8_t* out, unsigned long long* err2) {
+  const int32_t Hq = H - 7, Wq = W - 7, D = 64 * C;
+  unsigned long long e = 0, g = 0;
+  for (int32_t y = 0; y < H; ++y) {
+    for (int32_t x = 0; x < W; ++x) {
+      for (int32_t c = 0; c < C; ++c) {
+        uint64_t sum = 0, count = 0;
+        for (int32_t py = (y - 7 > 0 ? y - 7 : 0); py <= y && py < Hq; ++py) {
+          for (int32_t px = (x - 7 > 0 ? x - 7 : 0); px <= x && px < Wq; ++px) {
+            const int32_t r = annf[(int64_t)py * Wq + px];
+            if (r < 0 || r >= n) continue;
+            sum += R[(int64_t)r * D + ((int64_t)(y - py) * 8 + (x - px)) * C + c];
+            ++count;
+          }
+        }
+        const uint32_t v = count ? (uint32_t)((2 * sum + count) / (2 * count)) : 0u;
+        const int64_t o = ((int64_t)y * W + x) * C + c;
+        if (out) out[o] = (uint8_t)v;
+        if (frame) {
+          const int64_t d = (int64_t)frame[o] - (int64_t)v;
+          e += (unsigned long long)(d * d);
+          g += (unsigned long long)frame[o] * frame[o];
+        }
+      }
+    }
+  }
+  if (err2) {
+    err2[0] = e;
+    err2[1] = g;
+  }
+}

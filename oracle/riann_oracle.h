@@ -76,6 +76,18 @@ void oracle_riann_indexed(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
                           const int64_t* qidx, int64_t nq,
                           int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* nseed);
 
+/* Reconstruction by patch replacement (Sec. 4: "replacing each patch with
+ * its match and averaging overlapping patches").  out[y][x][c] = rounded
+ * average over the query patches (py, px) that cover (y, x) -- py <= y < py+8,
+ * px <= x < px+8, inside the query grid, with annf[py][px] in [0, n) -- of
+ * byte (y-py, x-px, c) of their matched reference patch.  Reading taken here:
+ * the average is rounded half up to 8 bits, (2*sum + count) / (2*count) in
+ * integers (0 where no valid patch covers the pixel).  frame / err2 nullable:
+ * err2[0] = sum over all bytes of (frame - out)^2, err2[1] = sum of frame^2,
+ * so that the paper's error E = ||f_GT - f_R|| / ||f_GT|| = sqrt(err2[0] / err2[1]). */
+void oracle_reconstruct(const uint8_t* R, int32_t n, int32_t C, const int32_t* annf, int32_t H, int32_t W,
+                        const uint8_t* frame, uint8_t* out, unsigned long long* err2);
+
 /* Number of OpenMP threads the oracle uses (1 when built without OpenMP). */
 int oracle_num_threads(void);
 void oracle_set_num_threads(int n);

@@ -14,6 +14,7 @@ import pytest
 import oracle
 import synth
 import test_oracle_pins as pins
+import test_oracle_reconstruct as rpins
 
 SRC = os.path.join(os.path.dirname(os.path.abspath(oracle.__file__)), "riann_oracle.c")
 
@@ -35,6 +36,11 @@ MUTANTS = {
                               "        in_all[r] = (uint8_t)inside;\n        s_size += (uint32_t)oracle_ring_member(P[(int64_t)r * K], B[0], Cd, alpha_num, alpha_den);"),
     "alpha_inverted": ("__int128 L = qq * ((__int128)A + (__int128)B) - (__int128)p * p * (__int128)C;",
                        "__int128 L = (__int128)p * p * ((__int128)A + (__int128)B) - qq * (__int128)C;"),
+    # Sec. 4 reconstruction
+    "recon_truncating_average": ("(uint32_t)((2 * sum + count) / (2 * count))", "(uint32_t)(sum / count)"),
+    "recon_patch_offset_transposed": ("((int64_t)(y - py) * 8 + (x - px)) * C + c", "((int64_t)(x - px) * 8 + (y - py)) * C + c"),
+    "recon_cover_misses_own_row": ("py <= y && py < Hq; ++py", "py < y && py < Hq; ++py"),
+    "recon_norm_not_squared": ("g += (unsigned long long)frame[o] * frame[o];", "g += (unsigned long long)frame[o];"),
 }
 
 
@@ -62,7 +68,10 @@ def _pins_fail() -> bool:
             pins.test_definitional_equals_indexed_random(1, a)
             pins.test_definitional_equals_indexed_random(3, a)
 
-    checks += [alpha_one, modes_agree]
+    checks += [alpha_one, modes_agree,
+               lambda: rpins.test_identity_field_reproduces_frame(23, 17, 3),
+               lambda: rpins.test_matches_scatter_formulation(13, 29, 1, 50),
+               rpins.test_constant_references_closed_form, rpins.test_golden_two_patches_round_half_up]
     for c in checks:
         try:
             c()
