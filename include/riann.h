@@ -385,6 +385,26 @@ int riann_server_info(riann_server_t s, riann_server_info_t* out);
 int riann_server_stream_counts(riann_server_t s, int32_t stream_id, int64_t* submitted, int64_t* dropped,
                                int64_t* completed);
 
+/* ------------------------------------------------------------------------
+ * Reconstruction (Sec. 4: "reconstruct the video by replacing each patch with
+ * its match and averaging overlapping patches", error
+ * E = ||f_GT - f_R||_2 / ||f_GT||_2).
+ *
+ * d_annf: device int32 [H-7][W-7], a field over this index (entries outside
+ *   [0, n) set RIANN_DEV_BAD_PREV and contribute nothing).
+ * d_out (nullable): device uint8 [H][W][C], f_R: every pixel the average of the
+ *   matched reference pixels of all query patches covering it, rounded half up
+ *   to 8 bits, (2 * sum + count) / (2 * count) in integers.
+ * d_frame (nullable): device uint8 [H][W][C], f_GT; with d_err2 it gives the
+ *   error sums.
+ * d_err2 (nullable, needs d_frame): device uint64 [2], written with
+ *   sum (f_GT - f_R)^2 and sum f_GT^2 over all bytes, so that
+ *   E = sqrt(err2[0] / err2[1]).
+ * Asynchronous on `stream`; the caller owns every buffer.
+ * ------------------------------------------------------------------------ */
+int riann_reconstruct(riann_index_t idx, riann_stream_t stream, const int32_t* d_annf, int32_t H, int32_t W,
+                      const uint8_t* d_frame, uint8_t* d_out, unsigned long long* d_err2);
+
 /* Synchronises `stream`, then returns RIANN_OK if the device status word is
  * clear, RIANN_ERR_DEVICE otherwise (and clears it); *bits (nullable) receives
  * the word. */

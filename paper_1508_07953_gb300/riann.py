@@ -134,6 +134,7 @@ _lib.riann_server_field.argtypes = [_P, _i32, _P]
 _lib.riann_server_stream_counts.argtypes = [_P, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                             ctypes.POINTER(_i64)]
 _lib.riann_status.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_uint32)]
+_lib.riann_reconstruct.argtypes = [_P, _P, _P, _i32, _i32, _P, _P, _P]
 
 
 class RiannError(RuntimeError):
@@ -262,6 +263,36 @@ def riann_annf_frame(index: RiannIndex, params: riann_params, frame: torch.Tenso
                                  _dev(out_dist, _U32, "out_dist", Q),
                                  _dev(out_count, _U32, "out_count", Q)),
            "riann_annf_frame")
+
+
+def riann_reconstruct(index: RiannIndex, annf: torch.Tensor, frame: Optional[torch.Tensor] = None,
+                      out: Optional[torch.Tensor] = None, err2: Optional[torch.Tensor] = None,
+                      stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Sec. 4 reconstruction of the frame from its field (asynchronous).
+
+    annf: int32 [H-7][W-7]; frame (f_GT, optional): uint8 [H][W](C); out
+    (optional): uint8 with the frame's element count; err2 (optional, needs
+    frame): 2 int64/uint64 elements receiving sum (f_GT - f_R)^2 and sum f_GT^2."""
+    if annf.dim() != 2:
+        raise ValueError("annf must be [H-7][W-7]")
+    H, W = annf.shape[0] + 7, annf.shape[1] + 7
+    n = H * W * index.C
+    _check(_lib.riann_reconstruct(index.handle, _stream(stream), _dev(annf, _I32, "annf", (H - 7) * (W - 7)), H, W,
+                                  _dev(frame, (torch.uint8,), "frame", n), _dev(out, (torch.uint8,), "out", n),
+                                  _dev(err2, (torch.int64, torch.uint64), "err2", 2)),
+           "riann_reconstruct")
+
+
+def reconstruct(index: RiannIndex, annf: torch.Tensor, frame: Optional[torch.Tensor] = None):
+    """Convenience: (f_R uint8 [H][W][C] on the device, E or None); synchronises."""
+    H, W = annf.shape[0] + 7, annf.shape[1] + 7
+    out = torch.empty((H, W, index.C), dtype=torch.uint8, device=annf.device)
+    err2 = torch.zeros(2, dtype=torch.int64, device=annf.device) if frame is not None else None
+    riann_reconstruct(index, annf, frame, out, err2)
+    if err2 is None:
+        return out, None
+    e, g = (int(v) for v in err2.cpu())
+    return out, (e / g) ** 0.5 if g else 0.0
 
 
 def riann_exact_nn(index: RiannIndex, frame: torch.Tensor, out_annf: torch.Tensor,
