@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "reconstruct.cuh"
 
 namespace riann {
 

@@ -152,18 +152,6 @@ struct DenseArgs {
   unsigned long long* stats;      // nullable; a whole-frame launch records Q brute-force queries
 };
 
-// Arguments of the reconstruction kernel (Sec. 4 patch replacement).
-struct ReconArgs {
-  const int32_t* annf;            // [H-7][W-7]
-  const uint8_t* R;
-  int n;
-  int32_t H, W;
-  const uint8_t* frame;           // nullable: f_GT
-  uint8_t* out;                   // nullable: f_R
-  unsigned long long* err2;       // nullable: [2] sum (f_GT - f_R)^2, sum f_GT^2
-  uint32_t* status;
-};
-
 // Record the start/end event of a profiled kernel slot (no-op when profiling is off).
 void prof_begin(Index& ix, int slot, cudaStream_t s);
 void prof_end(Index& ix, int slot, cudaStream_t s);
@@ -182,7 +170,6 @@ cudaError_t launch_sparse(const SparseArgs& a, int C, int shape, cudaStream_t s)
 cudaError_t launch_sparse_batch(const SparseArgs& a, int C, int shape, cudaStream_t s);
 
 cudaError_t launch_index_build(Index& ix, cudaStream_t s);
-cudaError_t launch_reconstruct(const ReconArgs& a, int C, cudaStream_t s);
 
 // Workspace management (allocation synchronises the device).
 int ensure_workspace(Workspace& ws, const Index& ix, int64_t Q);

@@ -8,9 +8,12 @@
 // it.  Pixel (y, x) is covered by the patches with top-left corner
 // (y - dy, x - dx), 0 <= dy, dx < 8, inside the valid query grid; it receives
 // byte (dy, dx, c) of each such patch's match.  The average is rounded half
-// up to 8 bits in integers: (2 sum + count) / (2 count).  The gathered rows
-// (64 or 192 bytes) are reused by up to 64 pixels each, so they come from L1.
-#include "common.cuh"
+// up to 8 bits in integers: (2 sum + count) / (2 count).  Gray: the CTA also
+// stages the 585 matched rows (64 B each, padded to 68 B so that the 32
+// patches a warp reads at one (dy, dx) fall in distinct banks) with coalesced
+// loads and gathers bytes from shared memory.  RGB (192-byte rows): the
+// gathers go to global memory, where each row is reused from L1.
+#include "reconstruct.cuh"
 
 namespace riann {
 namespace {
@@ -21,7 +24,9 @@ constexpr int kPY = kTY + kPatch - 1, kPX = kTX + kPatch - 1;
 template <int C>
 __global__ void __launch_bounds__(kTY * kTX) k_reconstruct(const ReconArgs a) {
   constexpr int D = 64 * C;
+  constexpr int RW = C == 1 ? 17 : 1;            // staged row stride in words (gray)
   __shared__ int32_t s_f[kPY][kPX];               // field entries of the covering patches
+  __shared__ uint32_t s_rows[C == 1 ? kPY * kPX : 1][RW];
   __shared__ unsigned long long s_red[2][kTY * kTX / 32];
   const int H = a.H, W = a.W, Hq = H - 7, Wq = W - 7;
   const int ty0 = blockIdx.y * kTY, tx0 = blockIdx.x * kTX;
@@ -38,6 +43,15 @@ __global__ void __launch_bounds__(kTY * kTX) k_reconstruct(const ReconArgs a) {
     s_f[i / kPX][i % kPX] = r;
   }
   __syncthreads();
+  if (C == 1) {
+    const uint32_t* R32 = reinterpret_cast<const uint32_t*>(a.R);
+    for (int i = threadIdx.x; i < kPY * kPX * 16; i += blockDim.x) {
+      const int p = i >> 4, w = i & 15;
+      const int32_t r = s_f[p / kPX][p % kPX];
+      s_rows[p][w] = r >= 0 ? __ldg(R32 + (int64_t)r * 16 + w) : 0u;
+    }
+    __syncthreads();
+  }
 
   const int ly = threadIdx.x / kTX, lx = threadIdx.x % kTX;
   const int y = ty0 + ly, x = tx0 + lx;
@@ -49,11 +63,16 @@ __global__ void __launch_bounds__(kTY * kTX) k_reconstruct(const ReconArgs a) {
     for (int dy = 0; dy < kPatch; ++dy) {
 #pragma unroll
       for (int dx = 0; dx < kPatch; ++dx) {
-        const int32_t r = s_f[ly + 7 - dy][lx + 7 - dx];   // patch (y - dy, x - dx)
+        const int pr = ly + 7 - dy, pc = lx + 7 - dx;       // patch (y - dy, x - dx)
+        const int32_t r = s_f[pr][pc];
         if (r >= 0) {
-          const uint8_t* p = a.R + (int64_t)r * D + (dy * kPatch + dx) * C;
+          if (C == 1) {
+            sum[0] += (s_rows[pr * kPX + pc][dy * 2 + (dx >> 2)] >> (8 * (dx & 3))) & 0xffu;
+          } else {
+            const uint8_t* p = a.R + (int64_t)r * D + (dy * kPatch + dx) * C;
 #pragma unroll
-          for (int c = 0; c < C; ++c) sum[c] += __ldg(p + c);
+            for (int c = 0; c < C; ++c) sum[c] += __ldg(p + c);
+          }
           ++cnt;
         }
       }
