@@ -59,6 +59,10 @@ def _load():
             lib.oracle_riann_indexed.argtypes = [P, i32, i32, i32, P, i32, P, i32, P, P, P, P,
                                                  i32, i32, i32, P, i64, P, P, P, P]
             lib.oracle_reconstruct.argtypes = [P, i32, i32, P, i32, i32, P, P, P]
+            lib.oracle_philox4x32_10.argtypes = [P, P, P]
+            lib.oracle_full_tables.argtypes = [P, i32, i32, P]
+            lib.oracle_riann_anchor.argtypes = [P, i32, i32, i32, P, i32, P, P, i32, i32, i32, i32,
+                                                ctypes.c_uint64, u32, P, i64, P, P, P, P]
             lib.oracle_num_threads.restype = ctypes.c_int
             lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -78,7 +82,8 @@ class use_library:
         self._saved = _lib
         lib = ctypes.CDLL(self.path)
         for name in ("oracle_ring_member", "oracle_key_distances", "oracle_sort_tables", "oracle_exact_nn",
-                     "oracle_riann_definitional", "oracle_riann_indexed", "oracle_reconstruct", "oracle_num_threads",
+                     "oracle_riann_definitional", "oracle_riann_indexed", "oracle_reconstruct",
+                     "oracle_philox4x32_10", "oracle_full_tables", "oracle_riann_anchor", "oracle_num_threads",
                      "oracle_set_num_threads"):
             f, g = getattr(self._saved, name), getattr(lib, name)
             g.argtypes, g.restype = f.argtypes, f.restype
@@ -204,4 +209,46 @@ def reconstruct(R: np.ndarray, annf: np.ndarray, frame: Optional[np.ndarray] = N
     err2 = np.zeros(2, np.uint64) if f is not None else None
     lib.oracle_reconstruct(_ptr(Rr), n, C, _ptr(a), H, W, _ptr(f), _ptr(out), _ptr(err2))
     return out, (None if err2 is None else (int(err2[0]), int(err2[1])))
+
+
+# ---- Alg. 1 with random anchors --------------------------------------------
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of a 4-word counter and a 2-word key -> 4 words."""
+    lib = _load()
+    c = np.asarray(ctr, np.uint32).copy()
+    k = np.asarray(key, np.uint32).copy()
+    out = np.zeros(4, np.uint32)
+    lib.oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return [int(v) for v in out]
+
+
+class FullIndex:
+    """Reference set with the sorted distance matrix of Sec. 3.4:
+    T[i][j] = (||r_i - r_id||^2 << 32) | id, each row ascending."""
+
+    def __init__(self, R: np.ndarray):
+        lib = _load()
+        self.R = _c(R, np.uint8).reshape(R.shape[0], -1)
+        self.n, self.D = self.R.shape
+        self.C = self.D // 64
+        self.T = np.empty((self.n, self.n), np.uint64)
+        lib.oracle_full_tables(_ptr(self.R), self.n, self.D, _ptr(self.T))
+
+
+def riann_anchor_frame(index: FullIndex, frame: np.ndarray, prev: Optional[np.ndarray], alpha=(1, 4),
+                       L: int = 20, max_rings: int = 64, seed: int = 0, frame_id: int = 0, qidx=None):
+    """Alg. 1 with random anchors: (annf, dist, count, rings); see riann_oracle.h
+    for the readings (anchor draw, ring test, final argmin)."""
+    lib = _load()
+    f = _frame3(frame)
+    H, W, C = f.shape
+    assert C == index.C
+    q = None if qidx is None else _c(qidx, np.int64)
+    pv = None if prev is None else _c(prev, np.int32)
+    annf, dist, count, rings = _outputs(f, q)
+    nq = 0 if q is None else len(q)
+    lib.oracle_riann_anchor(_ptr(f), H, W, C, _ptr(index.R), index.n, _ptr(index.T), _ptr(pv),
+                            alpha[0], alpha[1], L, max_rings, seed & ((1 << 64) - 1), frame_id & 0xffffffff,
+                            _ptr(q), nq, _ptr(annf), _ptr(dist), _ptr(count), _ptr(rings))
+    return annf, dist, count, rings
 

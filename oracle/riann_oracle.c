@@ -370,3 +370,119 @@ void oracle_reconstruct(const uint8_t* R, int32_t n, int32_t C, const int32_t* a
     err2[1] = g;
   }
 }
+
+/* ---- Alg. 1 with random anchors ------------------------------------------ */
+
+/* Philox4x32-10 as published: ten rounds of two 32x32->64-bit products with
+ * the multipliers 0xD2511F53 and 0xCD9E8D57, the key bumped by the Weyl
+ * constants 0x9E3779B9 and 0xBB67AE85 between rounds. */
+void oracle_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n1 = lo1, n2 = hi0 ^ c3 ^ k1, n3 = lo0;
+    c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+static int cmp_u64(const void* x, const void* y) {
+  const uint64_t u = *(const uint64_t*)x, v = *(const uint64_t*)y;
+  return u < v ? -1 : (u > v ? 1 : 0);
+}
+
+/* Sec. 3.4: "calculate the pairwise distance matrix and sort it". */
+void oracle_full_tables(const uint8_t* R, int32_t n, int32_t D, uint64_t* T) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int32_t i = 0; i < n; ++i) {
+    uint64_t* row = T + (int64_t)i * n;
+    for (int32_t j = 0; j < n; ++j)
+      row[j] = ((uint64_t)sqdist(R + (int64_t)i * D, R + (int64_t)j * D, D) << 32) | (uint32_t)j;
+    qsort(row, (size_t)n, sizeof(uint64_t), cmp_u64);
+  }
+}
+
+/* r in the ring of the anchor: (1 - a) d <= dist(anchor, r) <= (1 + a) d with
+ * d = dist(q, anchor), a = p/q, squared: A = ||anchor - r||^2, B = ||q - anchor||^2 */
+static int anchor_ring_member(uint32_t A, uint32_t B, int32_t p, int32_t q) {
+  const uint64_t qq = (uint64_t)q * (uint64_t)q;
+  if (p < q) {
+    const uint64_t lo = (uint64_t)(q - p) * (uint64_t)(q - p);
+    if (lo * B > qq * A) return 0;
+  }
+  const uint64_t hi = (uint64_t)(q + p) * (uint64_t)(q + p);
+  return qq * A <= hi * B;
+}
+
+void oracle_riann_anchor(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                         const uint8_t* R, int32_t n, const uint64_t* T, const int32_t* prev,
+                         int32_t alpha_num, int32_t alpha_den, int32_t L, int32_t max_rings,
+                         uint64_t seed, uint32_t frame_id,
+                         const int64_t* qidx, int64_t nq,
+                         int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* rings) {
+  const int32_t D = 64 * C, Wq = W - 7;
+  const int64_t Q = (int64_t)(H - 7) * Wq;
+  const int64_t NQ = qidx ? nq : Q;
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel
+  {
+    uint8_t q[192];
+    int32_t* S = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t* S2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)n);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < NQ; ++i) {
+      const int64_t qi = query_at(qidx, i);
+      extract_query(frame, W, C, (int32_t)(qi / Wq), (int32_t)(qi % Wq), q);
+      if (!prev) {
+        int32_t bi; uint32_t bd;
+        brute_force(q, R, n, D, &bi, &bd);
+        annf[i] = bi;
+        if (dist) dist[i] = bd;
+        if (count) count[i] = (uint32_t)n;
+        if (rings) rings[i] = 0;
+        continue;
+      }
+      const int32_t ri = prev[qi];
+      const uint32_t Bi = sqdist(q, R + (int64_t)ri * D, D);
+      int32_t bi = ri;                      /* best so far: r_i, then the anchors, then S */
+      uint32_t bd = Bi;
+      /* S_0: the ring of r_i, in row r_i of the sorted matrix */
+      int32_t ns = 0;
+      const uint64_t* row = T + (int64_t)ri * n;
+      for (int32_t j = 0; j < n; ++j)
+        if (anchor_ring_member((uint32_t)(row[j] >> 32), Bi, alpha_num, alpha_den)) S[ns++] = (int32_t)(uint32_t)row[j];
+      uint32_t t = 0;
+      while (ns >= L && (int32_t)t < max_rings) {
+        const uint32_t ctr[4] = {(uint32_t)qi, t, frame_id, 0u};
+        uint32_t x[4];
+        oracle_philox4x32_10(ctr, key, x);
+        const int32_t a = S[(int32_t)(((uint64_t)x[0] * (uint64_t)ns) >> 32)];
+        const uint32_t Ba = sqdist(q, R + (int64_t)a * D, D);
+        if (Ba < bd || (Ba == bd && a < bi)) { bd = Ba; bi = a; }
+        int32_t m = 0;
+        for (int32_t k = 0; k < ns; ++k) {
+          const uint32_t A = sqdist(R + (int64_t)a * D, R + (int64_t)S[k] * D, D);
+          if (anchor_ring_member(A, Ba, alpha_num, alpha_den)) S2[m++] = S[k];
+        }
+        int32_t* tmp = S; S = S2; S2 = tmp;
+        ns = m;
+        ++t;
+      }
+      for (int32_t k = 0; k < ns; ++k) {
+        const uint32_t d = sqdist(q, R + (int64_t)S[k] * D, D);
+        if (d < bd || (d == bd && S[k] < bi)) { bd = d; bi = S[k]; }
+      }
+      annf[i] = bi;
+      if (dist) dist[i] = bd;
+      if (count) count[i] = (uint32_t)ns;
+      if (rings) rings[i] = t;
+    }
+    free(S); free(S2);
+  }
+}

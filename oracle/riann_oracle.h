@@ -88,6 +88,38 @@ void oracle_riann_indexed(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
 void oracle_reconstruct(const uint8_t* R, int32_t n, int32_t C, const int32_t* annf, int32_t H, int32_t W,
                         const uint8_t* frame, uint8_t* out, unsigned long long* err2);
 
+/* ---- Alg. 1 with random anchors (the paper's own loop) ----------------- */
+
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy
+ * as 1, 2, 3", SC'11): counter ctr[4] and key key[2] -> out[4]. */
+void oracle_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
+
+/* Sec. 3.3 / Sec. 3.4 "sorted distance matrix": T[i*n + j] = (A << 32) | id,
+ * row i holding every reference sorted ascending by (A = ||r_i - r_id||^2, id). */
+void oracle_full_tables(const uint8_t* R, int32_t n, int32_t D, uint64_t* T);
+
+/* One frame of Alg. 1 for the queries of a frame with a previous field.
+ * Readings taken here (alpha = p/q):
+ *   ring of anchor a for query q: (1 - alpha) d_a <= dist(a, r) <= (1 + alpha) d_a
+ *     with d_a = dist(q, a) (Alg. 1: eps = alpha * d), decided exactly in integers:
+ *     (q - p)^2 ||q - a||^2 <= q^2 ||a - r||^2 (when p < q) and
+ *     q^2 ||a - r||^2 <= (q + p)^2 ||q - a||^2;
+ *   S_0 = ring of r_i = prev[q] (a range of row r_i of T), kept in that row's order;
+ *   while |S| >= L and fewer than max_rings anchors were drawn:
+ *     anchor = S[(x * |S|) >> 32], x the first word of Philox4x32-10 with
+ *     counter (query index, ring number t = 0, 1, ..., frame_id, 0) and key
+ *     (seed low word, seed high word);  S <- S n ring(anchor), order kept;
+ *   answer = argmin of dist(q, r) over S u {r_i} u {anchors drawn}, lower index
+ *     on ties (every one of them had its distance computed);
+ *   count = |S| at the end, rings = anchors drawn.
+ * prev == NULL: brute force (count = n, rings = 0). */
+void oracle_riann_anchor(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                         const uint8_t* R, int32_t n, const uint64_t* T, const int32_t* prev,
+                         int32_t alpha_num, int32_t alpha_den, int32_t L, int32_t max_rings,
+                         uint64_t seed, uint32_t frame_id,
+                         const int64_t* qidx, int64_t nq,
+                         int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* rings);
+
 /* Number of OpenMP threads the oracle uses (1 when built without OpenMP). */
 int oracle_num_threads(void);
 void oracle_set_num_threads(int n);

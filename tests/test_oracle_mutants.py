@@ -15,6 +15,7 @@ import oracle
 import synth
 import test_oracle_pins as pins
 import test_oracle_reconstruct as rpins
+import test_oracle_anchor as apins
 
 SRC = os.path.join(os.path.dirname(os.path.abspath(oracle.__file__)), "riann_oracle.c")
 
@@ -41,6 +42,13 @@ MUTANTS = {
     "recon_patch_offset_transposed": ("((int64_t)(y - py) * 8 + (x - px)) * C + c", "((int64_t)(x - px) * 8 + (y - py)) * C + c"),
     "recon_cover_misses_own_row": ("py <= y && py < Hq; ++py", "py < y && py < Hq; ++py"),
     "recon_norm_not_squared": ("g += (unsigned long long)frame[o] * frame[o];", "g += (unsigned long long)frame[o];"),
+    # Alg. 1 with random anchors
+    "anchor_ring_width_of_first_ring": ("if (anchor_ring_member(A, Ba, alpha_num, alpha_den)) S2[m++] = S[k];",
+                                        "if (anchor_ring_member(A, Bi, alpha_num, alpha_den)) S2[m++] = S[k];"),
+    "anchor_not_verified": ("if (Ba < bd || (Ba == bd && a < bi)) { bd = Ba; bi = a; }", ""),
+    "anchor_draw_modulo": ("S[(int32_t)(((uint64_t)x[0] * (uint64_t)ns) >> 32)]", "S[(int32_t)(x[0] % (uint32_t)ns)]"),
+    "anchor_loop_strict": ("while (ns >= L && (int32_t)t < max_rings)", "while (ns > L && (int32_t)t < max_rings)"),
+    "philox_multiplier": ("(uint64_t)0xD2511F53u * c0", "(uint64_t)0xD2511F55u * c0"),
 }
 
 
@@ -71,7 +79,11 @@ def _pins_fail() -> bool:
     checks += [alpha_one, modes_agree,
                lambda: rpins.test_identity_field_reproduces_frame(23, 17, 3),
                lambda: rpins.test_matches_scatter_formulation(13, 29, 1, 50),
-               rpins.test_constant_references_closed_form, rpins.test_golden_two_patches_round_half_up]
+               rpins.test_constant_references_closed_form, rpins.test_golden_two_patches_round_half_up,
+               apins.test_philox_known_answers, apins.test_alpha_one_is_exact_nn, apins.test_no_loop_is_first_ring_argmin,
+               apins.test_identical_references_stop_at_the_ring_cap, apins.test_golden_candidate_set_of_exactly_L,
+               lambda: apins.test_matches_independent_implementation((1, 4), 3),
+               lambda: apins.test_matches_independent_implementation((1, 2), 5)]
     for c in checks:
         try:
             c()
