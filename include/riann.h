@@ -405,6 +405,53 @@ int riann_server_stream_counts(riann_server_t s, int32_t stream_id, int64_t* sub
 int riann_reconstruct(riann_index_t idx, riann_stream_t stream, const int32_t* d_annf, int32_t H, int32_t W,
                       const uint8_t* d_frame, uint8_t* d_out, unsigned long long* d_err2);
 
+/* ------------------------------------------------------------------------
+ * Alg. 1 with random anchors, as the paper runs it (Sec. 3.2, 3.3, Alg. 1):
+ * the candidate set starts as the ring around the previous match r_i
+ * (radius d_i = dist(q, r_i), half-width alpha * d_i) and, while it holds L or
+ * more references, is intersected with the ring around an anchor drawn at
+ * random from it (radius and half-width from that anchor's distance to q);
+ * the answer is the closest of the final candidates, r_i and the anchors.
+ *
+ * The rings come from the sorted distance matrix of Sec. 3.4 (every
+ * reference's distances to all others, ascending): n^2 8-byte entries, built
+ * once by riann_full_create (34 GB for n = 65536).  Ring test, in integers,
+ * for anchor a and candidate r (alpha = p/q, B = ||q - a||^2):
+ *   (q - p)^2 B <= q^2 ||a - r||^2 (when p < q)  and  q^2 ||a - r||^2 <= (q + p)^2 B.
+ * The candidate set keeps the order of row r_i; the anchor of ring t is the
+ * candidate at position (x * |S|) >> 32, x the first output word of
+ * Philox4x32-10 with counter (query index, t, frame_id, 0) and key
+ * (seed low 32 bits, seed high 32 bits).  Ties: lower reference index.
+ * ------------------------------------------------------------------------ */
+typedef struct riann_full_s* riann_full_t;
+
+typedef struct {
+  int32_t alpha_num, alpha_den;   /* ring half-width alpha = num/den (den 1..8, num 0..8*den) */
+  int32_t L;                      /* stop below L candidates (the paper: 20); >= 1 */
+  int32_t max_rings;              /* at most this many anchors per query (0..4096) */
+  uint64_t seed;                  /* Philox key */
+  uint32_t frame_id;              /* Philox counter word: distinct per frame */
+} riann_anchor_params;
+
+/* alpha = 1/4, L = 20, max_rings = 64, seed = 0, frame_id = 0. */
+riann_anchor_params riann_default_anchor_params(void);
+
+/* Builds the sorted distance matrix of the index's references (the index
+ * must outlive the handle).  RIANN_ERR_OOM when it does not fit. */
+int riann_full_create(riann_index_t idx, riann_stream_t stream, riann_full_t* out);
+void riann_full_destroy(riann_full_t f);
+/* Row-major copy of the matrix to host memory: n * n keys
+ * (||r_i - r_id||^2 << 32) | id; synchronous. */
+int riann_full_table(riann_full_t f, riann_stream_t stream, uint64_t* host_T);
+
+/* One frame.  d_prev == NULL: brute force (count = n, rings = 0).  Outputs as
+ * riann_annf_frame plus d_out_rings (nullable): anchors drawn per query.
+ * Calls on one handle must not overlap on the GPU (they share its scratch). */
+int riann_anchor_frame(riann_full_t f, const riann_anchor_params* p, riann_stream_t stream,
+                       const uint8_t* d_frame, int32_t H, int32_t W, const int32_t* d_prev,
+                       int32_t* d_out_annf, uint32_t* d_out_dist, uint32_t* d_out_count,
+                       uint32_t* d_out_rings);
+
 /* Synchronises `stream`, then returns RIANN_OK if the device status word is
  * clear, RIANN_ERR_DEVICE otherwise (and clears it); *bits (nullable) receives
  * the word. */

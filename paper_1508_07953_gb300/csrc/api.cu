@@ -11,6 +11,7 @@
 
 #include "common.cuh"
 #include "reconstruct.cuh"
+#include "anchor.cuh"
 
 namespace riann {
 
@@ -431,6 +432,118 @@ int riann_index_tables(riann_index_t idx, riann_stream_t stream, uint32_t* P, ui
   if (e == cudaSuccess && Tid) e = cudaMemcpyAsync(Tid, idx->Tid, cnt * sizeof(int32_t), cudaMemcpyDefault, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   return from_cuda(e);
+}
+
+riann_anchor_params riann_default_anchor_params(void) {
+  riann_anchor_params p;
+  p.alpha_num = 1;
+  p.alpha_den = 4;
+  p.L = 20;
+  p.max_rings = 64;
+  p.seed = 0;
+  p.frame_id = 0;
+  return p;
+}
+
+}  // extern "C"
+
+struct riann_full_s {
+  riann_index_t idx = nullptr;
+  unsigned long long* T = nullptr;   // [n][NP]
+  int NP = 0;
+  int32_t* scratch = nullptr;        // [resident warps][2][n]
+  uint32_t* counter = nullptr;
+  size_t bytes = 0;
+};
+
+extern "C" {
+
+int riann_full_create(riann_index_t idx, riann_stream_t stream, riann_full_t* out) {
+  if (!idx || !out) return RIANN_ERR_INVALID_ARG;
+  *out = nullptr;
+  riann_full_s* f = new (std::nothrow) riann_full_s();
+  if (!f) return RIANN_ERR_OOM;
+  f->idx = idx;
+  f->NP = full_table_stride(idx->n);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = dalloc(&f->T, (size_t)idx->n * f->NP, f->bytes);
+  if (e == cudaSuccess) e = dalloc(&f->scratch, (size_t)anchor_resident_warps() * 2 * idx->n, f->bytes);
+  if (e == cudaSuccess) e = dalloc(&f->counter, 1, f->bytes);
+  if (e == cudaSuccess) e = build_full_table(*idx, f->T, f->NP, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(s);
+    cudaFree(f->T);
+    cudaFree(f->scratch);
+    cudaFree(f->counter);
+    delete f;
+    return from_cuda(e);
+  }
+  *out = f;
+  return RIANN_OK;
+}
+
+void riann_full_destroy(riann_full_t f) {
+  if (!f) return;
+  cudaDeviceSynchronize();
+  cudaFree(f->T);
+  cudaFree(f->scratch);
+  cudaFree(f->counter);
+  delete f;
+}
+
+int riann_full_table(riann_full_t f, riann_stream_t stream, uint64_t* host_T) {
+  if (!f || !host_T) return RIANN_ERR_INVALID_ARG;
+  const int n = f->idx->n;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpy2DAsync(host_T, sizeof(uint64_t) * n, f->T, sizeof(uint64_t) * f->NP,
+                                    sizeof(uint64_t) * n, (size_t)n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
+}
+
+int riann_anchor_frame(riann_full_t f, const riann_anchor_params* p, riann_stream_t stream,
+                       const uint8_t* d_frame, int32_t H, int32_t W, const int32_t* d_prev,
+                       int32_t* d_out_annf, uint32_t* d_out_dist, uint32_t* d_out_count,
+                       uint32_t* d_out_rings) {
+  if (!f || !p || !d_frame || !d_out_annf || !frame_ok(H, W) || p->alpha_den < 1 || p->alpha_den > 8 ||
+      p->alpha_num < 0 || p->alpha_num > 8 * p->alpha_den || p->L < 1 || p->max_rings < 0 || p->max_rings > 4096 ||
+      (const void*)d_prev == (const void*)d_out_annf)
+    return RIANN_ERR_INVALID_ARG;
+  Index& ix = *f->idx;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t Q = (int64_t)(H - 7) * (W - 7);
+  if (!d_prev) {   // no previous field: brute force (Alg. 1 "Initialize" read as exact NN)
+    int rc = riann_exact_nn(f->idx, stream, d_frame, H, W, d_out_annf, d_out_dist);
+    if (rc) return rc;
+    cudaError_t e = d_out_count ? launch_fill_u32(d_out_count, Q, (uint32_t)ix.n, s) : cudaSuccess;
+    if (e == cudaSuccess && d_out_rings) e = launch_fill_u32(d_out_rings, Q, 0u, s);
+    return from_cuda(e);
+  }
+  AnchorArgs a;
+  a.frame = d_frame;
+  a.H = H;
+  a.W = W;
+  a.prev = d_prev;
+  a.out_annf = d_out_annf;
+  a.out_dist = d_out_dist;
+  a.out_count = d_out_count;
+  a.out_rings = d_out_rings;
+  a.R = ix.R;
+  a.n = ix.n;
+  a.NP = f->NP;
+  a.T = f->T;
+  a.alpha_num = p->alpha_num;
+  a.alpha_den = p->alpha_den;
+  a.L = p->L;
+  a.max_rings = p->max_rings;
+  a.key0 = (uint32_t)p->seed;
+  a.key1 = (uint32_t)(p->seed >> 32);
+  a.frame_id = p->frame_id;
+  a.scratch = f->scratch;
+  a.counter = f->counter;
+  a.status = ix.status;
+  return from_cuda(launch_anchor(a, ix.C, s));
 }
 
 int riann_reconstruct(riann_index_t idx, riann_stream_t stream, const int32_t* d_annf, int32_t H, int32_t W,

@@ -188,6 +188,24 @@ __global__ void k_pack_codes(const int32_t* __restrict__ Tid, const uint8_t* __r
 
 }  // namespace
 
+// Ascending sort of nseg segments of NP keys each (NP a power of two >= 2048),
+// in batches of at most 32768 segments (the grid's y extent).
+cudaError_t sort_segments(unsigned long long* keys, int NP, int64_t nseg, cudaStream_t s) {
+  for (int64_t b0 = 0; b0 < nseg; b0 += 32768) {
+    const int nb = (int)(nseg - b0 < 32768 ? nseg - b0 : 32768);
+    unsigned long long* k0 = keys + b0 * NP;
+    k_bitonic_shared<<<dim3(NP / kChunk, nb), kChunk / 2, 0, s>>>(k0, NP, 0);
+    for (int k = 2 * kChunk; k <= NP; k <<= 1) {
+      for (int j = k >> 1; j >= kChunk; j >>= 1)
+        k_bitonic_global<<<dim3((NP / 2 + 255) / 256, nb), 256, 0, s>>>(k0, NP, k, j);
+      k_bitonic_shared<<<dim3(NP / kChunk, nb), kChunk / 2, 0, s>>>(k0, NP, k);
+    }
+  }
+  return cudaGetLastError();
+}
+
+int sort_chunk() { return kChunk; }
+
 cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
   const int n = ix.n, K = ix.K, D = ix.D;
   {

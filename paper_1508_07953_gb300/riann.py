@@ -137,6 +137,20 @@ _lib.riann_status.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_uint32)]
 _lib.riann_reconstruct.argtypes = [_P, _P, _P, _i32, _i32, _P, _P, _P]
 
 
+class riann_anchor_params(ctypes.Structure):
+    _fields_ = [("alpha_num", ctypes.c_int32), ("alpha_den", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("max_rings", ctypes.c_int32), ("seed", ctypes.c_uint64), ("frame_id", ctypes.c_uint32)]
+
+
+_lib.riann_default_anchor_params.restype = riann_anchor_params
+_lib.riann_default_anchor_params.argtypes = []
+_lib.riann_full_create.argtypes = [_P, _P, ctypes.POINTER(_P)]
+_lib.riann_full_destroy.argtypes = [_P]
+_lib.riann_full_destroy.restype = None
+_lib.riann_full_table.argtypes = [_P, _P, _P]
+_lib.riann_anchor_frame.argtypes = [_P, ctypes.POINTER(riann_anchor_params), _P, _P, _i32, _i32, _P, _P, _P, _P, _P]
+
+
 class RiannError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {_lib.riann_strerror(code).decode()} (code {code})")
@@ -293,6 +307,69 @@ def reconstruct(index: RiannIndex, annf: torch.Tensor, frame: Optional[torch.Ten
         return out, None
     e, g = (int(v) for v in err2.cpu())
     return out, (e / g) ** 0.5 if g else 0.0
+
+
+# ---------------------------------------------------------------------------
+# Alg. 1 with random anchors over the sorted distance matrix
+# ---------------------------------------------------------------------------
+def riann_default_anchor_params() -> riann_anchor_params:
+    return _lib.riann_default_anchor_params()
+
+
+class RiannFull:
+    """The sorted distance matrix of an index (n^2 8-byte keys on the device)."""
+
+    def __init__(self, index: RiannIndex, stream: Optional[torch.cuda.Stream] = None):
+        h = ctypes.c_void_p(0)
+        _check(_lib.riann_full_create(index.handle, _stream(stream), ctypes.byref(h)), "riann_full_create")
+        self.handle = h
+        self.index = index
+
+    def close(self):
+        if self.handle:
+            _lib.riann_full_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def riann_full_create(index: RiannIndex, stream=None) -> RiannFull:
+    return RiannFull(index, stream)
+
+
+def riann_full_table(full: RiannFull, stream=None):
+    """Host copy of the matrix: numpy uint64 [n][n]."""
+    import numpy as np
+    n = full.index.n
+    out = np.empty((n, n), np.uint64)
+    _check(_lib.riann_full_table(full.handle, _stream(stream), out.ctypes.data_as(ctypes.c_void_p)), "riann_full_table")
+    return out
+
+
+def riann_anchor_frame(full: RiannFull, params: riann_anchor_params, frame: torch.Tensor,
+                       prev: Optional[torch.Tensor], out_annf: torch.Tensor, out_dist=None, out_count=None,
+                       out_rings=None, stream: Optional[torch.cuda.Stream] = None) -> None:
+    H, W = _frame_dims(frame, full.index.C)
+    Q = (H - 7) * (W - 7)
+    _check(_lib.riann_anchor_frame(full.handle, ctypes.byref(params), _stream(stream),
+                                   _dev(frame, (torch.uint8,), "frame"), H, W, _dev(prev, _I32, "prev", Q),
+                                   _dev(out_annf, _I32, "out_annf", Q), _dev(out_dist, _U32, "out_dist", Q),
+                                   _dev(out_count, _U32, "out_count", Q), _dev(out_rings, _U32, "out_rings", Q)),
+           "riann_anchor_frame")
+
+
+def anchor(full: RiannFull, frame: torch.Tensor, prev: Optional[torch.Tensor], params: riann_anchor_params,
+           stream=None):
+    """Convenience: (annf, dist, count, rings) int32 tensors [H-7][W-7]."""
+    H, W = _frame_dims(frame, full.index.C)
+    shp = (H - 7, W - 7)
+    outs = [torch.empty(shp, dtype=torch.int32, device=frame.device) for _ in range(4)]
+    riann_anchor_frame(full, params, frame, prev, *outs, stream=stream)
+    return tuple(outs)
 
 
 def riann_exact_nn(index: RiannIndex, frame: torch.Tensor, out_annf: torch.Tensor,
