@@ -452,6 +452,11 @@ int riann_anchor_frame(riann_full_t f, const riann_anchor_params* p, riann_strea
                        int32_t* d_out_annf, uint32_t* d_out_dist, uint32_t* d_out_count,
                        uint32_t* d_out_rings);
 
+/* Work of the handle's last riann_anchor_frame (synchronises `stream`):
+ * out3[0] = sum of |S_0| (first-ring sizes), out3[1] = candidate tests made by
+ * the anchor rings, out3[2] = sum of the final |S|. */
+int riann_anchor_work(riann_full_t f, riann_stream_t stream, uint64_t* out3);
+
 /* Synchronises `stream`, then returns RIANN_OK if the device status word is
  * clear, RIANN_ERR_DEVICE otherwise (and clears it); *bits (nullable) receives
  * the word. */

@@ -149,6 +149,8 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
     const int lo = warp_lower_bound(row, a.n, amin << 32, lane);
     const int hi = amax >= 0xffffffffull ? a.n : warp_lower_bound(row, a.n, (amax + 1) << 32, lane);
     int ns = hi > lo ? hi - lo : 0;
+    const int ns0 = ns;
+    unsigned long long tests = 0;
     const int32_t* src = nullptr;                   // t = 0: the range of row r_i; then a scratch list
     uint32_t t = 0;
     while (ns >= a.L && (int)t < a.max_rings) {
@@ -163,6 +165,7 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
       const unsigned long long ka = ((unsigned long long)Ba << 32) | (unsigned)ra;
       best = ka < best ? ka : best;
       int32_t* dst = buf[t & 1];
+      tests += (unsigned long long)ns;
       int m = 0;
       for (int base = 0; base < ns; base += 32) {
         const int k = base + lane;
@@ -202,6 +205,11 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
       if (a.out_dist) a.out_dist[qi] = (uint32_t)(best >> 32);
       if (a.out_count) a.out_count[qi] = (uint32_t)ns;
       if (a.out_rings) a.out_rings[qi] = t;
+      if (a.work) {
+        atomicAdd(a.work, (unsigned long long)ns0);
+        atomicAdd(a.work + 1, tests);
+        atomicAdd(a.work + 2, (unsigned long long)ns);
+      }
     }
     __syncwarp();
   }
@@ -236,6 +244,7 @@ int anchor_resident_warps() { return kAnchorCtasPerSm * sm_count() * kAnchorWarp
 
 cudaError_t launch_anchor(const AnchorArgs& a, int C, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(a.counter, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess && a.work) e = cudaMemsetAsync(a.work, 0, 3 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   const int grid = kAnchorCtasPerSm * sm_count();
   if (C == 1) k_anchor<1><<<grid, kAnchorWarps * 32, 0, s>>>(a);

@@ -24,6 +24,7 @@ struct AnchorArgs {
   uint32_t key0, key1, frame_id;  // Philox4x32-10 key and the frame word of the counter
   int32_t* scratch;               // [resident warps][2][n] candidate lists
   uint32_t* counter;              // next query (zeroed before the launch)
+  unsigned long long* work;       // [3] sum |S_0|, candidate tests of the anchor rings, final |S| (zeroed)
   uint32_t* status;
 };
 

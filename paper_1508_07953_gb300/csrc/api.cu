@@ -453,6 +453,7 @@ struct riann_full_s {
   int NP = 0;
   int32_t* scratch = nullptr;        // [resident warps][2][n]
   uint32_t* counter = nullptr;
+  unsigned long long* work = nullptr;   // [3] counters of the last frame
   size_t bytes = 0;
 };
 
@@ -469,6 +470,7 @@ int riann_full_create(riann_index_t idx, riann_stream_t stream, riann_full_t* ou
   cudaError_t e = dalloc(&f->T, (size_t)idx->n * f->NP, f->bytes);
   if (e == cudaSuccess) e = dalloc(&f->scratch, (size_t)anchor_resident_warps() * 2 * idx->n, f->bytes);
   if (e == cudaSuccess) e = dalloc(&f->counter, 1, f->bytes);
+  if (e == cudaSuccess) e = dalloc(&f->work, 3, f->bytes);
   if (e == cudaSuccess) e = build_full_table(*idx, f->T, f->NP, s);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -476,6 +478,7 @@ int riann_full_create(riann_index_t idx, riann_stream_t stream, riann_full_t* ou
     cudaFree(f->T);
     cudaFree(f->scratch);
     cudaFree(f->counter);
+    cudaFree(f->work);
     delete f;
     return from_cuda(e);
   }
@@ -489,7 +492,16 @@ void riann_full_destroy(riann_full_t f) {
   cudaFree(f->T);
   cudaFree(f->scratch);
   cudaFree(f->counter);
+  cudaFree(f->work);
   delete f;
+}
+
+int riann_anchor_work(riann_full_t f, riann_stream_t stream, uint64_t* out3) {
+  if (!f || !out3) return RIANN_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(out3, f->work, 3 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  return from_cuda(e);
 }
 
 int riann_full_table(riann_full_t f, riann_stream_t stream, uint64_t* host_T) {
@@ -542,6 +554,7 @@ int riann_anchor_frame(riann_full_t f, const riann_anchor_params* p, riann_strea
   a.frame_id = p->frame_id;
   a.scratch = f->scratch;
   a.counter = f->counter;
+  a.work = f->work;
   a.status = ix.status;
   return from_cuda(launch_anchor(a, ix.C, s));
 }

@@ -149,6 +149,7 @@ _lib.riann_full_destroy.argtypes = [_P]
 _lib.riann_full_destroy.restype = None
 _lib.riann_full_table.argtypes = [_P, _P, _P]
 _lib.riann_anchor_frame.argtypes = [_P, ctypes.POINTER(riann_anchor_params), _P, _P, _i32, _i32, _P, _P, _P, _P, _P]
+_lib.riann_anchor_work.argtypes = [_P, _P, _P]
 
 
 class RiannError(RuntimeError):
@@ -360,6 +361,13 @@ def riann_anchor_frame(full: RiannFull, params: riann_anchor_params, frame: torc
                                    _dev(out_annf, _I32, "out_annf", Q), _dev(out_dist, _U32, "out_dist", Q),
                                    _dev(out_count, _U32, "out_count", Q), _dev(out_rings, _U32, "out_rings", Q)),
            "riann_anchor_frame")
+
+
+def riann_anchor_work(full: RiannFull, stream=None) -> dict:
+    """Counters of the last riann_anchor_frame on this handle."""
+    buf = (ctypes.c_uint64 * 3)()
+    _check(_lib.riann_anchor_work(full.handle, _stream(stream), buf), "riann_anchor_work")
+    return {"sum_first_ring": int(buf[0]), "ring_tests": int(buf[1]), "sum_final": int(buf[2])}
 
 
 def anchor(full: RiannFull, frame: torch.Tensor, prev: Optional[torch.Tensor], params: riann_anchor_params,
