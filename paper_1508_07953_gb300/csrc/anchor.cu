@@ -6,8 +6,12 @@
 // The matrix: row i holds every reference as a 64-bit key
 // (||r_i - r_id||^2 << 32) | id, ascending, so a ring around r_i is one
 // contiguous range of row i, found by two searches.  Later rings are tested on
-// the candidates themselves (one distance each), which leaves the order of the
-// candidate list unchanged.
+// the candidates, which leaves the order of the candidate list unchanged:
+// either by one distance each or, when the anchor's own ring (a range of its
+// row) holds no more references than there are candidates and n <= 65536, by
+// marking that range in a per-warp bitmap and testing one bit per candidate --
+// the same set, since the range holds exactly the references with A in the
+// ring's bounds.  (Marking a larger ring costs more than the distances.)
 //
 // One warp per query in a persistent launch (queries from an atomic counter:
 // their cost varies by orders of magnitude).  Ring test for anchor a with
@@ -104,7 +108,11 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
   constexpr int D = 64 * C, NW = D / 4;
   __shared__ __align__(16) uint32_t s_q[kAnchorWarps][NW];   // the query patch
   __shared__ __align__(16) uint32_t s_a[kAnchorWarps][NW];   // the current anchor's row
+  __shared__ uint32_t s_bits[kAnchorWarps][kAnchorBitmapN / 32];   // members of an anchor's ring
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* bits = s_bits[warp];
+  for (int w = lane; w < kAnchorBitmapN / 32; w += 32) bits[w] = 0u;   // kept all-zero between rings
+  __syncwarp();
   const int Wq = a.W - 7;
   const int64_t Q = (int64_t)(a.H - 7) * Wq;
   const uint32_t p = (uint32_t)a.alpha_num, qa = (uint32_t)a.alpha_den;
@@ -166,6 +174,24 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
       best = ka < best ? ka : best;
       int32_t* dst = buf[t & 1];
       tests += (unsigned long long)ns;
+      // the anchor's ring as a range [alo, ahi) of its own row
+      int alo = 0, ahi = 0;
+      bool use_bits = false;
+      const unsigned long long* arow = a.T + (int64_t)ra * a.NP;
+      if (a.n <= kAnchorBitmapN) {
+        const unsigned long long bmin = p < qa ? ((unsigned long long)(qa - p) * (qa - p) * Ba + qq - 1) / qq : 0ull;
+        const unsigned long long bmax = (unsigned long long)(qa + p) * (qa + p) * Ba / qq;
+        alo = warp_lower_bound(arow, a.n, bmin << 32, lane);
+        ahi = bmax >= 0xffffffffull ? a.n : warp_lower_bound(arow, a.n, (bmax + 1) << 32, lane);
+        use_bits = ahi - alo <= ns;
+        if (use_bits) {
+          for (int k = alo + lane; k < ahi; k += 32) {
+            const uint32_t id = (uint32_t)__ldg(arow + k);
+            atomicOr(bits + (id >> 5), 1u << (id & 31));
+          }
+          __syncwarp();
+        }
+      }
       int m = 0;
       for (int base = 0; base < ns; base += 32) {
         const int k = base + lane;
@@ -173,14 +199,22 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
         int rj = 0;
         if (k < ns) {
           rj = src ? src[k] : (int)(uint32_t)__ldg(row + lo + k);
-          const uint32_t A = row_sqdist<NW>(a4, reinterpret_cast<const uint4*>(a.R + (int64_t)rj * D));
-          keep = in_anchor_ring(A, Ba, p, qa);
+          if (use_bits) {
+            keep = (bits[rj >> 5] >> (rj & 31)) & 1u;
+          } else {
+            const uint32_t A = row_sqdist<NW>(a4, reinterpret_cast<const uint4*>(a.R + (int64_t)rj * D));
+            keep = in_anchor_ring(A, Ba, p, qa);
+          }
         }
         const unsigned bal = __ballot_sync(kFull, keep);
         if (keep) dst[m + __popc(bal & below_mask)] = rj;   // order kept
         m += __popc(bal);
       }
       __syncwarp();
+      if (use_bits) {   // back to all-zero
+        for (int k = alo + lane; k < ahi; k += 32) bits[(uint32_t)__ldg(arow + k) >> 5] = 0u;
+        __syncwarp();
+      }
       src = dst;
       ns = m;
       ++t;

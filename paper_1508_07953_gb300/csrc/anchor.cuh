@@ -6,8 +6,9 @@
 
 namespace riann {
 
-constexpr int kAnchorWarps = 8;      // warps per CTA of the persistent anchor launch
-constexpr int kAnchorCtasPerSm = 2;
+constexpr int kAnchorWarps = 4;      // warps per CTA of the persistent anchor launch
+constexpr int kAnchorCtasPerSm = 4;
+constexpr int kAnchorBitmapN = 65536;   // references a warp's membership bitmap covers (8 KB)
 
 struct AnchorArgs {
   const uint8_t* frame;
