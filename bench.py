@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-recon", action="store_true", help="skip the Sec. 4 reconstruction block")
     ap.add_argument("--no-anchor", action="store_true", help="skip the Alg. 1 random-anchor block")
+    ap.add_argument("--anchor-refs", type=int, default=0,
+                    help="anchor block on the first N references only (small cases for profiler captures)")
     ap.add_argument("--batch-ticks", type=int, default=6, help="timed ticks of the 32-stream batched form")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -400,8 +402,9 @@ def run_anchor(riann, idx, frames, H, W, stream, flush, steps: int, warm: int = 
            + nf * (H * W + 4 * Q + 16 * Q))
     hbm = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
     frame_ms = sum(ms) / nf
-    out = {"workload": "1080p gray frames as above, n=65536 refs, alpha=1/4, L=20, max_rings=64, Philox seed 0x5EED",
-           "matrix_bytes": 65536 * 65536 * 8, "matrix_build_ms": build_ms,
+    n = idx.n
+    out = {"workload": f"the frames above, n={n} refs, alpha=1/4, L=20, max_rings=64, Philox seed 0x5EED",
+           "matrix_bytes": n * n * 8, "matrix_build_ms": build_ms,
            "frames": nf, "ms_per_frame": frame_ms, "queries_per_s": Q / (frame_ms / 1000.0),
            "mean_first_ring": tot["sum_first_ring"] / (nf * Q), "mean_rings": sum(rings) / nf,
            "mean_final_candidates": tot["sum_final"] / (nf * Q), "ring_tests_per_query": tot["ring_tests"] / (nf * Q),
@@ -544,8 +547,15 @@ def run_ours(args, rank, world, local):
     # Alg. 1 with random anchors over the sorted distance matrix (the paper's
     # own loop): same frames, chained from the same brute-force start
     anchor_line = None
-    if not args.no_anchor and not args.crop:
-        anchor_line = run_anchor(riann, idx, frames, H, W, stream, flush, min(args.steps, 3))
+    if not args.no_anchor and (not args.crop or args.anchor_refs):
+        aidx = idx
+        if args.anchor_refs:
+            aidx = riann.riann_build_reference_index(torch.from_numpy(R[:args.anchor_refs]).to(dev),
+                                                     torch.from_numpy(KP).to(dev), stream=stream)
+        anchor_line = run_anchor(riann, aidx, frames, H, W, stream, flush, min(args.steps, 3))
+        if args.anchor_refs:
+            anchor_line["refs"] = args.anchor_refs
+            aidx.close()
 
     # end to end: pinned host frame in, ANN field out, through the public call
     e2e = None
