@@ -66,7 +66,26 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(ms: float, world: int, device="cpu") -> float:
+    """The job's time: the slowest rank's (every rank works through its own
+    streams; no data crosses ranks).  Collective only when world > 1."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, steps: int, queries_per_frame: int, job_ms: float) -> float:
+    """Whole-job queries/s: every rank processed `steps` frames of its own stream."""
+    return world * steps * queries_per_frame / (job_ms / 1000.0)
+
+
 def video_for_rank(rank: int) -> synth.Video:
+    """Rank r's stream: the workload's video with its seed moved by 1000 r
+    (rank 0 keeps the workload's own), so ranks share no frames."""
     spec = WORKLOAD.video
     if rank:
         spec = synth.VideoSpec(**{**spec.__dict__, "seed": spec.seed + 1000 * rank})
@@ -503,11 +522,8 @@ def run_ours(args, rank, world, local):
                 dense_flops.append(2.0 * st["dense_queries"] * WORKLOAD.n * 64)
         torch.cuda.synchronize()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = float(sum(step_ms))
+    total_ms = max_over_ranks(float(sum(step_ms)), world, dev)
     if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     riann.riann_profile_enable(idx, False)
     status = riann.riann_status(idx, stream)
@@ -582,19 +598,15 @@ def run_ours(args, rank, world, local):
                 prev = cur
             e1.record(stream)
         stream.synchronize()
-        e2e_ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        e2e = {"value": world * args.steps * Q / (e2e_ms / 1000.0), "unit": UNIT,
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": job_throughput(world, args.steps, Q, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": H * W, "d2h_bytes_per_step": 4 * Q}
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-    value = world * args.steps * Q / (total_ms / 1000.0)
+    value = job_throughput(world, args.steps, Q, total_ms)
     peaks = measured_peaks()
     hbm = peaks["hbm_gbs"] if peaks else 6800.0
     ring_avg_ms = float(np.mean(ring_ms)) if ring_ms else None
