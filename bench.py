@@ -448,6 +448,33 @@ def run_anchor(riann, idx, frames, H, W, stream, flush, steps: int, warm: int = 
     ex, gx = (int(v) for v in err2.cpu())
     out["E_field"] = {"frame_index": last, "anchor_loop": (e / g) ** 0.5, "exact_nn": (ex / gx) ** 0.5,
                       "exact_nn_agreement": float((exact == prev).double().mean())}
+    # Alg. 1 from its own start: a random field (Uniform over R), then the loop
+    # on the next frames; the paper reports convergence "after very few frames"
+    conv = {"ms": [], "E_anchor_loop": [], "E_exact_nn": [], "exact_nn_agreement": []}
+    rf = torch.empty_like(prev)
+    riann.riann_random_field(H, W, idx.n, 0xBADC0DE, 0, rf, stream=stream)
+    prev = rf
+    for i in range(1, min(5, len(frames))):
+        cur = outs[i % 2]
+        p.frame_id = 1000 + i
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            riann.riann_anchor_frame(full, p, frames[i], prev, *cur, stream=stream)
+            e1.record(stream)
+            riann.riann_reconstruct(idx, cur[0], frames[i], None, err2, stream=stream)
+        stream.synchronize()
+        conv["ms"].append(e0.elapsed_time(e1))
+        e, g = (int(v) for v in err2.cpu())
+        conv["E_anchor_loop"].append((e / g) ** 0.5)
+        with torch.cuda.stream(stream):
+            riann.riann_exact_nn(idx, frames[i], exact, stream=stream)
+            riann.riann_reconstruct(idx, exact, frames[i], None, err2, stream=stream)
+        stream.synchronize()
+        ex, gx = (int(v) for v in err2.cpu())
+        conv["E_exact_nn"].append((ex / gx) ** 0.5)
+        conv["exact_nn_agreement"].append(float((exact == cur[0]).double().mean()))
+        prev = cur[0]
+    out["from_random_field"] = conv
     full.close()
     return out
 

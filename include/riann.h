@@ -452,6 +452,13 @@ int riann_anchor_frame(riann_full_t f, const riann_anchor_params* p, riann_strea
                        int32_t* d_out_annf, uint32_t* d_out_dist, uint32_t* d_out_count,
                        uint32_t* d_out_rings);
 
+/* Alg. 1 "Initialize: ANNF^(0)(x,y) ~ Uniform[1,|R|]" (0-based): writes the
+ * int32 [H-7][W-7] field d_out_annf, entry q = (x * n) >> 32 with x the first
+ * word of Philox4x32-10 at counter (q, 0, frame_id, 1), key (seed low, seed
+ * high).  Asynchronous on `stream`. */
+int riann_random_field(riann_stream_t stream, int32_t H, int32_t W, int32_t n, uint64_t seed, uint32_t frame_id,
+                       int32_t* d_out_annf);
+
 /* Work of the handle's last riann_anchor_frame (synchronises `stream`):
  * out3[0] = sum of |S_0| (first-ring sizes), out3[1] = candidate tests made by
  * the anchor rings, out3[2] = sum of the final |S|. */

@@ -60,6 +60,7 @@ def _load():
                                                  i32, i32, i32, P, i64, P, P, P, P]
             lib.oracle_reconstruct.argtypes = [P, i32, i32, P, i32, i32, P, P, P]
             lib.oracle_philox4x32_10.argtypes = [P, P, P]
+            lib.oracle_random_field.argtypes = [i32, i32, i32, ctypes.c_uint64, u32, P]
             lib.oracle_full_tables.argtypes = [P, i32, i32, P]
             lib.oracle_riann_anchor.argtypes = [P, i32, i32, i32, P, i32, P, P, i32, i32, i32, i32,
                                                 ctypes.c_uint64, u32, P, i64, P, P, P, P]
@@ -83,7 +84,8 @@ class use_library:
         lib = ctypes.CDLL(self.path)
         for name in ("oracle_ring_member", "oracle_key_distances", "oracle_sort_tables", "oracle_exact_nn",
                      "oracle_riann_definitional", "oracle_riann_indexed", "oracle_reconstruct",
-                     "oracle_philox4x32_10", "oracle_full_tables", "oracle_riann_anchor", "oracle_num_threads",
+                     "oracle_philox4x32_10", "oracle_full_tables", "oracle_riann_anchor", "oracle_random_field",
+                     "oracle_num_threads",
                      "oracle_set_num_threads"):
             f, g = getattr(self._saved, name), getattr(lib, name)
             g.argtypes, g.restype = f.argtypes, f.restype
@@ -251,4 +253,12 @@ def riann_anchor_frame(index: FullIndex, frame: np.ndarray, prev: Optional[np.nd
                             alpha[0], alpha[1], L, max_rings, seed & ((1 << 64) - 1), frame_id & 0xffffffff,
                             _ptr(q), nq, _ptr(annf), _ptr(dist), _ptr(count), _ptr(rings))
     return annf, dist, count, rings
+
+
+def random_field(H: int, W: int, n: int, seed: int = 0, frame_id: int = 0) -> np.ndarray:
+    """Alg. 1's random initial field, 0-based: int32 [H-7][W-7]."""
+    lib = _load()
+    out = np.empty((H - 7, W - 7), np.int32)
+    lib.oracle_random_field(H, W, n, seed & ((1 << 64) - 1), frame_id & 0xffffffff, _ptr(out))
+    return out
 

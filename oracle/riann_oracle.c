@@ -486,3 +486,14 @@ void oracle_riann_anchor(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
     free(S); free(S2);
   }
 }
+
+void oracle_random_field(int32_t H, int32_t W, int32_t n, uint64_t seed, uint32_t frame_id, int32_t* annf) {
+  const int64_t Q = (int64_t)(H - 7) * (W - 7);
+  const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t q = 0; q < Q; ++q) {
+    const uint32_t ctr[4] = {(uint32_t)q, 0u, frame_id, 1u};
+    uint32_t x[4];
+    oracle_philox4x32_10(ctr, key, x);
+    annf[q] = (int32_t)(((uint64_t)x[0] * (uint64_t)(uint32_t)n) >> 32);
+  }
+}

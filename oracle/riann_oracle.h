@@ -120,6 +120,11 @@ void oracle_riann_anchor(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
                          const int64_t* qidx, int64_t nq,
                          int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* rings);
 
+/* Alg. 1 "Initialize: ANNF^(0)(x,y) ~ Uniform[1,|R|]", 0-based: entry q =
+ * (x * n) >> 32, x the first word of Philox4x32-10 with counter
+ * (q, 0, frame_id, 1) and key (seed low, seed high). */
+void oracle_random_field(int32_t H, int32_t W, int32_t n, uint64_t seed, uint32_t frame_id, int32_t* annf);
+
 /* Number of OpenMP threads the oracle uses (1 when built without OpenMP). */
 int oracle_num_threads(void);
 void oracle_set_num_threads(int n);

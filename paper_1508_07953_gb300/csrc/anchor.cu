@@ -249,6 +249,15 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
   }
 }
 
+// Alg. 1 "Initialize": entry q = (x * n) >> 32, x from Philox4x32-10 with counter (q, 0, frame id, 1).
+__global__ void k_random_field(int64_t Q, int n, uint32_t key0, uint32_t key1, uint32_t frame_id, int32_t* out) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t x;
+    philox4x32_10((uint32_t)q, 0u, frame_id, 1u, key0, key1, &x);
+    out[q] = (int32_t)(((unsigned long long)x * (unsigned)n) >> 32);
+  }
+}
+
 __global__ void k_fill_u32(uint32_t* p, int64_t count, uint32_t v) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = v;
@@ -283,6 +292,14 @@ cudaError_t launch_anchor(const AnchorArgs& a, int C, cudaStream_t s) {
   const int grid = kAnchorCtasPerSm * sm_count();
   if (C == 1) k_anchor<1><<<grid, kAnchorWarps * 32, 0, s>>>(a);
   else k_anchor<3><<<grid, kAnchorWarps * 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_random_field(int64_t Q, int n, uint64_t seed, uint32_t frame_id, int32_t* out, cudaStream_t s) {
+  if (Q <= 0) return cudaSuccess;
+  int64_t blocks = (Q + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_random_field<<<(unsigned)blocks, 256, 0, s>>>(Q, n, (uint32_t)seed, (uint32_t)(seed >> 32), frame_id, out);
   return cudaGetLastError();
 }
 

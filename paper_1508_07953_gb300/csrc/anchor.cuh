@@ -37,6 +37,7 @@ cudaError_t build_full_table(const Index& ix, unsigned long long* T, int NP, cud
 int anchor_resident_warps();
 cudaError_t launch_anchor(const AnchorArgs& a, int C, cudaStream_t s);
 cudaError_t launch_fill_u32(uint32_t* p, int64_t count, uint32_t value, cudaStream_t s);
+cudaError_t launch_random_field(int64_t Q, int n, uint64_t seed, uint32_t frame_id, int32_t* out, cudaStream_t s);
 
 // index_build.cu
 cudaError_t sort_segments(unsigned long long* keys, int NP, int64_t nseg, cudaStream_t s);

@@ -496,6 +496,13 @@ void riann_full_destroy(riann_full_t f) {
   delete f;
 }
 
+int riann_random_field(riann_stream_t stream, int32_t H, int32_t W, int32_t n, uint64_t seed, uint32_t frame_id,
+                       int32_t* d_out_annf) {
+  if (!d_out_annf || !frame_ok(H, W) || n < 1) return RIANN_ERR_INVALID_ARG;
+  return from_cuda(launch_random_field((int64_t)(H - 7) * (W - 7), n, seed, frame_id, d_out_annf,
+                                       reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int riann_anchor_work(riann_full_t f, riann_stream_t stream, uint64_t* out3) {
   if (!f || !out3) return RIANN_ERR_INVALID_ARG;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);

@@ -150,6 +150,7 @@ _lib.riann_full_destroy.restype = None
 _lib.riann_full_table.argtypes = [_P, _P, _P]
 _lib.riann_anchor_frame.argtypes = [_P, ctypes.POINTER(riann_anchor_params), _P, _P, _i32, _i32, _P, _P, _P, _P, _P]
 _lib.riann_anchor_work.argtypes = [_P, _P, _P]
+_lib.riann_random_field.argtypes = [_P, _i32, _i32, _i32, ctypes.c_uint64, ctypes.c_uint32, _P]
 
 
 class RiannError(RuntimeError):
@@ -361,6 +362,13 @@ def riann_anchor_frame(full: RiannFull, params: riann_anchor_params, frame: torc
                                    _dev(out_annf, _I32, "out_annf", Q), _dev(out_dist, _U32, "out_dist", Q),
                                    _dev(out_count, _U32, "out_count", Q), _dev(out_rings, _U32, "out_rings", Q)),
            "riann_anchor_frame")
+
+
+def riann_random_field(H: int, W: int, n: int, seed: int, frame_id: int, out: torch.Tensor,
+                       stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Alg. 1's random initial field into out (int32 [H-7][W-7])."""
+    _check(_lib.riann_random_field(_stream(stream), H, W, n, seed & ((1 << 64) - 1), frame_id & 0xffffffff,
+                                   _dev(out, _I32, "out", (H - 7) * (W - 7))), "riann_random_field")
 
 
 def riann_anchor_work(full: RiannFull, stream=None) -> dict:

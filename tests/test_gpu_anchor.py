@@ -101,3 +101,11 @@ def test_bad_prev_sets_status(rt):
     assert a[0, 0] == -1 and a[2, 3] == -1
     full.close()
     idx.close()
+
+
+def test_random_field_matches_oracle(rt):
+    import torch
+    for H, W, n, seed, fid in ((8, 8, 1, 0, 0), (37, 100, 65536, 0x5EED, 3), (720, 1280, 16384, 1 << 63, 11)):
+        out = torch.empty((H - 7, W - 7), dtype=torch.int32, device="cuda")
+        rt.riann_random_field(H, W, n, seed, fid, out)
+        assert np.array_equal(out.cpu().numpy(), oracle.random_field(H, W, n, seed, fid))

@@ -157,3 +157,13 @@ def test_golden_candidate_set_of_exactly_L():
         a, dist, c, k = oracle.riann_anchor_frame(fi, frame, prev, alpha=tuple(d["alpha"]), L=d["L"][0], seed=seed)
         assert (int(a[0, 0]), int(dist[0, 0]), int(c[0, 0]), int(k[0, 0])) == (
             d["expect_annf"][0], d["expect_dist"][0], d["expect_count"][0], d["expect_rings"][0])
+
+
+def test_random_field_definition_and_range():
+    H, W, n, seed, fid = 20, 31, 777, 0xABCDEF0123, 5
+    f = oracle.random_field(H, W, n, seed, fid)
+    want = [(philox_py([q, 0, fid, 1], [seed & M32, seed >> 32])[0] * n) >> 32 for q in range((H - 7) * (W - 7))]
+    assert np.array_equal(f.reshape(-1), np.array(want))
+    big = oracle.random_field(300, 300, 10, 1)          # roughly uniform over [0, n)
+    counts = np.bincount(big.reshape(-1), minlength=10)
+    assert counts.min() > 0.9 * big.size / 10 and counts.max() < 1.1 * big.size / 10
