@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-recon", action="store_true", help="skip the Sec. 4 reconstruction block")
     ap.add_argument("--no-anchor", action="store_true", help="skip the Alg. 1 random-anchor block")
+    ap.add_argument("--no-other", action="store_true", help="skip the tiny and 720p RGB workloads")
     ap.add_argument("--anchor-refs", type=int, default=0,
                     help="anchor block on the first N references only (small cases for profiler captures)")
     ap.add_argument("--batch-ticks", type=int, default=6, help="timed ticks of the 32-stream batched form")
@@ -230,10 +231,57 @@ def oracle_chain_rate(oracle, oix, frames_np, params, n_samp, seed, budget_s):
 def cpu_baseline(R, KP, frames_np, params, budget_s=12.0, n_samp=16384):
     oracle, oix = oracle_setup(R, KP)
     q, el, nf = oracle_chain_rate(oracle, oix, frames_np, params, n_samp, 100, budget_s)
-    return {"value": q / el, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+    cores = oracle.num_threads()
+    oracle.set_num_threads(1)                       # the same work on one core, shorter sample
+    q1, el1, nf1 = oracle_chain_rate(oracle, oix, frames_np, params, 1024, 101, 4.0)
+    oracle.set_num_threads(cores)
+    return {"value": q / el, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{n_samp} query positions sampled uniformly from a 1080p frame, chained over "
                       f"{nf} consecutive frames (indexed oracle mode: ring step, brute force for wide "
-                      f"rings); {el:.1f} s of oracle time"}
+                      f"rings); {el:.1f} s of oracle time",
+            "single_core_value": q1 / el1,
+            "single_core_sample": f"1024 positions over {nf1} frames, {el1:.1f} s"}
+
+
+def run_other_configs(riann, dev, flush):
+    """The other single-frame workloads (plain per-frame form): GPU queries/s
+    over chained frames (L2 flushed before each) and the oracle's on a
+    bounded sample of the same frames."""
+    import torch
+    out = {}
+    for name, frames_t, n_samp in (("tiny", range(0, 8), 1 << 30), ("720p_rgb", range(0, 10), 4096)):
+        w = synth.WORKLOADS[name]
+        R = synth.workload_reference(w)
+        KP = synth.workload_keypoints(w, R)
+        v = synth.Video(w.video)
+        fnp = [v.frame(t) for t in frames_t]
+        fr = [torch.from_numpy(np.ascontiguousarray(f)).to(dev) for f in fnp]
+        H, W = fnp[0].shape[:2]
+        Q = (H - 7) * (W - 7)
+        idx = riann.riann_build_reference_index(torch.from_numpy(R).to(dev), torch.from_numpy(KP).to(dev))
+        p = riann.riann_default_params(w.n)
+        bufs = [torch.empty((H - 7, W - 7), dtype=torch.int32, device=dev) for _ in range(2)]
+        prev = None
+        ms = []
+        for i, f in enumerate(fr):
+            flush.fill_(i & 0xff)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            riann.riann_annf_frame(idx, p, f, prev, bufs[i % 2])
+            e1.record()
+            torch.cuda.synchronize()
+            if i >= 3:
+                ms.append(e0.elapsed_time(e1))
+            prev = bufs[i % 2]
+        idx.close()
+        oracle, oix = oracle_setup(R, KP)
+        pd = {"alpha_num": 1, "alpha_den": 4, "ring_limit": w.n // 8}
+        q, el, nf = oracle_chain_rate(oracle, oix, fnp[2:], pd, n_samp, 7, 3.0)
+        out[name] = {"n": w.n, "K": w.K, "channels": w.C, "frame": f"{H}x{W}", "queries_per_frame": Q,
+                     "gpu_queries_per_s": Q / (float(np.mean(ms)) / 1000.0), "gpu_ms_per_frame": float(np.mean(ms)),
+                     "gpu_frames": len(ms), "oracle_queries_per_s": q / el, "oracle_cores": oracle.num_threads(),
+                     "oracle_sample": f"{min(n_samp, Q)} positions over {nf} frames, {el:.1f} s"}
+    return out
 
 
 def run_reference(args, rank, world):
@@ -446,8 +494,21 @@ def run_anchor(riann, idx, frames, H, W, stream, flush, steps: int, warm: int = 
         riann.riann_reconstruct(idx, exact, frames[last], None, err2, stream=stream)
     stream.synchronize()
     ex, gx = (int(v) for v in err2.cpu())
+    # the fixed-key ring step on the same frames, from the same brute-force start
+    kp = riann.riann_default_params(idx.n)
+    fk = [torch.empty_like(prev) for _ in range(2)]
+    fprev = None
+    with torch.cuda.stream(stream):
+        for i in range(0, last + 1):
+            riann.riann_annf_frame(idx, kp, frames[i], fprev, fk[i % 2], None, None, stream=stream)
+            fprev = fk[i % 2]
+        riann.riann_reconstruct(idx, fprev, frames[last], None, err2, stream=stream)
+    stream.synchronize()
+    fe, fg = (int(v) for v in err2.cpu())
     out["E_field"] = {"frame_index": last, "anchor_loop": (e / g) ** 0.5, "exact_nn": (ex / gx) ** 0.5,
-                      "exact_nn_agreement": float((exact == prev).double().mean())}
+                      "fixed_key_ring_step": (fe / fg) ** 0.5,
+                      "exact_nn_agreement": float((exact == prev).double().mean()),
+                      "fixed_key_exact_nn_agreement": float((exact == fprev).double().mean())}
     # Alg. 1 from its own start: a random field (Uniform over R), then the loop
     # on the next frames; the paper reports convergence "after very few frames"
     conv = {"ms": [], "E_anchor_loop": [], "E_exact_nn": [], "exact_nn_agreement": []}
@@ -690,6 +751,10 @@ def run_ours(args, rank, world, local):
     if world == 1 and not args.no_cpu_baseline:
         pd = {"alpha_num": params.alpha_num, "alpha_den": params.alpha_den, "ring_limit": params.ring_limit}
         line["cpu_baseline"] = cpu_baseline(R, KP, frames_np, pd)
+    if world == 1 and not args.no_other:
+        fl = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+        line["other_configs"] = run_other_configs(riann, dev, fl)
+        del fl
     print(json.dumps(line), flush=True)
     idx.close()
     if world > 1:
