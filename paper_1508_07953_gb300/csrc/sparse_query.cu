@@ -110,23 +110,18 @@ __device__ __forceinline__ uint32_t sq4(const uint32_t* q, uint4 u, uint32_t acc
 }
 
 // code(x) = (number of bucket edges <= x) - 1, in [-1, 255].  Two levels:
-// every 16th edge in shared memory, then the 16 edges of one 64-byte segment.
+// every 4th edge in shared memory (64 per key), then the 4 edges of one
+// 16-byte segment from global memory.
 __device__ __forceinline__ int bucket_code(const uint32_t* __restrict__ coarse, const uint32_t* __restrict__ e,
                                            uint32_t x) {
   int c = 0;   // coarse edges <= x
 #pragma unroll
-  for (int half = 8; half > 0; half >>= 1)
+  for (int half = 32; half > 0; half >>= 1)
     if (coarse[c + half - 1] <= x) c += half;
-  if (c == 15 && coarse[15] <= x) c = 16;
+  if (c == 63 && coarse[63] <= x) c = 64;
   if (c == 0) return -1;
-  const uint4* seg = reinterpret_cast<const uint4*>(e + 16 * (c - 1));
-  int cnt = 0;
-#pragma unroll
-  for (int v = 0; v < 4; ++v) {
-    const uint4 u = __ldg(seg + v);
-    cnt += (u.x <= x) + (u.y <= x) + (u.z <= x) + (u.w <= x);
-  }
-  return 16 * (c - 1) + cnt - 1;
+  const uint4 u = __ldg(reinterpret_cast<const uint4*>(e + 4 * (c - 1)));
+  return 4 * (c - 1) + (u.x <= x) + (u.y <= x) + (u.z <= x) + (u.w <= x) - 1;
 }
 
 // Number of entries of the sorted range t[lo, hi) below v (le: at most v),
@@ -195,12 +190,12 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   constexpr int kMaxG = kMaxK / 4;
   __shared__ __align__(16) uint8_t s_tile[(TY + 7) * TROWP];
   __shared__ uint32_t s_kp[kMaxK * KPW];
-  __shared__ uint32_t s_coarse[kMaxK][16];        // every 16th bucket edge per key
+  __shared__ uint32_t s_coarse[kMaxK][65];        // every 4th bucket edge per key (padded: no bank conflicts)
   // exact ring bounds [lo, hi] on A as (lo, hi - lo) per key; padding keys (0, ~0)
   __shared__ __align__(16) uint32_t s_lw[kWarps][2 * kMaxK];
   __shared__ int16_t s_clo[kWarps][kMaxK];        // their bucket codes (-1..255)
   __shared__ int16_t s_chi[kWarps][kMaxK];
-  __shared__ uint32_t s_ub[kWarps][kMaxK];        // bucket-granular upper bound on |Ring_m|
+  __shared__ uint32_t s_ub[kWarps][kMaxK];        // buckets each ring touches
   __shared__ uint32_t s_lo4[kWarps][kMaxG];       // per group: packed code ranges
   __shared__ uint32_t s_hi4[kWarps][kMaxG];
   __shared__ uint32_t s_any4[kWarps][kMaxG];      // bytes of keys that always pass (seed, padding)
@@ -216,7 +211,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   {
     const uint32_t* kp = reinterpret_cast<const uint32_t*>(a.KP);
     for (int i = threadIdx.x; i < K * NW; i += blockDim.x) s_kp[(i / NW) * KPW + (i % NW)] = kp[i];
-    for (int i = threadIdx.x; i < K * 16; i += blockDim.x) s_coarse[i >> 4][i & 15] = __ldg(a.E + (i >> 4) * kBuckets + 16 * (i & 15));
+    for (int i = threadIdx.x; i < K * 64; i += blockDim.x) s_coarse[i >> 6][i & 63] = __ldg(a.E + (i >> 6) * kBuckets + 4 * (i & 63));
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t p2 = (uint32_t)(a.alpha_num * a.alpha_num);
@@ -313,8 +308,6 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     // bucket codes, and bucket-granular bounds lb <= |Ring_m| <= ub.
     const float sC = (float)Cd;
     unsigned long long seedkey = ~0ull;
-    bool small = false;      // some ring certainly holds <= ring_limit references
-    bool maybe = false;      // some ring might (its lower bound is <= ring_limit)
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int m = lane + 32 * h;
@@ -331,22 +324,18 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         const uint32_t lo = ring_low(B, Cd, p2, q2, base - cross);
         const uint32_t hi = ring_high(B, Cd, p2, q2, base + cross, Amax);
         const uint32_t* e = a.E + m * kBuckets;
-        const uint32_t* rb = a.RB + m * (kBuckets + 1);
         const int clo = bucket_code(s_coarse[m], e, lo);
         const int chi = bucket_code(s_coarse[m], e, hi);
-        const uint32_t ub = __ldg(rb + chi + 1) - (clo < 0 ? 0u : __ldg(rb + clo));
-        const uint32_t lb = chi > clo + 1 ? __ldg(rb + chi) - __ldg(rb + clo + 1) : 0u;
+        // buckets the ring touches: picks the seed and orders the filter
+        // groups (performance only; the result does not depend on them)
+        const uint32_t width = chi < 0 ? 0u : (uint32_t)(chi - (clo < 0 ? 0 : clo) + 1);
         s_lw[warp][2 * m] = lo;
         s_lw[warp][2 * m + 1] = hi - lo;
         s_clo[warp][m] = (int16_t)clo;
         s_chi[warp][m] = (int16_t)chi;
-        s_ub[warp][m] = ub;
-        const unsigned long long key = ((unsigned long long)ub << 32) | (unsigned)m;
+        s_ub[warp][m] = width;
+        const unsigned long long key = ((unsigned long long)width << 32) | (unsigned)m;
         seedkey = key < seedkey ? key : seedkey;
-        if (a.ring_limit >= 0) {
-          if (ub <= (uint32_t)a.ring_limit) small = true;
-          else if (lb <= (uint32_t)a.ring_limit) maybe = true;
-        }
       } else if (m < a.Kp) {   // padding key of a distance row: always passes
         s_lw[warp][2 * m] = 0u;
         s_lw[warp][2 * m + 1] = 0xffffffffu;
@@ -357,31 +346,61 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       const unsigned long long v = __shfl_xor_sync(kFull, seedkey, o);
       seedkey = v < seedkey ? v : seedkey;
     }
-    const int ms = (int)(seedkey & 0xffffffffu);
+    int ms = (int)(seedkey & 0xffffffffu);
     __syncwarp();
 
-    // routing: brute force iff every ring holds more than ring_limit references
-    if (a.ring_limit >= 0 && !__any_sync(kFull, small)) {
-      bool found = false;
-      unsigned cand = __ballot_sync(kFull, maybe);
-      // exact sizes of the rings whose bucket bounds straddle the limit
-      for (int h = 0; h < 2 && !found; ++h) {
-        unsigned todo = 0;
-        const int m0 = lane + 32 * h;
+    // exact run of the seed ring in its sorted list (the whole warp searches)
+    int2 run = ring_run(a.TA + (int64_t)ms * n, a.RB + ms * (kBuckets + 1), s_clo[warp][ms],
+                        s_chi[warp][ms], s_lw[warp][2 * ms], s_lw[warp][2 * ms] + s_lw[warp][2 * ms + 1], lane);
+
+    // routing: brute force iff every ring holds more than ring_limit
+    // references.  Settled by the seed ring's exact size when it is within
+    // the limit; otherwise by bucket-granular bounds on every ring (first ranks
+    // of the buckets, RB) and exact sizes of the rings whose bounds straddle
+    // it -- the ring that settles it becomes the seed.
+    if (a.ring_limit >= 0 && (uint32_t)(run.y - run.x) > (uint32_t)a.ring_limit) {
+      unsigned long long ubkey = ~0ull;            // smallest upper bound over the other rings
+      unsigned straddle[2];                        // rings whose bounds straddle the limit, per half
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int m = lane + 32 * h;
         bool mine = false;
-        if (m0 < K && cand) {
-          const int clo = s_clo[warp][m0], chi = s_chi[warp][m0];
-          const uint32_t* rb = a.RB + m0 * (kBuckets + 1);
+        if (m < K && m != ms) {
+          const int clo = s_clo[warp][m], chi = s_chi[warp][m];
+          const uint32_t* rb = a.RB + m * (kBuckets + 1);
+          const uint32_t ub = __ldg(rb + chi + 1) - (clo < 0 ? 0u : __ldg(rb + clo));
           const uint32_t lb = chi > clo + 1 ? __ldg(rb + chi) - __ldg(rb + clo + 1) : 0u;
-          mine = s_ub[warp][m0] > (uint32_t)a.ring_limit && lb <= (uint32_t)a.ring_limit;
+          const unsigned long long k2 = ((unsigned long long)ub << 32) | (unsigned)m;
+          ubkey = k2 < ubkey ? k2 : ubkey;
+          mine = ub > (uint32_t)a.ring_limit && lb <= (uint32_t)a.ring_limit;
         }
-        todo = __ballot_sync(kFull, mine);
+        straddle[h] = __ballot_sync(kFull, mine);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(kFull, ubkey, o);
+        ubkey = v < ubkey ? v : ubkey;
+      }
+      bool found = false;
+      if ((uint32_t)(ubkey >> 32) <= (uint32_t)a.ring_limit) {   // a ring certainly within the limit
+        ms = (int)(ubkey & 0xffffffffu);
+        run = ring_run(a.TA + (int64_t)ms * n, a.RB + ms * (kBuckets + 1), s_clo[warp][ms], s_chi[warp][ms],
+                       s_lw[warp][2 * ms], s_lw[warp][2 * ms] + s_lw[warp][2 * ms + 1], lane);
+        found = true;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        unsigned todo = straddle[h];
         while (todo && !found) {
           const int m = __ffs(todo) - 1 + 32 * h;
           todo &= todo - 1;
-          const int2 run = ring_run(a.TA + (int64_t)m * n, a.RB + m * (kBuckets + 1), s_clo[warp][m],
-                                    s_chi[warp][m], s_lw[warp][2 * m], s_lw[warp][2 * m] + s_lw[warp][2 * m + 1], lane);
-          if ((uint32_t)(run.y - run.x) <= (uint32_t)a.ring_limit) found = true;
+          const int2 r2 = ring_run(a.TA + (int64_t)m * n, a.RB + m * (kBuckets + 1), s_clo[warp][m],
+                                   s_chi[warp][m], s_lw[warp][2 * m], s_lw[warp][2 * m] + s_lw[warp][2 * m + 1], lane);
+          if ((uint32_t)(r2.y - r2.x) <= (uint32_t)a.ring_limit) {
+            found = true;
+            ms = m;
+            run = r2;
+          }
         }
       }
       if (!found) {
@@ -389,15 +408,11 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         continue;
       }
     }
-
-    // exact run of the seed ring in its sorted list (the whole warp searches)
-    const int2 run = ring_run(a.TA + (int64_t)ms * n, a.RB + ms * (kBuckets + 1), s_clo[warp][ms],
-                              s_chi[warp][ms], s_lw[warp][2 * ms],
-                              s_lw[warp][2 * ms] + s_lw[warp][2 * ms + 1], lane);
     const int jlo = run.x, jhi = run.y;
 
     // per group of 4 keys: packed code ranges, keys that always pass, and an
-    // estimate of the fraction of references passing (product of ub / n)
+    // estimate of the fraction of references passing (product over its keys of
+    // the fraction of buckets each ring touches)
     float est = 2.f;
     if (lane < G) {
       uint32_t lo4 = 0, hi4 = 0, any4 = 0;
@@ -412,7 +427,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
           hh = (uint32_t)(chi < 0 ? 0 : chi);
           if (chi < 0) l = 1;                 // empty ring: no code fits
           any = 0;
-          est *= (float)s_ub[warp][k] / (float)n;
+          est *= (float)s_ub[warp][k] * (1.f / kBuckets);   // fraction of buckets the ring touches
         }
         lo4 |= l << (8 * i);
         hi4 |= hh << (8 * i);
