@@ -76,7 +76,6 @@ FrameItem make_item(const uint8_t* frame, const int32_t* prev, int32_t* out, uin
   it.Hq = H - 7;
   it.Wq = W - 7;
   it.tiles_x = (it.Wq + ring_tile_cols(shape) - 1) / ring_tile_cols(shape);
-  it.tile_begin = 0;
   it.query_begin = 0;
   return it;
 }
@@ -235,6 +234,8 @@ struct riann_session_s {
   std::mutex mu;
 };
 
+constexpr int kBranches = 4;   // streams the ring launches of a batched step are spread over
+
 // A batch context: scratch for the union of its frames, pinned descriptor
 // staging, and the captured graph of one batched step.
 struct riann_batch_s {
@@ -252,7 +253,12 @@ struct riann_batch_s {
   cudaGraphExec_t exec = nullptr;
   riann_params gp{};             // parameters baked into the graph
   int g_shape = -1, g_depth = -1;
+  int g_items = 0;                     // ring launches of a step ...
+  std::vector<int> g_tiles;            // ... and the grid of each (slot i: its largest frame so far)
+  int tiles_shape = -1;                // tile shape g_tiles counts in
   cudaStream_t cap_stream = nullptr;   // private stream the graph is captured on
+  cudaStream_t branch[kBranches] = {};
+  cudaEvent_t fork = nullptr, join[kBranches] = {};
   cudaEvent_t done = nullptr;
   bool pending = false;
   int64_t runs = 0, graph_builds = 0;
@@ -278,6 +284,11 @@ void free_batch(riann_batch_s* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   if (b->done) cudaEventDestroy(b->done);
+  if (b->fork) cudaEventDestroy(b->fork);
+  for (int k = 0; k < kBranches; ++k) {
+    if (b->join[k]) cudaEventDestroy(b->join[k]);
+    if (b->branch[k]) cudaStreamDestroy(b->branch[k]);
+  }
   if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   cudaFreeHost(b->h_items);
   cudaFreeHost(b->h_hdr);
@@ -288,7 +299,10 @@ void free_batch(riann_batch_s* b) {
   delete b;
 }
 
-// The launch sequence of one batched step (captured into the graph).
+// The launch sequence of one batched step (captured into the graph): the
+// descriptor upload, one ring launch per slot (grid b->g_tiles[i]) spread
+// over the branch streams so that the frames' tails overlap, then one
+// brute-force launch over the queries of all frames.
 cudaError_t enqueue_batch(riann_batch_s* b, const riann_params* p, cudaStream_t s) {
   Index& ix = *b->ix;
   cudaError_t e = cudaMemcpyAsync(b->d_items, b->h_items, sizeof(FrameItem) * b->max_items,
@@ -300,7 +314,17 @@ cudaError_t enqueue_batch(riann_batch_s* b, const riann_params* p, cudaStream_t 
   SparseArgs sa = sparse_args(ix, p, b->ws, b->stats);
   sa.items = b->d_items;
   sa.hdr = b->d_hdr;
-  e = launch_sparse_batch(sa, ix.C, ix.tile_shape, s);
+  const int nb = b->g_items < kBranches ? b->g_items : kBranches;
+  e = cudaEventRecord(b->fork, s);
+  for (int k = 0; k < nb && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->branch[k], b->fork, 0);
+  for (int i = 0; i < b->g_items && e == cudaSuccess; ++i) {
+    sa.item = i;
+    e = launch_sparse_item(sa, ix.C, ix.tile_shape, b->g_tiles[i], b->branch[i % nb]);
+  }
+  for (int k = 0; k < nb && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(b->join[k], b->branch[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, b->join[k], 0);
+  }
   if (e != cudaSuccess) return e;
   DenseArgs da = dense_args(ix, b->stats);
   da.items = b->d_items;
@@ -853,6 +877,12 @@ int riann_batch_create(riann_index_t idx, int32_t max_items, int64_t max_queries
   if (e == cudaSuccess) e = dalloc(&b->d_hdr, 1, b->bytes);
   if (e == cudaSuccess) e = dalloc(&b->stats, kStats, b->bytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int k = 0; k < kBranches && e == cudaSuccess; ++k) {
+    e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->branch[k], cudaStreamNonBlocking);
+  }
+  if (e == cudaSuccess) b->g_tiles.assign((size_t)max_items, 0);
   if (e == cudaSuccess && b->use_graph) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -887,7 +917,6 @@ int riann_batch_run(riann_batch_t b, const riann_params* p, riann_stream_t strea
     if (e != cudaSuccess) return from_cuda(e);
     b->pending = false;
   }
-  int tiles = 0;
   int64_t queries = 0;
   for (int i = 0; i < n; ++i) queries += sessions[i]->Q;
   if (queries > b->cap_q) return RIANN_ERR_TOO_LARGE;
@@ -896,18 +925,32 @@ int riann_batch_run(riann_batch_t b, const riann_params* p, riann_stream_t strea
     riann_session_s* s = sessions[i];
     FrameItem it = make_item(d_frames[i], s->have_prev ? s->field[s->cur] : nullptr, s->field[s->cur ^ 1], s->dist,
                              s->count, s->H, s->W, ix.tile_shape);
-    it.tile_begin = tiles;
     it.query_begin = queries;
-    tiles += item_tiles(it, ix.tile_shape);
     queries += s->Q;
     b->h_items[i] = it;
   }
   b->h_hdr->n_items = n;
-  b->h_hdr->total_tiles = tiles;
   b->h_hdr->total_queries = queries;
+  // ring launch grids: a slot keeps the grid of its largest frame so far (a
+  // smaller frame's extra CTAs leave at once); slots past n stay empty
+  if (b->tiles_shape != ix.tile_shape) {
+    std::fill(b->g_tiles.begin(), b->g_tiles.end(), 0);
+    b->g_items = 0;
+    b->tiles_shape = ix.tile_shape;
+  }
+  bool grown = n > b->g_items;
+  for (int i = 0; i < n; ++i) {
+    const int t = item_tiles(b->h_items[i], ix.tile_shape);
+    if (t > b->g_tiles[i]) {
+      b->g_tiles[i] = t;
+      grown = true;
+    }
+  }
+  if (n > b->g_items) b->g_items = n;
+  for (int i = n; i < b->g_items; ++i) b->h_items[i] = FrameItem{};
   cudaError_t e = cudaSuccess;
   if (b->use_graph) {
-    const bool stale = !b->exec || b->gp.alpha_num != p->alpha_num || b->gp.alpha_den != p->alpha_den ||
+    const bool stale = !b->exec || grown || b->gp.alpha_num != p->alpha_num || b->gp.alpha_den != p->alpha_den ||
                        b->gp.ring_limit != p->ring_limit || b->gp.cap != p->cap || b->g_shape != ix.tile_shape ||
                        b->g_depth != ix.depth;
     if (stale) {

@@ -44,14 +44,12 @@ struct FrameItem {
   uint32_t* out_count;    // nullable
   int32_t H, W, Hq, Wq;
   int32_t tiles_x;        // ring-kernel tiles per row of queries
-  int32_t tile_begin;     // first tile of this item in the launch
   int64_t query_begin;    // first global query id of this item
 };
 
 // Device header of a batched launch.
 struct BatchHeader {
   int32_t n_items;
-  int32_t total_tiles;
   int64_t total_queries;
 };
 
@@ -59,7 +57,7 @@ struct BatchHeader {
 struct Workspace {
   int64_t cap_q = 0;                    // queries it can hold
   int32_t* dense_list = nullptr;        // [cap_q] global query ids routed to brute force
-  uint32_t* counters = nullptr;         // [4]: 0 brute-force list length, 1 tile counter
+  uint32_t* counters = nullptr;         // [4]: 0 brute-force list length
   unsigned long long* best = nullptr;   // [cap_q] packed (dist << 32 | index)
   __nv_bfloat16* Aq = nullptr;          // [cap_q padded to 128][D] bf16 query rows
   uint32_t* qnorm = nullptr;            // [cap_q padded] ||q||^2
@@ -122,6 +120,7 @@ struct SparseArgs {
   FrameItem one;                  // the frame of a single-frame launch
   const FrameItem* items;         // batched launch: device item array
   const BatchHeader* hdr;         // batched launch: device header
+  int item;                       // batched launch: the entry of `items` this launch covers
   const uint8_t* R;
   const uint8_t* KP;
   const uint32_t* P;
@@ -134,7 +133,7 @@ struct SparseArgs {
   int alpha_num, alpha_den, ring_limit;
   int depth;                      // stage-1 filter depth (1..5)
   int32_t* dense_list;
-  uint32_t* counters;             // [0] brute-force list length, [1] tile counter
+  uint32_t* counters;             // [0] brute-force list length
   uint32_t* status;
   unsigned long long* stats;      // nullable
 };
@@ -163,11 +162,12 @@ cudaError_t launch_dense_tc(const DenseArgs& a, Index& ix, Workspace& ws, cudaSt
 int64_t noalloc_max_queries(int C);
 cudaError_t launch_exact_nn_noalloc(const DenseArgs& a, Index& ix, cudaStream_t s);
 
-// ring kernel: one frame (grid = its tiles), or a persistent batched launch
+// ring kernel: one frame (grid = its tiles), its descriptor in the launch
+// parameters or (batched form) in a device array
 int ring_tile_rows(int shape);
 int ring_tile_cols(int shape);
 cudaError_t launch_sparse(const SparseArgs& a, int C, int shape, cudaStream_t s);
-cudaError_t launch_sparse_batch(const SparseArgs& a, int C, int shape, cudaStream_t s);
+cudaError_t launch_sparse_item(const SparseArgs& a, int C, int shape, int tiles, cudaStream_t s);
 
 cudaError_t launch_index_build(Index& ix, cudaStream_t s);
 

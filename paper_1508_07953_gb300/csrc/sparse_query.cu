@@ -175,10 +175,13 @@ __device__ __forceinline__ bool codes_pass(uint32_t w, uint32_t lo4, uint32_t hi
 constexpr int kQueue = 256;   // per-warp ring buffer of stage-1 survivors
 constexpr int kRowBatch = 4;  // 16-byte words of a distance row loaded per round (4 keys each)
 
-// One CTA per tile of TY x TX query positions.  Single-frame launch
-// (BATCH = false): the grid is the frame's tiles.  Batched launch: a
-// persistent grid whose CTAs take tiles of all the batch's frames from an
-// atomic counter, in the order of the items.
+// One CTA per tile of TY x TX query positions; the grid is one frame's tiles.
+// Single-frame launch (BATCH = false): the frame's descriptor is a kernel
+// parameter.  Batched form (BATCH = true): one launch per frame of the batch,
+// the descriptor read from the device item array (entry a.item), so a
+// captured graph of the launches stays valid while the descriptors change
+// from one step to the next.  (A persistent launch taking the tiles of all
+// frames from an atomic counter measured 8 % slower.)
 template <int C, int SHAPE, bool BATCH>
 __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid_constant__ SparseArgs a) {
   constexpr int TY = SHAPE == kTile4x32 ? 4 : 8;
@@ -203,8 +206,8 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   __shared__ int32_t s_queue[kWarps][kQueue];     // stage-1 survivors (seed-run positions)
   __shared__ __align__(16) uint32_t s_q[kWarps][NW];   // the warp's query patch
   __shared__ int32_t s_dense[TY * TX];
-  __shared__ int s_next, s_ndense, s_dense_base, s_tile_id;
-  __shared__ FrameItem s_item;                    // batched launch: the current tile's frame
+  __shared__ int s_next, s_ndense, s_dense_base;
+  __shared__ FrameItem s_item;                    // batched launch: this launch's frame
   __shared__ unsigned long long s_stat[3];        // ring-answered queries, scanned entries, sum of |S|
 
   const int K = a.K, n = a.n, G = a.G;
@@ -219,32 +222,18 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   const float alpha = (float)a.alpha_num / (float)a.alpha_den;
   const uint32_t Amax = max_sqdist(D);
 
-  for (int round = 0;; ++round) {
-  // ---- the next tile and its frame (kept in shared memory or read from the
-  // kernel parameters, not copied into registers) ----
+  {
+  // ---- this CTA's tile and its frame (kept in shared memory or read from
+  // the kernel parameters, not copied into registers) ----
   if (BATCH) {
-    __syncthreads();   // the previous tile's shared state is no longer read
-    if (threadIdx.x == 0) {
-      const int tg = (int)atomicAdd(a.counters + 1, 1u);
-      int t = -1;
-      if (tg < a.hdr->total_tiles) {
-        int lo = 0, hi = a.hdr->n_items - 1;   // last item with tile_begin <= tg
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (a.items[mid].tile_begin <= tg) lo = mid; else hi = mid - 1;
-        }
-        s_item = a.items[lo];
-        t = tg - s_item.tile_begin;
-      }
-      s_tile_id = t;
-    }
+    if (threadIdx.x == 0) s_item = a.items[a.item];
     __syncthreads();
-    if (s_tile_id < 0) break;
-  } else if (round > 0) {
-    break;
   }
   const FrameItem& it = BATCH ? s_item : a.one;
-  const int tile = BATCH ? s_tile_id : (int)blockIdx.x;
+  const int tile = (int)blockIdx.x;
+  // a batched launch is sized for the largest frame its slot has held
+  // (an empty slot has tiles_x = 0): CTAs past this frame's tiles leave
+  if (BATCH && tile >= it.tiles_x * ((it.Hq + TY - 1) / TY)) return;
   const int ty0 = (tile / it.tiles_x) * TY;
   const int tx0 = (tile % it.tiles_x) * TX;
   {
@@ -618,7 +607,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   }
   __syncthreads();
   for (int i = threadIdx.x; i < s_ndense; i += blockDim.x) a.dense_list[s_dense_base + i] = s_dense[i];
-  }   // tiles
+  }
 }
 
 template <int C, int SHAPE>
@@ -646,9 +635,10 @@ cudaError_t launch_sparse(const SparseArgs& a, int C, int shape, cudaStream_t s)
   return launch_any(a, C, shape, false, tiles, s);
 }
 
-// Persistent batched launch: as many CTAs as stay resident.
-cudaError_t launch_sparse_batch(const SparseArgs& a, int C, int shape, cudaStream_t s) {
-  return launch_any(a, C, shape, true, kCtasPerSm * sm_count(), s);
+// One frame of a batch: `tiles` CTAs, the frame's descriptor at a.items[a.item].
+cudaError_t launch_sparse_item(const SparseArgs& a, int C, int shape, int tiles, cudaStream_t s) {
+  if (tiles <= 0) return cudaSuccess;
+  return launch_any(a, C, shape, true, tiles, s);
 }
 
 }  // namespace riann
