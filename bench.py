@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-recon", action="store_true", help="skip the Sec. 4 reconstruction block")
     ap.add_argument("--no-anchor", action="store_true", help="skip the Alg. 1 random-anchor block")
     ap.add_argument("--no-other", action="store_true", help="skip the tiny and 720p RGB workloads")
+    ap.add_argument("--no-knn", action="store_true", help="skip the k-NN output block")
     ap.add_argument("--anchor-refs", type=int, default=0,
                     help="anchor block on the first N references only (small cases for profiler captures)")
     ap.add_argument("--batch-ticks", type=int, default=6, help="timed ticks of the 32-stream batched form")
@@ -543,6 +544,90 @@ def run_anchor(riann, idx, frames, H, W, stream, flush, steps: int, warm: int = 
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def run_knn(riann, idx, frames, frames_np, H, W, stream, flush, params, steps, k, R, KP, ref_field, cpu):
+    """k-NN output (Sec. 6, k best of the argmin's candidate set) on the same
+    frames: brute-force first frame, warm-up, then `steps` timed frames with
+    the L2 flushed before each; per-kernel event times; optionally the oracle
+    on a sample of positions."""
+    Q = (H - 7) * (W - 7)
+    out = [torch.empty((H - 7, W - 7), dtype=torch.int32, device=frames[0].device) for _ in range(2)]
+    kn = torch.empty((H - 7, W - 7, k), dtype=torch.int32, device=frames[0].device)
+    kd = torch.empty_like(kn)
+    warm = len(frames) - 1 - steps
+    riann.riann_profile_enable(idx, True)
+    ring_ms, dense_ms, byts, dflops = [], [], [], []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        # untimed first call: grows the k-NN scratch (allocation synchronises)
+        riann.riann_knn_frame(idx, params, frames[0], None, k, out[0], kn, kd, None, stream=stream)
+        flush.fill_(1)
+        f0 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        f0[0].record(stream)
+        riann.riann_knn_frame(idx, params, frames[0], None, k, out[0], kn, kd, None, stream=stream)
+        f0[1].record(stream)
+        prev = out[0]
+        for i in range(1, 1 + warm):
+            riann.riann_knn_frame(idx, params, frames[i], prev, k, out[i % 2], kn, kd, None, stream=stream)
+            prev = out[i % 2]
+    riann.riann_profile_read(idx, stream)
+    for j in range(steps):
+        i = 1 + warm + j
+        with torch.cuda.stream(stream):
+            flush.fill_(j & 0xff)
+            ev[j][0].record(stream)
+            riann.riann_knn_frame(idx, params, frames[i], prev, k, out[i % 2], kn, kd, None, stream=stream)
+            ev[j][1].record(stream)
+            prev = out[i % 2]
+        ms = riann.riann_profile_read(idx, stream)
+        st = riann.riann_frame_stats(idx, stream)
+        if ms[0] >= 0:
+            ring_ms.append(ms[0])
+            byts.append(ring_kernel_bytes(st, H, W, 1, R.shape[0], KP.shape[0]) + 8 * k * Q)
+        if ms[1] >= 0:
+            dense_ms.append(ms[1])
+            dflops.append(2.0 * st["dense_queries"] * R.shape[0] * 64)
+    stream.synchronize()
+    riann.riann_profile_enable(idx, False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    peaks = measured_peaks() or {}
+    hbm, bf16 = peaks.get("hbm_gbs", 6800.0), peaks.get("bf16_tflops", 1900.0)
+    ring_avg = float(np.mean(ring_ms))
+    ach = float(np.mean(byts)) / (ring_avg / 1000.0) / 1e9
+    dtf = sum(dflops) / (sum(dense_ms) / 1000.0) / 1e12 if dense_ms and sum(dense_ms) > 0 else None
+    blk = {"workload": f"the frames above, k = {k} (ids and squared distances out)",
+           "k": k, "frames": steps, "ms_per_frame": float(np.mean(step_ms)),
+           "queries_per_s": Q / (float(np.mean(step_ms)) / 1000.0),
+           "kernels_ms": {"ring": ring_avg, "dense": float(np.mean(dense_ms)) if dense_ms else None},
+           "frame0_brute_force_ms": f0[0].elapsed_time(f0[1]),
+           "first_entry_equals_argmin_field": bool(torch.equal(prev, ref_field)) if ref_field is not None else None,
+           "roofline": {"bound": "hbm", "kernel": "k_sparse k-NN variant (ring intersection + best-k list)",
+                        "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                        "algorithmic_bytes_per_launch": float(np.mean(byts))},
+           "roofline_dense": {"bound": "tensor", "kernel": "k_dense_tc k-NN variant (best-8 epilogue)",
+                              "achieved": dtf, "peak": bf16, "unit": "TFLOP/s",
+                              "frac": dtf / bf16 if dtf else None}}
+    if cpu:
+        import oracle
+        oix = oracle.Index(R, KP)
+        rng = np.random.default_rng(300)
+        qidx = np.sort(rng.choice(Q, 512, replace=False)).astype(np.int64)
+        pk, _, _ = oracle.riann_knn(oix, frames_np[0], None, k, qidx=qidx)
+        pv = np.zeros(Q, np.int32)
+        t_el, nq = 0.0, 0
+        for t in (1, 2):
+            pv[qidx] = pk[:, 0]
+            t0 = time.perf_counter()
+            pk, _, _ = oracle.riann_knn(oix, frames_np[t], pv.reshape(H - 7, W - 7), k,
+                                        alpha=(params.alpha_num, params.alpha_den),
+                                        ring_limit=params.ring_limit, qidx=qidx)
+            t_el += time.perf_counter() - t0
+            nq += len(qidx)
+        blk["oracle_queries_per_s"] = nq / t_el
+        blk["oracle_cores"] = oracle.num_threads()
+        blk["oracle_sample"] = f"512 positions over 2 frames (definitional oracle), {t_el:.1f} s"
+    return blk
+
+
 def run_ours(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -648,6 +733,13 @@ def run_ours(args, rank, world, local):
                               "achieved": alg / (rms / 1000.0) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                               "frac": alg / (rms / 1000.0) / 1e9 / hbm_peak, "algorithmic_bytes": alg}}
 
+    # k-NN output on the same frames (the last timed field is the reference
+    # for the first k-NN entry)
+    knn_line = None
+    if not args.no_knn and rank == 0:
+        knn_line = run_knn(riann, idx, frames, frames_np, H, W, stream, flush, params, min(args.steps, 10),
+                           8, R, KP, prev, world == 1 and not args.no_cpu_baseline)
+
     # Alg. 1 with random anchors over the sorted distance matrix (the paper's
     # own loop): same frames, chained from the same brute-force start
     anchor_line = None
@@ -736,6 +828,8 @@ def run_ours(args, rank, world, local):
     }
     if recon:
         line["reconstruction"] = recon
+    if knn_line:
+        line["knn"] = knn_line
     if anchor_line:
         line["anchor_loop"] = anchor_line
     clocks = clk.summary()

@@ -146,6 +146,33 @@ int riann_annf_frame(riann_index_t idx, const riann_params* p, riann_stream_t st
                      uint32_t* d_out_dist, uint32_t* d_out_count);
 
 /*
+ * k-NN variant of riann_annf_frame (Sec. 6: the method can return several
+ * close matches instead of one).  The candidate set of a query is the one the
+ * argmin of riann_annf_frame ranges over -- S u {r_p} (r_p counted once) for a
+ * ring-answered query, all n references for frame 0 and for queries routed to
+ * brute force -- and the output is its k smallest entries in ascending
+ * (distance, index) order:
+ *   k               1 <= k <= RIANN_KNN_MAX
+ *   d_out_annf      device int32 [H-7][W-7]: the first of them (required; the
+ *                   field the next frame takes as d_prev_annf, equal to
+ *                   riann_annf_frame's output)
+ *   d_out_knn       device int32 [H-7][W-7][k] (required); entries past the
+ *                   size of the candidate set are -1
+ *   d_out_knn_dist  device uint32 [H-7][W-7][k], squared distances (nullable);
+ *                   0xFFFFFFFF past the size of the candidate set
+ *   d_out_count     as riann_annf_frame
+ * Neither output may alias d_prev_annf.  The first call on a larger frame also
+ * grows the brute-force path's k-NN scratch (128 bytes per query, at least
+ * 10 MB; allocates and synchronises).  Single-frame form only (no session or batch
+ * variant).
+ */
+#define RIANN_KNN_MAX 8
+int riann_knn_frame(riann_index_t idx, const riann_params* p, riann_stream_t stream,
+                    const uint8_t* d_frame, int32_t H, int32_t W,
+                    const int32_t* d_prev_annf, int32_t k, int32_t* d_out_annf,
+                    int32_t* d_out_knn, uint32_t* d_out_knn_dist, uint32_t* d_out_count);
+
+/*
  * Brute-force exact nearest neighbour field (the dense tensor-core path on its
  * own; Alg. 1 "Initialize" replaced by exact NN).  Arguments as riann_annf_frame.
  */

@@ -58,6 +58,8 @@ def _load():
                                                       i32, i32, i32, P, i64, P, P, P, P]
             lib.oracle_riann_indexed.argtypes = [P, i32, i32, i32, P, i32, P, i32, P, P, P, P,
                                                  i32, i32, i32, P, i64, P, P, P, P]
+            lib.oracle_riann_knn.argtypes = [P, i32, i32, i32, P, i32, P, i32, P, P,
+                                             i32, i32, i32, i32, P, i64, P, P, P]
             lib.oracle_reconstruct.argtypes = [P, i32, i32, P, i32, i32, P, P, P]
             lib.oracle_philox4x32_10.argtypes = [P, P, P]
             lib.oracle_random_field.argtypes = [i32, i32, i32, ctypes.c_uint64, u32, P]
@@ -83,7 +85,7 @@ class use_library:
         self._saved = _lib
         lib = ctypes.CDLL(self.path)
         for name in ("oracle_ring_member", "oracle_key_distances", "oracle_sort_tables", "oracle_exact_nn",
-                     "oracle_riann_definitional", "oracle_riann_indexed", "oracle_reconstruct",
+                     "oracle_riann_definitional", "oracle_riann_indexed", "oracle_riann_knn", "oracle_reconstruct",
                      "oracle_philox4x32_10", "oracle_full_tables", "oracle_riann_anchor", "oracle_random_field",
                      "oracle_num_threads",
                      "oracle_set_num_threads"):
@@ -192,6 +194,28 @@ def riann_frame(index: Index, frame: np.ndarray, prev: Optional[np.ndarray],
     else:
         raise ValueError(mode)
     return annf, dist, count, nseed
+
+
+def riann_knn(index: Index, frame: np.ndarray, prev: Optional[np.ndarray], k: int,
+              alpha=(1, 4), ring_limit: int = -1, qidx=None):
+    """k-NN output of one RIANN query step: (knn [.., k] int32, knn_dist [.., k]
+    uint32, count), the k best of the argmin's candidate set (Sec. 6)."""
+    lib = _load()
+    f = _frame3(frame)
+    H, W, C = f.shape
+    assert C == index.C and k >= 1
+    q = None if qidx is None else _c(qidx, np.int64)
+    pv = None if prev is None else _c(prev, np.int32)
+    if pv is not None:
+        assert pv.shape == (H - 7, W - 7)
+    shape = (len(q),) if q is not None else (H - 7, W - 7)
+    knn = np.empty(shape + (k,), np.int32)
+    kd = np.empty(shape + (k,), np.uint32)
+    count = np.empty(shape, np.uint32)
+    lib.oracle_riann_knn(_ptr(f), H, W, C, _ptr(index.R), index.n, _ptr(index.KP), index.K,
+                         _ptr(index.P), _ptr(pv), alpha[0], alpha[1], ring_limit, k, _ptr(q),
+                         0 if q is None else len(q), _ptr(knn), _ptr(kd), _ptr(count))
+    return knn, kd, count
 
 
 def reconstruct(R: np.ndarray, annf: np.ndarray, frame: Optional[np.ndarray] = None):

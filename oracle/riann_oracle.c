@@ -233,6 +233,89 @@ void oracle_riann_definitional(const uint8_t* frame, int32_t H, int32_t W, int32
   }
 }
 
+/*
+ * k-NN output (Sec. 6: the method can return several closest matches, not
+ * only one).  The candidate set of a query is the set Alg. 1 takes its argmin
+ * over, with the readings of oracle_riann_definitional: S u {r_p} (r_p once)
+ * when some ring holds at most ring_limit references, otherwise (and for
+ * frame 0) all of R.  The output is that set sorted by (distance, index),
+ * cut to its first k entries.  Written as that definition: the ring test over
+ * all references, every candidate's distance, one sort.
+ */
+typedef struct { uint32_t d; int32_t r; } cand_t;
+
+static int cmp_cand(const void* x, const void* y) {
+  const cand_t* a = (const cand_t*)x;
+  const cand_t* b = (const cand_t*)y;
+  if (a->d != b->d) return a->d < b->d ? -1 : 1;
+  return (a->r > b->r) - (a->r < b->r);
+}
+
+void oracle_riann_knn(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                      const uint8_t* R, int32_t n,
+                      const uint8_t* KP, int32_t K, const uint32_t* P,
+                      const int32_t* prev, int32_t alpha_num, int32_t alpha_den,
+                      int32_t ring_limit, int32_t k,
+                      const int64_t* qidx, int64_t nq,
+                      int32_t* knn, uint32_t* knn_dist, uint32_t* count) {
+  const int32_t D = PATCH * PATCH * C;
+  const int32_t Wq = W - PATCH + 1;
+  const int64_t Q = (int64_t)(H - PATCH + 1) * Wq;
+  const int64_t N = qidx ? nq : Q;
+#pragma omp parallel
+  {
+    uint8_t q[PATCH * PATCH * 3];
+    uint32_t* B = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)K);
+    uint32_t* ring_size = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)K);
+    uint8_t* in_s = (uint8_t*)malloc((size_t)n);
+    cand_t* cand = (cand_t*)malloc(sizeof(cand_t) * (size_t)n);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < N; ++i) {
+      int64_t qi = query_at(qidx, i);
+      extract_query(frame, W, C, (int32_t)(qi / Wq), (int32_t)(qi % Wq), q);
+      int all = 1;                                   /* candidate set = all of R */
+      int32_t rp = -1;
+      uint32_t s_size = 0;
+      if (prev) {
+        rp = prev[qi];
+        const uint32_t Cd = sqdist(q, R + (int64_t)rp * D, D);
+        for (int32_t m = 0; m < K; ++m) {
+          B[m] = sqdist(q, KP + (int64_t)m * D, D);
+          ring_size[m] = 0;
+        }
+        for (int32_t r = 0; r < n; ++r) {
+          int inside = 1;
+          for (int32_t m = 0; m < K; ++m) {
+            int mem = oracle_ring_member(P[(int64_t)r * K + m], B[m], Cd, alpha_num, alpha_den);
+            ring_size[m] += (uint32_t)mem;
+            inside &= mem;
+          }
+          in_s[r] = (uint8_t)inside;
+          s_size += (uint32_t)inside;
+        }
+        uint32_t ns = ring_size[0];
+        for (int32_t m = 1; m < K; ++m) if (ring_size[m] < ns) ns = ring_size[m];
+        all = ring_limit >= 0 && ns > (uint32_t)ring_limit;
+      }
+      int32_t nc = 0;
+      for (int32_t r = 0; r < n; ++r) {
+        if (all || in_s[r] || r == rp) {
+          cand[nc].d = sqdist(q, R + (int64_t)r * D, D);
+          cand[nc].r = r;
+          ++nc;
+        }
+      }
+      qsort(cand, (size_t)nc, sizeof(cand_t), cmp_cand);
+      for (int32_t j = 0; j < k; ++j) {
+        knn[i * k + j] = j < nc ? cand[j].r : -1;
+        if (knn_dist) knn_dist[i * k + j] = j < nc ? cand[j].d : 0xffffffffu;
+      }
+      if (count) count[i] = all ? (uint32_t)n : s_size;
+    }
+    free(B); free(ring_size); free(in_s); free(cand);
+  }
+}
+
 /* A sorted list splits into three runs around a ring: references below it
  * (not members, A < B), the members, and references above it (not members,
  * A > B).  The members are one contiguous run because |sqrt(A) - sqrt(B)|

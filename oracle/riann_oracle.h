@@ -76,6 +76,19 @@ void oracle_riann_indexed(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
                           const int64_t* qidx, int64_t nq,
                           int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* nseed);
 
+/* k-NN output (Sec. 6, "several closest matches"): the set the argmin of
+ * oracle_riann_definitional ranges over -- S u {r_p} (r_p once), or all of R
+ * for frame 0 / rings too wide -- sorted by (dist, index) and cut to its first
+ * k entries: knn[i*k + j], knn_dist[i*k + j] (nullable); -1 / UINT32_MAX past
+ * the size of the set.  count as oracle_riann_definitional. */
+void oracle_riann_knn(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                      const uint8_t* R, int32_t n,
+                      const uint8_t* KP, int32_t K, const uint32_t* P,
+                      const int32_t* prev, int32_t alpha_num, int32_t alpha_den,
+                      int32_t ring_limit, int32_t k,
+                      const int64_t* qidx, int64_t nq,
+                      int32_t* knn, uint32_t* knn_dist, uint32_t* count);
+
 /* Reconstruction by patch replacement (Sec. 4: "replacing each patch with
  * its match and averaging overlapping patches").  out[y][x][c] = rounded
  * average over the query patches (py, px) that cover (y, x) -- py <= y < py+8,

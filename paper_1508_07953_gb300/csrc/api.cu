@@ -122,8 +122,10 @@ DenseArgs dense_args(const Index& ix, unsigned long long* stats) {
 
 // One frame on a workspace: brute force when there is no previous field,
 // else the ring kernel followed by brute force for the queries it routed.
+// k > 0: also the k-NN output (knn_idx, knn_dist [Q][k]).
 cudaError_t run_frame(Index& ix, Workspace& ws, const riann_params* p, cudaStream_t s, const FrameItem& it,
-                      unsigned long long* stats) {
+                      unsigned long long* stats, int k = 0, int32_t* knn_idx = nullptr,
+                      uint32_t* knn_dist = nullptr) {
   cudaError_t e = cudaSuccess;
   if (stats) e = cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * kStats, s);
   if (e != cudaSuccess) return e;
@@ -131,6 +133,9 @@ cudaError_t run_frame(Index& ix, Workspace& ws, const riann_params* p, cudaStrea
   DenseArgs da = dense_args(ix, stats);
   da.one = it;
   da.Q = Q;
+  da.knn = k;
+  da.knn_idx = knn_idx;
+  da.knn_dist = knn_dist;
   if (!it.prev) {
     da.list = nullptr;
     da.list_count = nullptr;
@@ -140,6 +145,9 @@ cudaError_t run_frame(Index& ix, Workspace& ws, const riann_params* p, cudaStrea
   if (e != cudaSuccess) return e;
   SparseArgs sa = sparse_args(ix, p, ws, stats);
   sa.one = it;
+  sa.knn = k;
+  sa.knn_idx = knn_idx;
+  sa.knn_dist = knn_dist;
   prof_begin(ix, kSlotSparse, s);
   e = launch_sparse(sa, ix.C, ix.tile_shape, s);
   prof_end(ix, kSlotSparse, s);
@@ -179,6 +187,9 @@ void free_workspace(Workspace& ws) {
   cudaFree(ws.best);
   cudaFree(ws.Aq);
   cudaFree(ws.qnorm);
+  cudaFree(ws.knn_lists);
+  ws.knn_lists = nullptr;
+  ws.knn_cap = 0;
   ws.dense_list = nullptr;
   ws.counters = nullptr;
   ws.best = nullptr;
@@ -208,6 +219,24 @@ int ensure_workspace(Workspace& ws, const Index& ix, int64_t Q) {
     return RIANN_ERR_UNSUPPORTED;
   }
   ws.cap_q = Q;
+  return RIANN_OK;
+}
+
+int ensure_knn_lists(Workspace& ws, int64_t Q) {
+  const int64_t need = dense_knn_list_entries(Q);
+  if (ws.knn_cap >= need) return RIANN_OK;
+  if (ws.knn_lists) {
+    cudaFree(ws.knn_lists);
+    ws.bytes -= (size_t)ws.knn_cap * sizeof(unsigned long long);
+    ws.knn_lists = nullptr;
+    ws.knn_cap = 0;
+  }
+  const cudaError_t e = dalloc(&ws.knn_lists, (size_t)need, ws.bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return from_cuda(e);
+  }
+  ws.knn_cap = need;
   return RIANN_OK;
 }
 
@@ -619,6 +648,24 @@ int riann_annf_frame(riann_index_t idx, const riann_params* p, riann_stream_t st
   if (rc) return rc;
   const FrameItem it = make_item(d_frame, d_prev_annf, d_out_annf, d_out_dist, d_out_count, H, W, ix.tile_shape);
   return from_cuda(run_frame(ix, ix.ws, p, reinterpret_cast<cudaStream_t>(stream), it, ix.stats));
+}
+
+int riann_knn_frame(riann_index_t idx, const riann_params* p, riann_stream_t stream, const uint8_t* d_frame,
+                    int32_t H, int32_t W, const int32_t* d_prev_annf, int32_t k, int32_t* d_out_annf,
+                    int32_t* d_out_knn, uint32_t* d_out_knn_dist, uint32_t* d_out_count) {
+  if (!idx || !params_ok(p) || !d_frame || !d_out_annf || !d_out_knn || !frame_ok(H, W) || k < 1 ||
+      k > RIANN_KNN_MAX || (const void*)d_prev_annf == (const void*)d_out_annf ||
+      (const void*)d_prev_annf == (const void*)d_out_knn)
+    return RIANN_ERR_INVALID_ARG;
+  Index& ix = *idx;
+  std::lock_guard<std::mutex> lock(ix.mu);
+  const int64_t Q = (int64_t)(H - 7) * (W - 7);
+  int rc = ensure_workspace(ix.ws, ix, Q);
+  if (rc == RIANN_OK) rc = ensure_knn_lists(ix.ws, Q);
+  if (rc) return rc;
+  const FrameItem it = make_item(d_frame, d_prev_annf, d_out_annf, nullptr, d_out_count, H, W, ix.tile_shape);
+  return from_cuda(run_frame(ix, ix.ws, p, reinterpret_cast<cudaStream_t>(stream), it, ix.stats, k, d_out_knn,
+                             d_out_knn_dist));
 }
 
 int riann_exact_nn(riann_index_t idx, riann_stream_t stream, const uint8_t* d_frame, int32_t H, int32_t W,

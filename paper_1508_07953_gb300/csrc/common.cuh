@@ -19,6 +19,8 @@ constexpr int kMaxDim = 192;
 constexpr int kDenseTileN = 256;   // reference rows per tensor-core tile
 constexpr int kDenseTileM = 128;   // query rows per tensor-core tile
 constexpr int kBuckets = 256;      // quantile buckets per key point (8-bit codes)
+constexpr int kKnnMax = 8;         // largest k of the k-NN output
+static_assert(kKnnMax == RIANN_KNN_MAX, "k-NN list length");
 
 // Work counters of the last frame or batch (riann_frame_stats).
 enum StatSlot { kStatRingQueries = 0, kStatDenseQueries, kStatSumSeed, kStatSumS, kStats = 8 };
@@ -62,8 +64,22 @@ struct Workspace {
   __nv_bfloat16* Aq = nullptr;          // [cap_q padded to 128][D] bf16 query rows
   uint32_t* qnorm = nullptr;            // [cap_q padded] ||q||^2
   CUtensorMap tmAq;                     // Aq rows, box 64 x 128
+  unsigned long long* knn_lists = nullptr;   // k-NN brute force: per-work-item best-8 lists
+  int64_t knn_cap = 0;                  // entries of knn_lists
   size_t bytes = 0;
 };
+
+// Reference-tile split of the brute-force launch: with fewer than two query
+// tiles per CTA, each query tile's reference tiles are shared among nsplit
+// work items.
+__host__ __device__ inline int dense_nsplit(int64_t n_qt, int grid, int n_rt) {
+  int nsplit = 1;
+  if (n_qt > 0 && n_qt < 2 * (int64_t)grid) {
+    nsplit = (int)((2 * (int64_t)grid + n_qt - 1) / n_qt);
+    if (nsplit > n_rt) nsplit = n_rt;
+  }
+  return nsplit;
+}
 
 // Device-resident index (Sec. 3.3 pre-processing restricted to K key points).
 struct Index {
@@ -132,6 +148,9 @@ struct SparseArgs {
   int n, K, Kp, G, nw;
   int alpha_num, alpha_den, ring_limit;
   int depth;                      // stage-1 filter depth (1..5)
+  int knn;                        // k of the k-NN variant (0: 1-NN path)
+  int32_t* knn_idx;               // k-NN variant: [Q][knn] matches, ascending (dist, index); -1 past |S u {r_p}|
+  uint32_t* knn_dist;             // k-NN variant: [Q][knn] their squared distances (nullable; ~0 past the end)
   int32_t* dense_list;
   uint32_t* counters;             // [0] brute-force list length
   uint32_t* status;
@@ -149,6 +168,9 @@ struct DenseArgs {
   const uint8_t* R;
   int n;
   unsigned long long* stats;      // nullable; a whole-frame launch records Q brute-force queries
+  int knn;                        // k of the k-NN output (0: argmin only); single frame only
+  int32_t* knn_idx;               // [Q][knn]
+  uint32_t* knn_dist;             // [Q][knn], nullable
 };
 
 // Record the start/end event of a profiled kernel slot (no-op when profiling is off).
@@ -159,6 +181,8 @@ void prof_end(Index& ix, int slot, cudaStream_t s);
 bool make_row_map(CUtensorMap* m, const void* base, uint64_t rows, int D, int box_rows);
 int dense_ref_rows_per_tile(int C);
 cudaError_t launch_dense_tc(const DenseArgs& a, Index& ix, Workspace& ws, cudaStream_t s);
+// entries of Workspace::knn_lists a k-NN brute-force launch over up to Q queries needs
+int64_t dense_knn_list_entries(int64_t Q);
 int64_t noalloc_max_queries(int C);
 cudaError_t launch_exact_nn_noalloc(const DenseArgs& a, Index& ix, cudaStream_t s);
 
@@ -173,6 +197,7 @@ cudaError_t launch_index_build(Index& ix, cudaStream_t s);
 
 // Workspace management (allocation synchronises the device).
 int ensure_workspace(Workspace& ws, const Index& ix, int64_t Q);
+int ensure_knn_lists(Workspace& ws, int64_t Q);
 void free_workspace(Workspace& ws);
 
 int sm_count();

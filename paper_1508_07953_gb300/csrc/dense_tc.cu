@@ -25,6 +25,8 @@
 //               quadrant, each half the columns), fused ||r||^2 - 2 q.r and a
 //               running (value, index) minimum per query row; results merge
 //               across work items with a 64-bit atomicMin on (dist << 32 | index)
+//               (k-NN variant: a running best-8 list per row and half, written
+//               per work item and merged by k_dense_knn_finish)
 // Every wait is bounded; on timeout the CTA records RIANN_DEV_TIMEOUT, drains
 // and frees its TMEM.
 #include <cuda.h>
@@ -77,8 +79,27 @@ struct TcArgs {
   int64_t Qfix;
   int n_pad;
   unsigned long long* best;       // [rows] packed (dist << 32 | index), pre-set to ~0
+  unsigned long long* lists;      // k-NN: [work items][kM][2 halves][kKnnMax] packed, ascending
   uint32_t* status;
 };
+
+// k-NN: insert score s of column c into the ascending list (s < its last
+// entry); an equal score already listed keeps its place, so that the lower
+// column comes first (each thread visits its columns in ascending order).
+template <int KM>
+__device__ __forceinline__ void knn_insert(float (&ls)[KM], int (&li)[KM], float s, int c) {
+#pragma unroll
+  for (int p = KM - 1; p > 0; --p) {
+    const bool shift = ls[p - 1] > s;
+    const bool here = !shift && ls[p] > s;
+    ls[p] = shift ? ls[p - 1] : (here ? s : ls[p]);
+    li[p] = shift ? li[p - 1] : (here ? c : li[p]);
+  }
+  if (ls[0] > s) {
+    ls[0] = s;
+    li[0] = c;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -247,7 +268,7 @@ __device__ __forceinline__ float min3(float a, float b, float c) {
 // ---------------------------------------------------------------------------
 // the GEMM + argmin kernel
 // ---------------------------------------------------------------------------
-template <int C>
+template <int C, bool KNN>
 __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant__ TcArgs a) {
   using G = Cfg<C>;
   constexpr uint32_t IDESC = instr_desc(kM, G::BN);
@@ -271,11 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
   const int64_t Qd = a.count ? (int64_t)*a.count : a.Qfix;
   const int64_t n_qt = (Qd + kM - 1) / kM;
   const int n_rt = a.n_pad / G::BN;
-  int nsplit = 1;   // split the reference tiles when there are few query tiles
-  if (n_qt > 0 && n_qt < 2 * (int64_t)gridDim.x) {
-    nsplit = (int)((2 * (int64_t)gridDim.x + n_qt - 1) / n_qt);
-    if (nsplit > n_rt) nsplit = n_rt;
-  }
+  const int nsplit = dense_nsplit(n_qt, (int)gridDim.x, n_rt);
   const int per = (n_rt + nsplit - 1) / nsplit;
   const int64_t n_items = n_qt * nsplit;
   if ((int64_t)blockIdx.x >= n_items) return;   // uniform for the whole CTA
@@ -406,6 +423,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
       const int rt0 = part * per, rt1 = min(n_rt, rt0 + per);
       float bv = __int_as_float(0x7f800000);
       int bi = 0;
+      float ls[KNN ? kKnnMax : 1];
+      int li[KNN ? kKnnMax : 1];
+#pragma unroll
+      for (int j = 0; j < (KNN ? kKnnMax : 1); ++j) {
+        ls[j] = __int_as_float(0x7f800000);
+        li[j] = 0;
+      }
       for (int rt = rt0; rt < rt1; ++rt) {
         const int colt = rt * G::BN + half * HALF;
         // RGB: ||r||^2 of this tile's first 32 columns, fetched while the MMA runs
@@ -460,13 +484,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
             const float m0 = min3(m[0], m[1], m[2]), m1 = min3(m[3], m[4], m[5]);
             const float mm2 = min3(m[6], m[7], m[8]), m3 = fminf(m[9], m[10]);
             const float cmin = fminf(min3(m0, m1, mm2), m3);
-            if (cmin < bv) {       // rare after the first tiles: locate the lowest column
-              int jj = 31;
+            if (!KNN) {
+              if (cmin < bv) {       // rare after the first tiles: locate the lowest column
+                int jj = 31;
 #pragma unroll
-              for (int j = 31; j >= 0; --j)
-                if (x[j] == cmin) jj = j;
-              bv = cmin;
-              bi = col0 + jj;
+                for (int j = 31; j >= 0; --j)
+                  if (x[j] == cmin) jj = j;
+                bv = cmin;
+                bi = col0 + jj;
+              }
+            } else if (cmin < ls[(KNN ? kKnnMax : 1) - 1]) {
+              // the columns below the current k-th, in ascending order; a
+              // lane's work follows its own count (the warp waits for the
+              // largest), not all 32 columns
+              const float thr = ls[(KNN ? kKnnMax : 1) - 1];
+              uint32_t mask = 0;
+#pragma unroll
+              for (int j = 0; j < 32; ++j) mask |= (x[j] < thr ? 1u : 0u) << j;
+              while (mask) {
+                const int jj = __ffs(mask) - 1;
+                mask &= mask - 1;
+                float v = x[0];
+#pragma unroll
+                for (int j = 1; j < 32; ++j) v = jj == j ? x[j] : v;
+                if (v < ls[(KNN ? kKnnMax : 1) - 1]) knn_insert(ls, li, v, col0 + jj);
+              }
             }
           }
         }
@@ -480,7 +522,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
       }
       const int64_t i = (int64_t)qt * kM + row;
       // padding columns score +inf (RGB) or 2^24 (gray), above every real score
-      if (ok && i < Qd && bv < 16777216.f) {
+      if (KNN) {
+        if (ok && i < Qd) {
+          unsigned long long* dst = a.lists + (((size_t)it * kM + row) * 2 + half) * kKnnMax;
+          const float qn = (float)a.qnorm[i];
+#pragma unroll
+          for (int j = 0; j < (KNN ? kKnnMax : 1); ++j)
+            dst[j] = ls[j] < 16777216.f ? ((unsigned long long)(uint32_t)(qn + ls[j]) << 32) | (unsigned)li[j]
+                                        : ~0ull;
+        }
+      } else if (ok && i < Qd && bv < 16777216.f) {
         const uint32_t dist = (uint32_t)((float)a.qnorm[i] + bv);   // exact: integer < 2^24
         atomicMin(a.best + i, ((unsigned long long)dist << 32) | (unsigned)bi);
       }
@@ -579,6 +630,73 @@ __global__ void k_dense_finish(FinishArgs a) {
   }
 }
 
+// k-NN: the k best of a query's per-(work item, half) lists -- every list
+// ascending, ties already in index order -- and the outputs.
+struct KnnFinishArgs {
+  FrameItem one;
+  const int32_t* list;
+  const uint32_t* list_count;
+  int64_t Q;
+  const unsigned long long* lists;
+  int grid, n_rt, n, k;
+  int32_t* knn_idx;
+  uint32_t* knn_dist;
+  unsigned long long* stats;
+};
+
+__global__ void k_dense_knn_finish(KnnFinishArgs a) {
+  const int64_t nq = a.list ? (int64_t)*a.list_count : a.Q;
+  if (!a.list && a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[kStatDenseQueries] = (unsigned long long)nq;
+  const int nsplit = dense_nsplit((nq + kM - 1) / kM, a.grid, a.n_rt);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t qt = i / kM;
+    const int row = (int)(i % kM);
+    unsigned long long top[kKnnMax];
+#pragma unroll
+    for (int j = 0; j < kKnnMax; ++j) top[j] = ~0ull;
+    for (int part = 0; part < nsplit; ++part) {
+      for (int half = 0; half < 2; ++half) {
+        const unsigned long long* src = a.lists + (((size_t)(qt * nsplit + part) * kM + row) * 2 + half) * kKnnMax;
+        for (int j = 0; j < kKnnMax; ++j) {
+          const unsigned long long v = src[j];
+          if (v >= top[kKnnMax - 1]) break;           // the rest of this list is larger
+#pragma unroll
+          for (int p = kKnnMax - 1; p > 0; --p) {      // insert (keys are distinct)
+            const bool shift = top[p - 1] > v;
+            top[p] = shift ? top[p - 1] : (top[p] > v ? v : top[p]);
+          }
+          if (top[0] > v) top[0] = v;
+        }
+      }
+    }
+    const int64_t gid = a.list ? (int64_t)a.list[i] : i;
+    const int64_t qi = gid - a.one.query_begin;
+#pragma unroll
+    for (int j = 0; j < kKnnMax; ++j) {
+      if (j < a.k) {
+        a.knn_idx[qi * a.k + j] = top[j] == ~0ull ? -1 : (int32_t)(top[j] & 0xffffffffu);
+        if (a.knn_dist) a.knn_dist[qi * a.k + j] = (uint32_t)(top[j] >> 32);
+      }
+    }
+    a.one.out_annf[qi] = (int32_t)(top[0] & 0xffffffffu);
+    if (a.one.out_dist) a.one.out_dist[qi] = (uint32_t)(top[0] >> 32);
+    if (a.one.out_count) a.one.out_count[qi] = (uint32_t)a.n;
+  }
+}
+
+template <int C, bool KNN>
+cudaError_t launch_tc(const TcArgs& t, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_dense_tc<C, KNN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<C>());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_dense_tc<C, KNN><<<sm_count(), kThreads, smem_bytes<C>(), s>>>(t);
+  return cudaGetLastError();
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
@@ -610,6 +728,15 @@ bool make_row_map(CUtensorMap* m, const void* base, uint64_t rows, int D, int bo
 }
 
 int dense_ref_rows_per_tile(int C) { return C == 1 ? Cfg<1>::BN : Cfg<3>::BN; }
+
+// Work items of a launch: n_qt * nsplit, at most n_qt (nsplit = 1) or below
+// 4 * grid (nsplit = ceil(2 grid / n_qt) with n_qt < 2 grid); each item holds
+// kM rows x 2 halves x kKnnMax entries.
+int64_t dense_knn_list_entries(int64_t Q) {
+  const int64_t n_qt = (Q + kM - 1) / kM;
+  const int64_t g4 = 4 * (int64_t)sm_count();
+  return (n_qt > g4 ? n_qt : g4) * kM * 2 * kKnnMax;
+}
 
 cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, Workspace& ws, cudaStream_t s) {
   if (!ix.tm_ready) return cudaErrorNotSupported;
@@ -643,25 +770,32 @@ cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, Workspace& ws, cudaSt
   t.Qfix = d.Q;
   t.n_pad = ix.n_pad;
   t.best = ws.best;
+  t.lists = ws.knn_lists;
   t.status = ix.status;
-  const int grid = sm_count();
+  const bool knn = d.knn > 0;
+  if (knn && (!ws.knn_lists || dense_knn_list_entries(d.Q) > ws.knn_cap)) return cudaErrorInvalidValue;
   prof_begin(ix, kSlotDense, s);
-  if (C == 1) {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_dense_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>());
-      attr = true;
-    }
-    k_dense_tc<1><<<grid, kThreads, smem_bytes<1>(), s>>>(t);
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      cudaFuncSetAttribute(k_dense_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<3>());
-      attr = true;
-    }
-    k_dense_tc<3><<<grid, kThreads, smem_bytes<3>(), s>>>(t);
-  }
+  cudaError_t e = C == 1 ? (knn ? launch_tc<1, true>(t, s) : launch_tc<1, false>(t, s))
+                         : (knn ? launch_tc<3, true>(t, s) : launch_tc<3, false>(t, s));
   prof_end(ix, kSlotDense, s);
+  if (e != cudaSuccess) return e;
+  if (knn) {
+    KnnFinishArgs f;
+    f.one = d.one;
+    f.list = d.list;
+    f.list_count = d.list_count;
+    f.Q = d.Q;
+    f.lists = ws.knn_lists;
+    f.grid = sm_count();
+    f.n_rt = ix.n_pad / dense_ref_rows_per_tile(C);
+    f.n = ix.n;
+    f.k = d.knn;
+    f.knn_idx = d.knn_idx;
+    f.knn_dist = d.knn_dist;
+    f.stats = d.stats;
+    k_dense_knn_finish<<<(unsigned)blocks, 256, 0, s>>>(f);
+    return cudaGetLastError();
+  }
 
   FinishArgs f;
   f.one = d.one;
@@ -789,17 +923,10 @@ cudaError_t launch_exact_nn_noalloc(const DenseArgs& d, Index& ix, cudaStream_t 
   t.Qfix = d.Q;
   t.n_pad = ix.n_pad;
   t.best = best;
+  t.lists = nullptr;
   t.status = ix.status;
-  const int grid = sm_count();
-  if (C == 1) {
-    e = cudaFuncSetAttribute(k_dense_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<1>());
-    if (e != cudaSuccess) return e;
-    k_dense_tc<1><<<grid, kThreads, smem_bytes<1>(), s>>>(t);
-  } else {
-    e = cudaFuncSetAttribute(k_dense_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<3>());
-    if (e != cudaSuccess) return e;
-    k_dense_tc<3><<<grid, kThreads, smem_bytes<3>(), s>>>(t);
-  }
+  e = C == 1 ? launch_tc<1, false>(t, s) : launch_tc<3, false>(t, s);
+  if (e != cudaSuccess) return e;
 
   FinishArgs f;
   f.one = d.one;

@@ -172,6 +172,28 @@ __device__ __forceinline__ bool codes_pass(uint32_t w, uint32_t lo4, uint32_t hi
   return ((bytes_ge(w, lo4) & bytes_ge(hi4, w)) | (any4 & kHi)) == kHi;
 }
 
+// k-NN variant: the warp's best keys so far, lane j < k holding the j-th
+// smallest (dist << 32 | index), the other lanes ~0.  Each lane offers one
+// key (~0: none); offers are merged smallest first while they beat the k-th.
+__device__ __forceinline__ void knn_merge(unsigned long long& list, unsigned long long offer, int k, int lane) {
+  unsigned long long kth = __shfl_sync(kFull, list, k - 1);
+  bool pend = offer < kth;
+  while (__any_sync(kFull, pend)) {
+    unsigned long long m = pend ? offer : ~0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(kFull, m, o);
+      m = v < m ? v : m;
+    }
+    if (offer == m) pend = false;                  // keys are distinct (distinct indices)
+    const int pos = __popc(__ballot_sync(kFull, list < m));
+    const unsigned long long up = __shfl_up_sync(kFull, list, 1);
+    if (lane < k) list = lane < pos ? list : (lane == pos ? m : up);
+    kth = __shfl_sync(kFull, list, k - 1);
+    pend = pend && offer < kth;
+  }
+}
+
 constexpr int kQueue = 256;   // per-warp ring buffer of stage-1 survivors
 constexpr int kRowBatch = 4;  // 16-byte words of a distance row loaded per round (4 keys each)
 
@@ -181,8 +203,9 @@ constexpr int kRowBatch = 4;  // 16-byte words of a distance row loaded per roun
 // the descriptor read from the device item array (entry a.item), so a
 // captured graph of the launches stays valid while the descriptors change
 // from one step to the next.  (A persistent launch taking the tiles of all
-// frames from an atomic counter measured 8 % slower.)
-template <int C, int SHAPE, bool BATCH>
+// frames from an atomic counter measured 8 % slower.)  KNN: the k-NN output
+// (the k best of S u {r_p} instead of the argmin), single-frame launches only.
+template <int C, int SHAPE, bool BATCH, bool KNN>
 __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid_constant__ SparseArgs a) {
   constexpr int TY = SHAPE == kTile4x32 ? 4 : 8;
   constexpr int TX = SHAPE == kTile4x32 ? 32 : 16;
@@ -283,6 +306,10 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         it.out_annf[qi] = -1;
         if (it.out_dist) it.out_dist[qi] = 0xffffffffu;
         if (it.out_count) it.out_count[qi] = 0u;
+      }
+      if (KNN && lane < a.knn) {
+        a.knn_idx[qi * a.knn + lane] = -1;
+        if (a.knn_dist) a.knn_dist[qi * a.knn + lane] = 0xffffffffu;
       }
       continue;
     }
@@ -444,6 +471,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     // queued entry and tests its distance row exactly against every ring,
     // lo_m <= A_m <= hi_m as one unsigned compare (A_m - lo_m <= hi_m - lo_m);
     // members are verified against the query.
+    // (k-NN: the same start -- r_p on lane 0 -- is the warp's best-k list)
     unsigned long long best = lane == 0 ? (((unsigned long long)Cd << 32) | (unsigned)rp) : ~0ull;
     uint32_t cnt = 0;
     const uint32_t* cw = a.CW + (int64_t)ms * G * a.nw;
@@ -490,15 +518,18 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
           alive = ok != 0u;
         }
       }
+      unsigned long long key = ~0ull;
       if (alive) {
         ++cnt;
         const uint4* r4 = reinterpret_cast<const uint4*>(a.R + (int64_t)r * D);
         uint32_t d = 0;
 #pragma unroll
         for (int v = 0; v < NW / 4; ++v) d = sq4(q + 4 * v, __ldg(r4 + v), d);
-        const unsigned long long key = ((unsigned long long)d << 32) | (unsigned)r;
-        best = key < best ? key : best;
+        key = ((unsigned long long)d << 32) | (unsigned)r;
+        if (!KNN) best = key < best ? key : best;
       }
+      // k-NN: r_p is on the list already (S u {r_p} is a set)
+      if (KNN) knn_merge(best, alive && r != rp ? key : ~0ull, a.knn, lane);
     };
 
     const int ja = jlo & ~3;
@@ -577,10 +608,19 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       }
       if (!more) break;
     }
+    if (KNN) {
+      if (lane < a.knn) {
+        a.knn_idx[qi * a.knn + lane] = best == ~0ull ? -1 : (int32_t)(best & 0xffffffffu);
+        if (a.knn_dist) a.knn_dist[qi * a.knn + lane] = (uint32_t)(best >> 32);
+      }
+      best = __shfl_sync(kFull, best, 0);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long v = __shfl_xor_sync(kFull, best, o);
-      best = v < best ? v : best;
+      if (!KNN) {
+        const unsigned long long v = __shfl_xor_sync(kFull, best, o);
+        best = v < best ? v : best;
+      }
       cnt += __shfl_xor_sync(kFull, cnt, o);
     }
     if (lane == 0) {
@@ -612,8 +652,9 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
 
 template <int C, int SHAPE>
 cudaError_t launch_ring(const SparseArgs& a, bool batch, int grid, cudaStream_t s) {
-  if (batch) k_sparse<C, SHAPE, true><<<grid, kWarps * 32, 0, s>>>(a);
-  else k_sparse<C, SHAPE, false><<<grid, kWarps * 32, 0, s>>>(a);
+  if (batch) k_sparse<C, SHAPE, true, false><<<grid, kWarps * 32, 0, s>>>(a);
+  else if (a.knn > 0) k_sparse<C, SHAPE, false, true><<<grid, kWarps * 32, 0, s>>>(a);
+  else k_sparse<C, SHAPE, false, false><<<grid, kWarps * 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 

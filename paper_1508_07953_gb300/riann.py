@@ -89,6 +89,7 @@ _lib.riann_index_destroy.restype = None
 _lib.riann_index_info.argtypes = [_P, ctypes.POINTER(riann_index_info_t)]
 _lib.riann_index_tables.argtypes = [_P, _P, _P, _P, _P]
 _lib.riann_annf_frame.argtypes = [_P, ctypes.POINTER(riann_params), _P, _P, _i32, _i32, _P, _P, _P, _P]
+_lib.riann_knn_frame.argtypes = [_P, ctypes.POINTER(riann_params), _P, _P, _i32, _i32, _P, _i32, _P, _P, _P, _P]
 _lib.riann_exact_nn.argtypes = [_P, _P, _P, _i32, _i32, _P, _P]
 _lib.riann_frame_stats.argtypes = [_P, _P, ctypes.POINTER(riann_frame_stats_t)]
 _lib.riann_profile_enable.argtypes = [_P, ctypes.c_int]
@@ -281,6 +282,30 @@ def riann_annf_frame(index: RiannIndex, params: riann_params, frame: torch.Tenso
            "riann_annf_frame")
 
 
+RIANN_KNN_MAX = 8
+
+
+def riann_knn_frame(index: RiannIndex, params: riann_params, frame: torch.Tensor,
+                    prev_annf: Optional[torch.Tensor], k: int, out_annf: torch.Tensor,
+                    out_knn: torch.Tensor, out_knn_dist: Optional[torch.Tensor] = None,
+                    out_count: Optional[torch.Tensor] = None,
+                    stream: Optional[torch.cuda.Stream] = None) -> None:
+    """k-NN query step (Sec. 6): out_knn / out_knn_dist [H-7][W-7][k], the k best
+    of the argmin's candidate set in ascending (distance, index) order."""
+    H, W = _frame_dims(frame, index.C)
+    Q = (H - 7) * (W - 7)
+    k = int(k)
+    Qk = Q * k if 1 <= k <= RIANN_KNN_MAX else None    # an invalid k is the library's to reject
+    _check(_lib.riann_knn_frame(index.handle, ctypes.byref(params), _stream(stream),
+                                _dev(frame, (torch.uint8,), "frame"), H, W,
+                                _dev(prev_annf, _I32, "prev_annf", Q), k,
+                                _dev(out_annf, _I32, "out_annf", Q),
+                                _dev(out_knn, _I32, "out_knn", Qk),
+                                _dev(out_knn_dist, _U32, "out_knn_dist", Qk),
+                                _dev(out_count, _U32, "out_count", Q)),
+           "riann_knn_frame")
+
+
 def riann_reconstruct(index: RiannIndex, annf: torch.Tensor, frame: Optional[torch.Tensor] = None,
                       out: Optional[torch.Tensor] = None, err2: Optional[torch.Tensor] = None,
                       stream: Optional[torch.cuda.Stream] = None) -> None:
@@ -462,6 +487,22 @@ def annf(index: RiannIndex, frame: torch.Tensor, prev: Optional[torch.Tensor],
     riann_annf_frame(index, params if params is not None else riann_default_params(index.n),
                      frame, prev, out, dist, cnt, stream)
     return out, dist, cnt
+
+
+def knn(index: RiannIndex, frame: torch.Tensor, prev: Optional[torch.Tensor], k: int,
+        params: Optional[riann_params] = None, stream=None):
+    """Allocate outputs and run one k-NN frame: returns (annf int32 [Hq][Wq],
+    knn int32 [Hq][Wq][k], knn_dist int32 [Hq][Wq][k], count int32 [Hq][Wq])."""
+    H, W = _frame_dims(frame, index.C)
+    shape = (H - 7, W - 7)
+    dev = frame.device
+    out = torch.empty(shape, dtype=torch.int32, device=dev)
+    kn = torch.empty(shape + (int(k),), dtype=torch.int32, device=dev)
+    kd = torch.empty(shape + (int(k),), dtype=torch.int32, device=dev)
+    cnt = torch.empty(shape, dtype=torch.int32, device=dev)
+    riann_knn_frame(index, params if params is not None else riann_default_params(index.n),
+                    frame, prev, k, out, kn, kd, cnt, stream)
+    return out, kn, kd, cnt
 
 
 # ---------------------------------------------------------------------------

@@ -16,6 +16,7 @@ import synth
 import test_oracle_pins as pins
 import test_oracle_reconstruct as rpins
 import test_oracle_anchor as apins
+import test_oracle_knn as kpins
 
 SRC = os.path.join(os.path.dirname(os.path.abspath(oracle.__file__)), "riann_oracle.c")
 
@@ -49,6 +50,14 @@ MUTANTS = {
     "anchor_draw_modulo": ("S[(int32_t)(((uint64_t)x[0] * (uint64_t)ns) >> 32)]", "S[(int32_t)(x[0] % (uint32_t)ns)]"),
     "anchor_loop_strict": ("while (ns >= L && (int32_t)t < max_rings)", "while (ns > L && (int32_t)t < max_rings)"),
     "philox_multiplier": ("(uint64_t)0xD2511F53u * c0", "(uint64_t)0xD2511F55u * c0"),
+    # k-NN output
+    "knn_prev_dropped": ("if (all || in_s[r] || r == rp) {", "if (all || in_s[r]) {"),
+    "knn_ties_high_index_first": ("return (a->r > b->r) - (a->r < b->r);", "return (a->r < b->r) - (a->r > b->r);"),
+    "knn_cut_one_short": ("knn[i * k + j] = j < nc ? cand[j].r : -1;", "knn[i * k + j] = j + 1 < nc ? cand[j].r : -1;"),
+    "knn_routing_off_by_one": ("all = ring_limit >= 0 && ns > (uint32_t)ring_limit;",
+                               "all = ring_limit >= 0 && ns >= (uint32_t)ring_limit;"),
+    "knn_count_includes_prev": ("if (count) count[i] = all ? (uint32_t)n : s_size;",
+                                "if (count) count[i] = all ? (uint32_t)n : s_size + 1;"),
 }
 
 
@@ -83,7 +92,15 @@ def _pins_fail() -> bool:
                apins.test_philox_known_answers, apins.test_alpha_one_is_exact_nn, apins.test_no_loop_is_first_ring_argmin,
                apins.test_identical_references_stop_at_the_ring_cap, apins.test_golden_candidate_set_of_exactly_L,
                lambda: apins.test_matches_independent_implementation((1, 4), 3),
-               lambda: apins.test_matches_independent_implementation((1, 2), 5)]
+               lambda: apins.test_matches_independent_implementation((1, 2), 5),
+               lambda: kpins.test_frame0_is_sorted_brute_force(300, 1, 12, 20, 8),
+               lambda: kpins.test_frame0_is_sorted_brute_force(5, 1, 9, 9, 8),
+               lambda: kpins.test_k1_is_the_argmin_step((1, 2), 40),
+               lambda: kpins.test_k1_is_the_argmin_step((0, 1), -1),
+               kpins.test_routed_queries_are_sorted_brute_force, kpins.test_alpha_one_prefix_is_exact_knn,
+               kpins.test_routing_at_the_limit_follows_the_argmin_step,
+               lambda: kpins.test_matches_set_assembled_from_the_ring_predicate((1, 2)),
+               kpins.test_lists_are_sorted_unique_and_padded]
     for c in checks:
         try:
             c()
