@@ -174,11 +174,11 @@ def ring_kernel_bytes(stats: dict, H: int, W: int, C: int, n: int, K: int) -> in
 # full-size ring launch, 1080p frame 21, from a one-pass ncu capture of the
 # ring-kernel sources with these SHA-256 digests; reported only while the
 # sources are unchanged.
-RING_TRAFFIC = {"bytes": 1.22e9 + 28.75e6, "frame": 21,
+RING_TRAFFIC = {"bytes": 1.22e9 + 28.85e6, "frame": 21,
                 "sha256": {"paper_1508_07953_gb300/csrc/sparse_query.cu":
-                           "6b249d76e61c7372e717fb175fd8eedb3daa0488cbc34de7e020d9a5e0cf7b1d",
+                           "4ff556aa8e33ad80e063d1a83f466d3bf93bf5c3da4820cb4c0028adabc83113",
                            "paper_1508_07953_gb300/csrc/common.cuh":
-                           "1bd15ee080a5e43403973a2418915d71b37c5255f6a693ae3c1fad4e2de3822f"}}
+                           "23aa283732205fca0ff6ffcea7fb3f5f7ba017fabd682afc21a52cf11523150a"}}
 
 
 def ring_traffic():
@@ -283,6 +283,57 @@ def run_other_configs(riann, dev, flush):
                      "gpu_frames": len(ms), "oracle_queries_per_s": q / el, "oracle_cores": oracle.num_threads(),
                      "oracle_sample": f"{min(n_samp, Q)} positions over {nf} frames, {el:.1f} s"}
     return out
+
+
+def run_spatiotemporal(riann, dev, flush, frames_t=range(17, 33)):
+    """3-D spatio-temporal patches (8x8x3 volumes over three consecutive frames)
+    of the 1080p gray video against 65536 reference volumes: per frame the
+    interleaving kernel and the query step on the stacked frame, chained, L2
+    flushed before each; the oracle on a bounded sample of the same stacks."""
+    import torch
+    w = synth.WORKLOADS["1080p_st"]
+    R = synth.workload_reference(w)
+    KP = synth.workload_keypoints(w, R)
+    v = synth.Video(w.video)
+    gray_np = [v.frame(t)[..., 0] for t in range(frames_t.start - 2, frames_t.stop)]
+    gray = [torch.from_numpy(np.ascontiguousarray(g)).to(dev) for g in gray_np]
+    H, W = gray_np[0].shape
+    Q = (H - 7) * (W - 7)
+    idx = riann.riann_build_reference_index(torch.from_numpy(R).to(dev), torch.from_numpy(KP).to(dev))
+    p = riann.riann_default_params(w.n)
+    st = torch.empty((H, W, 3), dtype=torch.uint8, device=dev)
+    bufs = [torch.empty((H - 7, W - 7), dtype=torch.int32, device=dev) for _ in range(2)]
+    prev, ms, sms = None, [], []
+    for i in range(2, len(gray)):
+        flush.fill_(i & 0xff)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        riann.riann_stack_frames(gray[i - 2], gray[i - 1], gray[i], out=st)
+        e1.record()
+        riann.riann_annf_frame(idx, p, st, prev, bufs[i % 2])
+        e2.record()
+        torch.cuda.synchronize()
+        if i >= 6:
+            ms.append(e0.elapsed_time(e2))
+            sms.append(e0.elapsed_time(e1))
+        prev = bufs[i % 2]
+    assert riann.riann_status(idx) == 0
+    idx.close()
+    import oracle
+    stacks = [oracle.stack_frames(gray_np[i - 2], gray_np[i - 1], gray_np[i]) for i in range(2, 6)]
+    oix = oracle.Index(R, KP)
+    q, el, nf = oracle_chain_rate(oracle, oix, stacks, {"alpha_num": 1, "alpha_den": 4, "ring_limit": w.n // 8},
+                                  2048, 9, 6.0)
+    hbm = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+    stack_ms = float(np.median(sms))
+    return {"workload": "1080p gray video, 8x8x3 volumes over 3 consecutive frames, n=65536 reference volumes, K=64",
+            "frames": len(ms), "ms_per_frame": float(np.mean(ms)), "queries_per_s": Q / (float(np.mean(ms)) / 1000.0),
+            "stack_kernel_ms": stack_ms,
+            "stack_roofline": {"bound": "hbm", "kernel": "k_stack3", "achieved": 6 * H * W / (stack_ms / 1000.0) / 1e9,
+                               "peak": hbm, "unit": "GB/s", "frac": 6 * H * W / (stack_ms / 1000.0) / 1e9 / hbm,
+                               "note": "event time of a 12 MB launch, dominated by launch latency"},
+            "oracle_queries_per_s": q / el, "oracle_cores": oracle.num_threads(),
+            "oracle_sample": f"2048 positions over {nf} stacked frames, {el:.1f} s"}
 
 
 def run_reference(args, rank, world):
@@ -549,6 +600,7 @@ def run_knn(riann, idx, frames, frames_np, H, W, stream, flush, params, steps, k
     frames: brute-force first frame, warm-up, then `steps` timed frames with
     the L2 flushed before each; per-kernel event times; optionally the oracle
     on a sample of positions."""
+    import torch
     Q = (H - 7) * (W - 7)
     out = [torch.empty((H - 7, W - 7), dtype=torch.int32, device=frames[0].device) for _ in range(2)]
     kn = torch.empty((H - 7, W - 7, k), dtype=torch.int32, device=frames[0].device)
@@ -848,6 +900,7 @@ def run_ours(args, rank, world, local):
     if world == 1 and not args.no_other:
         fl = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
         line["other_configs"] = run_other_configs(riann, dev, fl)
+        line["other_configs"]["1080p_spatiotemporal"] = run_spatiotemporal(riann, dev, fl)
         del fl
     print(json.dumps(line), flush=True)
     idx.close()

@@ -173,6 +173,25 @@ int riann_knn_frame(riann_index_t idx, const riann_params* p, riann_stream_t str
                     int32_t* d_out_knn, uint32_t* d_out_knn_dist, uint32_t* d_out_count);
 
 /*
+ * 3-D spatio-temporal patches (Sec. 1: the method extends from 2-D patches to
+ * spatio-temporal ones).  A query becomes the 8 x 8 x 3 volume over three
+ * consecutive gray frames, in (dy, dx, tau) order with tau = 0 the oldest.
+ * riann_stack_frames interleaves the frames into one 3-channel frame,
+ *   d_out[(y*W + x)*3 + tau] = d_f<tau>[y*W + x],
+ * whose (dy, dx, c) patches are exactly those volumes; passed with a
+ * 3-channel index of reference volumes ([n][8][8][3], the same order) to
+ * riann_annf_frame (or riann_knn_frame, or a 3-channel session), it answers
+ * the spatio-temporal query step.  A video's first two frames have no full
+ * volume: a caller that wants fields for them repeats the earliest frame.
+ *   d_f0, d_f1, d_f2  device uint8 [H][W], oldest first
+ *   d_out             device uint8 [H][W][3]; may not alias an input
+ * Asynchronous on `stream`.  Errors: RIANN_ERR_INVALID_ARG for null
+ * pointers, aliasing or H, W < 1.
+ */
+int riann_stack_frames(riann_stream_t stream, const uint8_t* d_f0, const uint8_t* d_f1, const uint8_t* d_f2,
+                       int32_t H, int32_t W, uint8_t* d_out);
+
+/*
  * Brute-force exact nearest neighbour field (the dense tensor-core path on its
  * own; Alg. 1 "Initialize" replaced by exact NN).  Arguments as riann_annf_frame.
  */

@@ -196,6 +196,17 @@ def riann_frame(index: Index, frame: np.ndarray, prev: Optional[np.ndarray],
     return annf, dist, count, nseed
 
 
+def stack_frames(f0: np.ndarray, f1: np.ndarray, f2: np.ndarray) -> np.ndarray:
+    """3-D spatio-temporal patches: out[y][x][tau] = f_tau[y][x] (tau = 0 the
+    oldest frame), so that the (dy, dx, c) patch of the result at (y, x) is the
+    8x8x3 volume of the three frames in (dy, dx, tau) order."""
+    fs = [np.asarray(f, np.uint8).reshape(f.shape[0], f.shape[1]) for f in (f0, f1, f2)]
+    out = np.empty(fs[0].shape + (3,), np.uint8)
+    for tau, f in enumerate(fs):
+        out[:, :, tau] = f
+    return out
+
+
 def riann_knn(index: Index, frame: np.ndarray, prev: Optional[np.ndarray], k: int,
               alpha=(1, 4), ring_limit: int = -1, qidx=None):
     """k-NN output of one RIANN query step: (knn [.., k] int32, knn_dist [.., k]

@@ -668,6 +668,14 @@ int riann_knn_frame(riann_index_t idx, const riann_params* p, riann_stream_t str
                              d_out_knn_dist));
 }
 
+int riann_stack_frames(riann_stream_t stream, const uint8_t* d_f0, const uint8_t* d_f1, const uint8_t* d_f2,
+                       int32_t H, int32_t W, uint8_t* d_out) {
+  if (!d_f0 || !d_f1 || !d_f2 || !d_out || H < 1 || W < 1 || (int64_t)H * W >= ((int64_t)1 << 40) ||
+      d_out == d_f0 || d_out == d_f1 || d_out == d_f2)
+    return RIANN_ERR_INVALID_ARG;
+  return from_cuda(launch_stack3(d_f0, d_f1, d_f2, (int64_t)H * W, d_out, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int riann_exact_nn(riann_index_t idx, riann_stream_t stream, const uint8_t* d_frame, int32_t H, int32_t W,
                    int32_t* d_out_annf, uint32_t* d_out_dist) {
   if (!idx || !d_frame || !d_out_annf || !frame_ok(H, W)) return RIANN_ERR_INVALID_ARG;

@@ -195,6 +195,10 @@ cudaError_t launch_sparse_item(const SparseArgs& a, int C, int shape, int tiles,
 
 cudaError_t launch_index_build(Index& ix, cudaStream_t s);
 
+// stack.cu: out[p][tau] = f_tau[p] for the npix pixels of three gray frames
+cudaError_t launch_stack3(const uint8_t* f0, const uint8_t* f1, const uint8_t* f2, int64_t npix, uint8_t* out,
+                          cudaStream_t s);
+
 // Workspace management (allocation synchronises the device).
 int ensure_workspace(Workspace& ws, const Index& ix, int64_t Q);
 int ensure_knn_lists(Workspace& ws, int64_t Q);

@@ -91,6 +91,7 @@ _lib.riann_index_tables.argtypes = [_P, _P, _P, _P, _P]
 _lib.riann_annf_frame.argtypes = [_P, ctypes.POINTER(riann_params), _P, _P, _i32, _i32, _P, _P, _P, _P]
 _lib.riann_knn_frame.argtypes = [_P, ctypes.POINTER(riann_params), _P, _P, _i32, _i32, _P, _i32, _P, _P, _P, _P]
 _lib.riann_exact_nn.argtypes = [_P, _P, _P, _i32, _i32, _P, _P]
+_lib.riann_stack_frames.argtypes = [_P, _P, _P, _P, _i32, _i32, _P]
 _lib.riann_frame_stats.argtypes = [_P, _P, ctypes.POINTER(riann_frame_stats_t)]
 _lib.riann_profile_enable.argtypes = [_P, ctypes.c_int]
 _lib.riann_profile_read.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_float), _i32]
@@ -283,6 +284,24 @@ def riann_annf_frame(index: RiannIndex, params: riann_params, frame: torch.Tenso
 
 
 RIANN_KNN_MAX = 8
+
+
+def riann_stack_frames(f0: torch.Tensor, f1: torch.Tensor, f2: torch.Tensor, out: Optional[torch.Tensor] = None,
+                       stream: Optional[torch.cuda.Stream] = None) -> torch.Tensor:
+    """3-D spatio-temporal patches: three consecutive gray frames [H][W] (or
+    [H][W][1]), oldest first, interleaved into one uint8 [H][W][3] frame whose
+    (dy, dx, c) patches are the 8x8x3 volumes in (dy, dx, tau) order."""
+    H, W = int(f0.shape[0]), int(f0.shape[1])
+    for f in (f0, f1, f2):
+        if f.numel() != H * W:
+            raise ValueError("the three frames must have the same H x W gray shape")
+    if out is None:
+        out = torch.empty((H, W, 3), dtype=torch.uint8, device=f0.device)
+    _check(_lib.riann_stack_frames(_stream(stream), _dev(f0, (torch.uint8,), "f0", H * W),
+                                   _dev(f1, (torch.uint8,), "f1", H * W), _dev(f2, (torch.uint8,), "f2", H * W),
+                                   H, W, _dev(out, (torch.uint8,), "out", 3 * H * W)),
+           "riann_stack_frames")
+    return out
 
 
 def riann_knn_frame(index: RiannIndex, params: riann_params, frame: torch.Tensor,

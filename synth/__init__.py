@@ -106,6 +106,26 @@ def reference_set(seed: int, n: int, n_images: int, H: int, W: int, C: int) -> n
     return out
 
 
+def reference_volumes(seed: int, n: int, n_videos: int, H: int, W: int, T: int = 3) -> np.ndarray:
+    """n random 8x8xT spatio-temporal cuts (T consecutive frames) of n_videos
+    synthetic gray videos: uint8 [n][8][8][T], (dy, dx, tau) order, tau = 0
+    the oldest frame.  Each video has 8 frames of region motion."""
+    rng = np.random.default_rng(seed)
+    vids = []
+    for _ in range(n_videos):
+        spec = VideoSpec(H, W, 1, int(rng.integers(1 << 30)), speeds=(0.0, 0.5, 2.0, 6.0), noise_sigma=2.0)
+        vids.append(Video(spec).frames(0, 8)[..., 0])            # [8][H][W]
+    which = rng.integers(0, n_videos, size=n)
+    ts = rng.integers(0, 8 - T + 1, size=n)
+    ys = rng.integers(0, H - PATCH + 1, size=n)
+    xs = rng.integers(0, W - PATCH + 1, size=n)
+    out = np.empty((n, PATCH, PATCH, T), dtype=np.uint8)
+    for i in range(n):
+        v = vids[which[i]][ts[i]:ts[i] + T, ys[i]:ys[i] + PATCH, xs[i]:xs[i] + PATCH]   # [T][8][8]
+        out[i] = np.moveaxis(v, 0, -1)
+    return out
+
+
 def keypoints_kmeanspp(R: np.ndarray, K: int, seed: int) -> tuple[np.ndarray, np.ndarray]:
     """k-means++ D^2 seeding over the reference set; returns (indices, patches).
 
@@ -227,6 +247,7 @@ class Workload:
     video: VideoSpec
     frames: int
     kp_seed: int = 11
+    volumes: bool = False     # references are 8x8xC spatio-temporal cuts of gray videos (C frames)
 
 
 WORKLOADS = {
@@ -244,6 +265,14 @@ WORKLOADS = {
                       VideoSpec(1080, 1920, 1, 6, speeds=(0.0, 0.5, 2.0, 6.0), noise_sigma=2.0,
                                 cut_every=40), 120),
 }
+
+# 3-D spatio-temporal patches: 8x8x3 volumes (three consecutive gray frames) of
+# the 1080p video against 65536 reference volumes cut from 16 synthetic 480x640
+# gray videos (seed 14), 64 key volumes.
+WORKLOADS["1080p_st"] = Workload("1080p_st", 65536, 64, 3, 16, (480, 640), 14, WORKLOADS["1080p"].video, 120,
+                                 volumes=True)
+WORKLOADS["tiny_st"] = Workload("tiny_st", 4096, 16, 3, 8, (128, 128), 15, WORKLOADS["tiny"].video, 8,
+                                volumes=True)
 
 # Batched form: 32 gray streams (8 at each size) sharing a 16384-patch, 32-key index;
 # per-stream speeds drawn from {0.25, 1, 4} px/frame; stream s uses seed 1000 + s.
@@ -275,6 +304,8 @@ def batch_stream_spec(s: int) -> VideoSpec:
 
 def workload_reference(w: Workload) -> np.ndarray:
     H, W = w.ref_hw
+    if w.volumes:
+        return reference_volumes(w.ref_seed, w.n, w.ref_images, H, W, w.C)
     return reference_set(w.ref_seed, w.n, w.ref_images, H, W, w.C)
 
 
