@@ -61,6 +61,8 @@ def _load():
             lib.oracle_riann_knn.argtypes = [P, i32, i32, i32, P, i32, P, i32, P, P,
                                              i32, i32, i32, i32, P, i64, P, P, P]
             lib.oracle_reconstruct.argtypes = [P, i32, i32, P, i32, i32, P, P, P]
+            lib.oracle_cluster_references.argtypes = [P, i32, i32, i32, P, P]
+            lib.oracle_cluster_references.restype = i32
             lib.oracle_philox4x32_10.argtypes = [P, P, P]
             lib.oracle_random_field.argtypes = [i32, i32, i32, ctypes.c_uint64, u32, P]
             lib.oracle_full_tables.argtypes = [P, i32, i32, P]
@@ -85,7 +87,7 @@ class use_library:
         self._saved = _lib
         lib = ctypes.CDLL(self.path)
         for name in ("oracle_ring_member", "oracle_key_distances", "oracle_sort_tables", "oracle_exact_nn",
-                     "oracle_riann_definitional", "oracle_riann_indexed", "oracle_riann_knn", "oracle_reconstruct",
+                     "oracle_riann_definitional", "oracle_riann_indexed", "oracle_riann_knn", "oracle_reconstruct", "oracle_cluster_references",
                      "oracle_philox4x32_10", "oracle_full_tables", "oracle_riann_anchor", "oracle_random_field",
                      "oracle_num_threads",
                      "oracle_set_num_threads"):
@@ -194,6 +196,19 @@ def riann_frame(index: Index, frame: np.ndarray, prev: Optional[np.ndarray],
     else:
         raise ValueError(mode)
     return annf, dist, count, nseed
+
+
+def cluster_references(X: np.ndarray, leaf: int):
+    """Sec. 3.4 reference-set construction: (reps uint8 [m][...patch shape],
+    assign int32 [n]) of the regression-tree clustering of the n patches X."""
+    lib = _load()
+    Xc = _c(X, np.uint8)
+    n = Xc.shape[0]
+    D = int(np.prod(Xc.shape[1:])) if n else int(np.prod(X.shape[1:]))
+    reps = np.empty((max(n, 1), D), np.uint8)
+    assign = np.empty(max(n, 1), np.int32)
+    m = lib.oracle_cluster_references(_ptr(Xc), n, D, leaf, _ptr(reps), _ptr(assign))
+    return reps[:m].reshape((m,) + tuple(X.shape[1:])), assign[:n]
 
 
 def stack_frames(f0: np.ndarray, f1: np.ndarray, f2: np.ndarray) -> np.ndarray:

@@ -316,6 +316,101 @@ void oracle_riann_knn(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
   }
 }
 
+/*
+ * Reference-set construction (Sec. 3.4: the collected patches are clustered
+ * with a high-dimensional regression tree and each cluster is represented by
+ * its median).  Reading taken here, all in integers on the uint8 patches:
+ *   a node with more than `leaf` patches splits on the coordinate of largest
+ *   variance (cnt * sum x^2 - (sum x)^2, lowest coordinate on ties) at the
+ *   lower median m of that coordinate (the value of rank (cnt-1)/2):
+ *   left = {x <= m} when that leaves the right side non-empty, else
+ *   left = {x < m}; both sides keep their input order;
+ *   a node is a leaf when it holds at most `leaf` patches or no coordinate
+ *   varies;
+ *   the leaves, in the order of the final arrangement (left before right),
+ *   are the clusters; a cluster's representative is its per-coordinate lower
+ *   median.  (The paper also normalises representatives to unit length; the
+ *   uint8 reading of the query step drops that.)
+ * assign[i] = cluster of input patch i.  Returns the number of clusters.
+ */
+static int cmp_u8(const void* x, const void* y) {
+  return (int)*(const uint8_t*)x - (int)*(const uint8_t*)y;
+}
+
+static uint8_t lower_median(uint8_t* v, int32_t cnt) {
+  qsort(v, (size_t)cnt, 1, cmp_u8);
+  return v[(cnt - 1) / 2];
+}
+
+int32_t oracle_cluster_references(const uint8_t* X, int32_t n, int32_t D, int32_t leaf,
+                                  uint8_t* reps, int32_t* assign) {
+  int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  uint8_t* vals = (uint8_t*)malloc((size_t)(n > 0 ? n : 1));
+  int32_t* stack = (int32_t*)malloc(sizeof(int32_t) * 2 * (size_t)(n + 1));
+  for (int32_t i = 0; i < n; ++i) perm[i] = i;
+  int32_t top = 0, nclusters = 0;
+  if (n > 0) { stack[0] = 0; stack[1] = n; top = 1; }
+  while (top > 0) {                               /* depth first, left child first */
+    --top;
+    const int32_t b = stack[2 * top], e = stack[2 * top + 1], cnt = e - b;
+    int32_t best_d = -1;
+    unsigned long long best_v = 0;
+    if (cnt > leaf) {
+      for (int32_t d = 0; d < D; ++d) {
+        unsigned long long s = 0, s2 = 0;
+        for (int32_t i = b; i < e; ++i) {
+          const unsigned long long x = X[(int64_t)perm[i] * D + d];
+          s += x; s2 += x * x;
+        }
+        const unsigned long long v = (unsigned long long)cnt * s2 - s * s;
+        if (v > best_v) { best_v = v; best_d = d; }
+      }
+    }
+    uint8_t m = 0;
+    int strict = 0;
+    int32_t nl = 0;
+    if (best_d >= 0) {
+      for (int32_t i = b; i < e; ++i) vals[i - b] = X[(int64_t)perm[i] * D + best_d];
+      m = lower_median(vals, cnt);
+      int32_t nle = 0;
+      for (int32_t i = b; i < e; ++i) nle += X[(int64_t)perm[i] * D + best_d] <= m;
+      strict = nle == cnt;                        /* everything <= m: split off the values below m */
+      for (int32_t i = b; i < e; ++i) {
+        const uint8_t x = X[(int64_t)perm[i] * D + best_d];
+        nl += strict ? x < m : x <= m;
+      }
+      /* both sides are non-empty whenever the coordinate varies; a split that
+       * would leave one empty is never made */
+      if (nl == 0 || nl == cnt) best_d = -1;
+    }
+    if (best_d < 0) {                             /* a leaf: one cluster */
+      for (int32_t d = 0; d < D; ++d) {
+        for (int32_t i = b; i < e; ++i) vals[i - b] = X[(int64_t)perm[i] * D + d];
+        reps[(int64_t)nclusters * D + d] = lower_median(vals, cnt);
+      }
+      for (int32_t i = b; i < e; ++i) if (assign) assign[perm[i]] = nclusters;
+      ++nclusters;
+      continue;
+    }
+    int32_t nw = 0;
+    for (int32_t i = b; i < e; ++i) {
+      const uint8_t x = X[(int64_t)perm[i] * D + best_d];
+      if (strict ? x < m : x <= m) tmp[b + nw++] = perm[i];
+    }
+    int32_t nr = nl;
+    for (int32_t i = b; i < e; ++i) {
+      const uint8_t x = X[(int64_t)perm[i] * D + best_d];
+      if (!(strict ? x < m : x <= m)) tmp[b + nr++] = perm[i];
+    }
+    for (int32_t i = b; i < e; ++i) perm[i] = tmp[i];
+    stack[2 * top] = b + nl; stack[2 * top + 1] = e; ++top;     /* right, processed after left */
+    stack[2 * top] = b; stack[2 * top + 1] = b + nl; ++top;
+  }
+  free(perm); free(tmp); free(vals); free(stack);
+  return nclusters;
+}
+
 /* A sorted list splits into three runs around a ring: references below it
  * (not members, A < B), the members, and references above it (not members,
  * A > B).  The members are one contiguous run because |sqrt(A) - sqrt(B)|

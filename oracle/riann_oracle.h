@@ -89,6 +89,18 @@ void oracle_riann_knn(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
                       const int64_t* qidx, int64_t nq,
                       int32_t* knn, uint32_t* knn_dist, uint32_t* count);
 
+/* Reference-set construction (Sec. 3.4: regression-tree clusters, each
+ * represented by its median).  X: n patches of D bytes.  A node with more
+ * than `leaf` patches splits on its coordinate of largest variance (integer
+ * cnt*sum(x^2) - sum(x)^2, lowest coordinate on ties) at that coordinate's
+ * lower median m: {x <= m} go left unless that is every patch, then {x < m};
+ * order is kept on both sides.  Leaves (at most `leaf` patches, or no
+ * variance) in left-to-right order are the clusters; reps[c*D + d] = lower
+ * median of coordinate d over cluster c; assign[i] (nullable) = cluster of
+ * patch i.  Returns the number of clusters (reps must hold n rows). */
+int32_t oracle_cluster_references(const uint8_t* X, int32_t n, int32_t D, int32_t leaf,
+                                  uint8_t* reps, int32_t* assign);
+
 /* Reconstruction by patch replacement (Sec. 4: "replacing each patch with
  * its match and averaging overlapping patches").  out[y][x][c] = rounded
  * average over the query patches (py, px) that cover (y, x) -- py <= y < py+8,

@@ -17,6 +17,7 @@ import test_oracle_pins as pins
 import test_oracle_reconstruct as rpins
 import test_oracle_anchor as apins
 import test_oracle_knn as kpins
+import test_oracle_cluster as cpins
 
 SRC = os.path.join(os.path.dirname(os.path.abspath(oracle.__file__)), "riann_oracle.c")
 
@@ -58,6 +59,15 @@ MUTANTS = {
                                "all = ring_limit >= 0 && ns >= (uint32_t)ring_limit;"),
     "knn_count_includes_prev": ("if (count) count[i] = all ? (uint32_t)n : s_size;",
                                 "if (count) count[i] = all ? (uint32_t)n : s_size + 1;"),
+    # reference-set clustering
+    "cluster_variance_unsquared_mean": ("const unsigned long long v = (unsigned long long)cnt * s2 - s * s;",
+                                        "const unsigned long long v = s2 - s;"),
+    "cluster_upper_median": ("return v[(cnt - 1) / 2];", "return v[cnt / 2];"),
+    "cluster_tie_high_coordinate": ("if (v > best_v) { best_v = v; best_d = d; }", "if (v >= best_v && v) { best_v = v; best_d = d; }"),
+    "cluster_no_strict_fallback": ("strict = nle == cnt;", "strict = 0;"),
+    "cluster_leaf_off_by_one": ("if (cnt > leaf) {", "if (cnt >= leaf) {"),
+    "cluster_right_first": ("stack[2 * top] = b + nl; stack[2 * top + 1] = e; ++top;     /* right, processed after left */\n    stack[2 * top] = b; stack[2 * top + 1] = b + nl; ++top;",
+                            "stack[2 * top] = b; stack[2 * top + 1] = b + nl; ++top;\n    stack[2 * top] = b + nl; stack[2 * top + 1] = e; ++top;"),
 }
 
 
@@ -100,7 +110,13 @@ def _pins_fail() -> bool:
                kpins.test_routed_queries_are_sorted_brute_force, kpins.test_alpha_one_prefix_is_exact_knn,
                kpins.test_routing_at_the_limit_follows_the_argmin_step,
                lambda: kpins.test_matches_set_assembled_from_the_ring_predicate((1, 2)),
-               kpins.test_lists_are_sorted_unique_and_padded]
+               kpins.test_lists_are_sorted_unique_and_padded,
+               lambda: cpins.test_partition_sizes_and_medians(1000, 64, 16, 0),
+               lambda: cpins.test_partition_sizes_and_medians(64, 64, 64, 2),
+               cpins.test_few_patches_one_cluster, cpins.test_identical_patches_do_not_split,
+               cpins.test_two_separated_groups, cpins.test_single_varying_coordinate_gives_value_ranges,
+               cpins.test_split_on_largest_variance, cpins.test_tied_variance_splits_lowest_coordinate,
+               cpins.test_all_at_or_below_the_median_splits_strictly]
     for c in checks:
         try:
             c()
