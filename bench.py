@@ -336,6 +336,30 @@ def run_spatiotemporal(riann, dev, flush, frames_t=range(17, 33)):
             "oracle_sample": f"2048 positions over {nf} stacked frames, {el:.1f} s"}
 
 
+def run_clustering(riann, dev, n=262144, leaf=4):
+    """Sec. 3.4 reference-set construction: n synthetic 8x8 gray cuts clustered
+    to regression-tree leaves of at most `leaf` patches, median representatives;
+    the whole call timed (it synchronises), then the oracle on the same input."""
+    import torch
+    X = synth.reference_set(16, n, 32, 480, 640, 1)
+    Xd = torch.from_numpy(X).to(dev)
+    riann.riann_cluster_references(Xd[:4096], leaf)           # warm-up (module load, allocator)
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        reps, assign = riann.riann_cluster_references(Xd, leaf)
+        ts.append(time.perf_counter() - t0)
+    import oracle
+    t0 = time.perf_counter()
+    oreps, oassign = oracle.cluster_references(X, leaf)
+    t_or = time.perf_counter() - t0
+    equal = bool(np.array_equal(reps.cpu().numpy(), oreps) and np.array_equal(assign.cpu().numpy(), oassign))
+    return {"workload": f"{n} synthetic 8x8 gray cuts (32 scenes of 480x640), leaves of at most {leaf}",
+            "clusters": int(reps.shape[0]), "gpu_ms": 1000.0 * float(np.median(ts)),
+            "oracle_ms": 1000.0 * t_or, "oracle_cores": 1, "equal_to_oracle": equal,
+            "note": "wall time of the synchronous call: one split launch and one 4-byte read per tree level"}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle on the same frames, one bounded sample
     of query positions chained over the timed frames."""
@@ -901,6 +925,7 @@ def run_ours(args, rank, world, local):
         fl = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
         line["other_configs"] = run_other_configs(riann, dev, fl)
         line["other_configs"]["1080p_spatiotemporal"] = run_spatiotemporal(riann, dev, fl)
+        line["other_configs"]["reference_clustering"] = run_clustering(riann, dev)
         del fl
     print(json.dumps(line), flush=True)
     idx.close()

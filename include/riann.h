@@ -173,6 +173,31 @@ int riann_knn_frame(riann_index_t idx, const riann_params* p, riann_stream_t str
                     int32_t* d_out_knn, uint32_t* d_out_knn_dist, uint32_t* d_out_count);
 
 /*
+ * Reference-set construction (Sec. 3.4: the collected patches are clustered
+ * with a high-dimensional regression tree, each cluster represented by its
+ * median).  Integer reading on the uint8 patches: a node with more than
+ * `leaf` patches splits on its coordinate of largest variance
+ * (cnt * sum x^2 - (sum x)^2, lowest coordinate on ties) at that
+ * coordinate's lower median m (the value of rank (cnt-1)/2): {x <= m} go
+ * left, or {x < m} when that would be every patch; both sides keep their
+ * order.  Leaves (at most `leaf` patches, or no varying coordinate) are the
+ * clusters, numbered left to right; a cluster's representative is its
+ * per-coordinate lower median.  (The paper also scales representatives to
+ * unit length; the uint8 query path has no use for that.)
+ *   d_patches     device uint8 [n][8][8][channels], 1 <= n, channels 1 or 3
+ *   leaf          largest cluster that is not split further, >= 1
+ *   d_out_reps    device uint8 [n][8][8][channels] (room for n clusters); rows
+ *                 0 .. *out_count - 1 receive the representatives
+ *   d_out_assign  device int32 [n], cluster of each input patch (nullable)
+ *   out_count     host: number of clusters
+ * Synchronous: allocates its scratch (4 x 4 + 1 bytes per patch plus two
+ * node lists), builds the tree level by level (one launch and one small
+ * device-to-host read per level) and returns when the outputs are written.
+ */
+int riann_cluster_references(riann_stream_t stream, const uint8_t* d_patches, int32_t n, int32_t channels,
+                             int32_t leaf, uint8_t* d_out_reps, int32_t* d_out_assign, int32_t* out_count);
+
+/*
  * 3-D spatio-temporal patches (Sec. 1: the method extends from 2-D patches to
  * spatio-temporal ones).  A query becomes the 8 x 8 x 3 volume over three
  * consecutive gray frames, in (dy, dx, tau) order with tau = 0 the oldest.

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libriann.so")
-SOURCES = ["api.cu", "index_build.cu", "sparse_query.cu", "dense_tc.cu", "server.cu", "reconstruct.cu", "stack.cu",
+SOURCES = ["api.cu", "index_build.cu", "sparse_query.cu", "dense_tc.cu", "server.cu", "reconstruct.cu", "stack.cu", "cluster.cu",
            "anchor.cu"]
 HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(ROOT, "include", "riann.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -668,6 +668,16 @@ int riann_knn_frame(riann_index_t idx, const riann_params* p, riann_stream_t str
                              d_out_knn_dist));
 }
 
+int riann_cluster_references(riann_stream_t stream, const uint8_t* d_patches, int32_t n, int32_t channels,
+                             int32_t leaf, uint8_t* d_out_reps, int32_t* d_out_assign, int32_t* out_count) {
+  if (out_count) *out_count = 0;
+  if (!d_patches || !d_out_reps || !out_count || n < 1 || (channels != 1 && channels != 3) || leaf < 1 ||
+      (const void*)d_out_reps == (const void*)d_patches)
+    return RIANN_ERR_INVALID_ARG;
+  return from_cuda(cluster_references(d_patches, n, channels, leaf, d_out_reps, d_out_assign, out_count,
+                                      reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int riann_stack_frames(riann_stream_t stream, const uint8_t* d_f0, const uint8_t* d_f1, const uint8_t* d_f2,
                        int32_t H, int32_t W, uint8_t* d_out) {
   if (!d_f0 || !d_f1 || !d_f2 || !d_out || H < 1 || W < 1 || (int64_t)H * W >= ((int64_t)1 << 40) ||

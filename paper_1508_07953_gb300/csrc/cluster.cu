@@ -1,0 +1,280 @@
+// cluster.cu -- reference-set construction (Sec. 3.4): the collected patches
+// are clustered with a high-dimensional regression tree and every cluster is
+// represented by its median.  Integer reading on uint8 patches:
+//   * a node with more than `leaf` patches splits on its coordinate of
+//     largest variance, cnt * sum(x^2) - sum(x)^2 (lowest coordinate on ties),
+//     at that coordinate's lower median m (the value of rank (cnt-1)/2):
+//     {x <= m} go left, or {x < m} when that would be every patch; both sides
+//     keep their order;
+//   * a node is a leaf when it holds at most `leaf` patches or no coordinate
+//     varies; the leaves, left to right, are the clusters;
+//   * a cluster's representative is its per-coordinate lower median.
+//
+// The tree is built level by level over one index array: every node is a
+// contiguous range of it.  k_split (one CTA per node of the level) sums x and
+// x^2 per coordinate, picks the coordinate, finds m from a 256-bin histogram
+// (the values are bytes: no sort), and partitions its range stably with warp
+// ballots into a scratch copy; the children go to the next level's node list.
+// A leaf marks its first position.  Leaves are then enumerated in position
+// order (k_leaf_scan), and k_reps takes one warp per leaf: lower medians by a
+// binary search over the 256 byte values with ballot counts.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace riann {
+namespace {
+
+constexpr int kSplitThreads = 256;
+
+template <int D>
+__global__ void __launch_bounds__(kSplitThreads) k_split(const uint8_t* __restrict__ X, int32_t* perm,
+                                                         int32_t* tmp, uint8_t* leaf_start,
+                                                         const int2* __restrict__ segs_in, int2* segs_out,
+                                                         uint32_t* n_out, int leaf) {
+  constexpr int G = kSplitThreads / D;   // threads per coordinate in the sums
+  __shared__ unsigned long long s1[D], s2[D];
+  __shared__ uint32_t hist[256];
+  __shared__ int s_dim, s_m, s_strict, s_nl;
+  __shared__ uint32_t s_wl[kSplitThreads / 32], s_wr[kSplitThreads / 32];
+  const int2 sg = segs_in[blockIdx.x];
+  const int b = sg.x, e = sg.y, cnt = e - b;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (cnt <= leaf) {
+    if (tid == 0) leaf_start[b] = 1;
+    return;
+  }
+  for (int i = tid; i < D; i += blockDim.x) s1[i] = s2[i] = 0ull;
+  for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0u;
+  __syncthreads();
+  if (tid < G * D) {
+    const int g = tid / D, d = tid % D;
+    unsigned long long a1 = 0, a2 = 0;
+    for (int i = g; i < cnt; i += G) {
+      const unsigned x = __ldg(X + (int64_t)perm[b + i] * D + d);
+      a1 += x;
+      a2 += x * x;
+    }
+    atomicAdd(&s1[d], a1);
+    atomicAdd(&s2[d], a2);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long bv = 0;
+    int bd = D;
+    for (int d = lane; d < D; d += 32) {
+      const unsigned long long v = (unsigned long long)cnt * s2[d] - s1[d] * s1[d];
+      if (v > bv) {   // ascending d per lane: keeps the lowest on ties
+        bv = v;
+        bd = d;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long ov = __shfl_xor_sync(0xffffffffu, bv, o);
+      const int od = __shfl_xor_sync(0xffffffffu, bd, o);
+      if (ov > bv || (ov == bv && od < bd)) {
+        bv = ov;
+        bd = od;
+      }
+    }
+    if (lane == 0) s_dim = bv ? bd : -1;
+  }
+  __syncthreads();
+  const int d = s_dim;
+  if (d < 0) {   // no coordinate varies
+    if (tid == 0) leaf_start[b] = 1;
+    return;
+  }
+  for (int i = tid; i < cnt; i += blockDim.x) atomicAdd(&hist[__ldg(X + (int64_t)perm[b + i] * D + d)], 1u);
+  __syncthreads();
+  if (tid == 0) {
+    const uint32_t r = (uint32_t)(cnt - 1) / 2;
+    uint32_t cum = 0;
+    int m = 0;
+    for (; m < 256; ++m) {
+      cum += hist[m];
+      if (cum > r) break;
+    }
+    const int strict = cum == (uint32_t)cnt;   // everything <= m: the values below m split off
+    const int nl = strict ? (int)(cum - hist[m]) : (int)cum;
+    s_m = m;
+    s_strict = strict;
+    // both sides are non-empty whenever the coordinate varies; a split that
+    // would leave one empty is never made
+    s_nl = (nl == 0 || nl == cnt) ? -1 : nl;
+  }
+  __syncthreads();
+  const int m = s_m, strict = s_strict, nl = s_nl;
+  if (nl < 0) {
+    if (tid == 0) leaf_start[b] = 1;
+    return;
+  }
+  // stable partition into tmp[b, e), then back into perm
+  int lbase = 0, rbase = 0;
+  for (int c0 = 0; c0 < cnt; c0 += blockDim.x) {
+    const int i = c0 + tid;
+    const bool valid = i < cnt;
+    const int32_t p = valid ? perm[b + i] : 0;
+    const int x = valid ? (int)__ldg(X + (int64_t)p * D + d) : 0;
+    const bool left = valid && (strict ? x < m : x <= m);
+    const bool right = valid && !left;
+    const unsigned bl = __ballot_sync(0xffffffffu, left), br = __ballot_sync(0xffffffffu, right);
+    const unsigned lt = (1u << lane) - 1u;
+    if (lane == 0) {
+      s_wl[warp] = __popc(bl);
+      s_wr[warp] = __popc(br);
+    }
+    __syncthreads();
+    int offl = 0, offr = 0, totl = 0, totr = 0;
+#pragma unroll
+    for (int w = 0; w < kSplitThreads / 32; ++w) {
+      const int a = (int)s_wl[w], c = (int)s_wr[w];
+      if (w < warp) {
+        offl += a;
+        offr += c;
+      }
+      totl += a;
+      totr += c;
+    }
+    if (left) tmp[b + lbase + offl + __popc(bl & lt)] = p;
+    if (right) tmp[b + nl + rbase + offr + __popc(br & lt)] = p;
+    lbase += totl;
+    rbase += totr;
+    __syncthreads();   // s_wl / s_wr are rewritten by the next chunk
+  }
+  for (int i = tid; i < cnt; i += blockDim.x) perm[b + i] = tmp[b + i];
+  if (tid == 0) {
+    const uint32_t k = atomicAdd(n_out, 2u);
+    segs_out[k] = make_int2(b, b + nl);
+    segs_out[k + 1] = make_int2(b + nl, e);
+  }
+}
+
+// Leaves in position order: leaf_begin[k] = first position of leaf k, *count = leaves.
+__global__ void __launch_bounds__(1024) k_leaf_scan(const uint8_t* __restrict__ leaf_start, int n,
+                                                    int32_t* leaf_begin, uint32_t* count) {
+  __shared__ uint32_t s_w[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int base = 0;
+  for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+    const int i = c0 + tid;
+    const bool f = i < n && leaf_start[i];
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) s_w[warp] = __popc(bal);
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int w = 0; w < 32; ++w) {
+      if (w < warp) off += (int)s_w[w];
+      tot += (int)s_w[w];
+    }
+    if (f) leaf_begin[base + off + __popc(bal & ((1u << lane) - 1u))] = i;
+    base += tot;
+    __syncthreads();
+  }
+  if (tid == 0) *count = (uint32_t)base;
+}
+
+// One warp per leaf: its members' cluster id and its per-coordinate lower median.
+template <int D>
+__global__ void __launch_bounds__(256) k_reps(const uint8_t* __restrict__ X, const int32_t* __restrict__ perm,
+                                              const int32_t* __restrict__ leaf_begin, const uint32_t* count,
+                                              int n, uint8_t* reps, int32_t* assign) {
+  const int lane = threadIdx.x & 31;
+  const int L = (int)*count;
+  const int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (k >= L) return;
+  const int start = leaf_begin[k], end = k + 1 < L ? leaf_begin[k + 1] : n, cnt = end - start;
+  if (assign)
+    for (int i = lane; i < cnt; i += 32) assign[perm[start + i]] = k;
+  const int r = (cnt - 1) / 2;
+  const int32_t p0 = lane < cnt ? perm[start + lane] : 0;   // the first 32 members, kept in a register
+  for (int d = 0; d < D; ++d) {
+    const int x0 = lane < cnt ? (int)__ldg(X + (int64_t)p0 * D + d) : 256;
+    int lo = 0, hi = 255;
+    while (lo < hi) {   // smallest v with #{x <= v} > r
+      const int mid = (lo + hi) >> 1;
+      int c = __popc(__ballot_sync(0xffffffffu, x0 <= mid));
+      for (int i = 32; i < cnt; i += 32) {                      // members past the first 32
+        const int j = i + lane;
+        const int x = j < cnt ? (int)__ldg(X + (int64_t)perm[start + j] * D + d) : 256;
+        c += __popc(__ballot_sync(0xffffffffu, x <= mid));
+      }
+      if (c > r) hi = mid;
+      else lo = mid + 1;
+    }
+    if (lane == 0) reps[(int64_t)k * D + d] = (uint8_t)lo;
+  }
+}
+
+__global__ void k_iota(int32_t* p, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = i;
+}
+
+template <int D>
+cudaError_t run_tree(const uint8_t* X, int n, int leaf, int32_t* perm, int32_t* tmp, uint8_t* leaf_start,
+                     int2* segs0, int2* segs1, uint32_t* cnts, int32_t* leaf_begin, uint8_t* reps, int32_t* assign,
+                     int32_t* out_count, cudaStream_t s) {
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
+  k_iota<<<blocks, 256, 0, s>>>(perm, n);
+  cudaError_t e = cudaMemsetAsync(leaf_start, 0, (size_t)n, s);
+  const int2 root = make_int2(0, n);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(segs0, &root, sizeof(int2), cudaMemcpyHostToDevice, s);
+  int2* in = segs0;
+  int2* out = segs1;
+  uint32_t nseg = 1;
+  while (e == cudaSuccess && nseg > 0) {
+    e = cudaMemsetAsync(cnts, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) break;
+    k_split<D><<<nseg, kSplitThreads, 0, s>>>(X, perm, tmp, leaf_start, in, out, cnts, leaf);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nseg, cnts, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    std::swap(in, out);
+  }
+  if (e != cudaSuccess) return e;
+  k_leaf_scan<<<1, 1024, 0, s>>>(leaf_start, n, leaf_begin, cnts + 1);
+  uint32_t L = 0;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&L, cnts + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  k_reps<D><<<(L + 7) / 8, 256, 0, s>>>(X, perm, leaf_begin, cnts + 1, n, reps, assign);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  *out_count = (int32_t)L;
+  return e;
+}
+
+}  // namespace
+
+cudaError_t cluster_references(const uint8_t* X, int n, int C, int leaf, uint8_t* reps, int32_t* assign,
+                               int32_t* out_count, cudaStream_t s) {
+  int32_t *perm = nullptr, *tmp = nullptr, *leaf_begin = nullptr;
+  uint8_t* leaf_start = nullptr;
+  int2 *segs0 = nullptr, *segs1 = nullptr;
+  uint32_t* cnts = nullptr;
+  cudaError_t e = cudaMalloc(&perm, sizeof(int32_t) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(int32_t) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&leaf_begin, sizeof(int32_t) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&leaf_start, (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&segs0, sizeof(int2) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&segs1, sizeof(int2) * (size_t)n);
+  if (e == cudaSuccess) e = cudaMalloc(&cnts, sizeof(uint32_t) * 2);
+  if (e == cudaSuccess)
+    e = C == 1 ? run_tree<64>(X, n, leaf, perm, tmp, leaf_start, segs0, segs1, cnts, leaf_begin, reps, assign,
+                              out_count, s)
+               : run_tree<192>(X, n, leaf, perm, tmp, leaf_start, segs0, segs1, cnts, leaf_begin, reps, assign,
+                               out_count, s);
+  cudaStreamSynchronize(s);
+  cudaFree(perm);
+  cudaFree(tmp);
+  cudaFree(leaf_begin);
+  cudaFree(leaf_start);
+  cudaFree(segs0);
+  cudaFree(segs1);
+  cudaFree(cnts);
+  return e;
+}
+
+}  // namespace riann

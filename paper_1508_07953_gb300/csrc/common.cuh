@@ -195,6 +195,10 @@ cudaError_t launch_sparse_item(const SparseArgs& a, int C, int shape, int tiles,
 
 cudaError_t launch_index_build(Index& ix, cudaStream_t s);
 
+// cluster.cu: Sec. 3.4 reference-set construction (synchronises `s`)
+cudaError_t cluster_references(const uint8_t* X, int n, int C, int leaf, uint8_t* reps, int32_t* assign,
+                               int32_t* out_count, cudaStream_t s);
+
 // stack.cu: out[p][tau] = f_tau[p] for the npix pixels of three gray frames
 cudaError_t launch_stack3(const uint8_t* f0, const uint8_t* f1, const uint8_t* f2, int64_t npix, uint8_t* out,
                           cudaStream_t s);

@@ -92,6 +92,7 @@ _lib.riann_annf_frame.argtypes = [_P, ctypes.POINTER(riann_params), _P, _P, _i32
 _lib.riann_knn_frame.argtypes = [_P, ctypes.POINTER(riann_params), _P, _P, _i32, _i32, _P, _i32, _P, _P, _P, _P]
 _lib.riann_exact_nn.argtypes = [_P, _P, _P, _i32, _i32, _P, _P]
 _lib.riann_stack_frames.argtypes = [_P, _P, _P, _P, _i32, _i32, _P]
+_lib.riann_cluster_references.argtypes = [_P, _P, _i32, _i32, _i32, _P, _P, ctypes.POINTER(_i32)]
 _lib.riann_frame_stats.argtypes = [_P, _P, ctypes.POINTER(riann_frame_stats_t)]
 _lib.riann_profile_enable.argtypes = [_P, ctypes.c_int]
 _lib.riann_profile_read.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_float), _i32]
@@ -284,6 +285,24 @@ def riann_annf_frame(index: RiannIndex, params: riann_params, frame: torch.Tenso
 
 
 RIANN_KNN_MAX = 8
+
+
+def riann_cluster_references(patches: torch.Tensor, leaf: int, want_assign: bool = True,
+                             stream: Optional[torch.cuda.Stream] = None):
+    """Sec. 3.4 reference-set construction: returns (reps uint8 [m][8][8][C],
+    assign int32 [n] or None), the per-cluster lower medians of the
+    regression-tree leaves (at most `leaf` patches each) of the n patches."""
+    if patches.dim() != 4 or tuple(patches.shape[1:3]) != (8, 8) or patches.shape[3] not in (1, 3):
+        raise ValueError("patches must be uint8 [n][8][8][C], C in {1, 3}")
+    n, C = int(patches.shape[0]), int(patches.shape[3])
+    reps = torch.empty_like(patches)
+    assign = torch.empty(n, dtype=torch.int32, device=patches.device) if want_assign else None
+    m = _i32(0)
+    _check(_lib.riann_cluster_references(_stream(stream), _dev(patches, (torch.uint8,), "patches", n * 64 * C), n, C,
+                                         int(leaf), _dev(reps, (torch.uint8,), "reps", n * 64 * C),
+                                         _dev(assign, _I32, "assign", n), ctypes.byref(m)),
+           "riann_cluster_references")
+    return reps[:m.value], assign
 
 
 def riann_stack_frames(f0: torch.Tensor, f1: torch.Tensor, f2: torch.Tensor, out: Optional[torch.Tensor] = None,
