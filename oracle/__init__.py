@@ -35,7 +35,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-std=c99", "-O2", "-fopenmp", "-fPIC", "-shared", "-Wall", "-Wextra",
-           "-o", tmp, _SRC]
+           "-ffp-contract=off", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -62,6 +62,12 @@ def _load():
                                              i32, i32, i32, i32, P, i64, P, P, P]
             lib.oracle_reconstruct.argtypes = [P, i32, i32, P, i32, i32, P, P, P]
             lib.oracle_cluster_references.argtypes = [P, i32, i32, i32, P, P]
+            lib.oracle_unit_normalize.argtypes = [P, i32, i32, P]
+            lib.oracle_unit_dist.argtypes = [P, P, i32]
+            lib.oracle_unit_dist.restype = ctypes.c_float
+            lib.oracle_unit_ring_member.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, i32]
+            lib.oracle_unit_ring_member.restype = ctypes.c_int
+            lib.oracle_riann_unit.argtypes = [P, i32, i32, i32, P, i32, P, i32, P, i32, i32, i32, P, i64, P, P, P]
             lib.oracle_cluster_references.restype = i32
             lib.oracle_philox4x32_10.argtypes = [P, P, P]
             lib.oracle_random_field.argtypes = [i32, i32, i32, ctypes.c_uint64, u32, P]
@@ -88,6 +94,7 @@ class use_library:
         lib = ctypes.CDLL(self.path)
         for name in ("oracle_ring_member", "oracle_key_distances", "oracle_sort_tables", "oracle_exact_nn",
                      "oracle_riann_definitional", "oracle_riann_indexed", "oracle_riann_knn", "oracle_reconstruct", "oracle_cluster_references",
+                     "oracle_unit_normalize", "oracle_unit_dist", "oracle_unit_ring_member", "oracle_riann_unit",
                      "oracle_philox4x32_10", "oracle_full_tables", "oracle_riann_anchor", "oracle_random_field",
                      "oracle_num_threads",
                      "oracle_set_num_threads"):
@@ -209,6 +216,47 @@ def cluster_references(X: np.ndarray, leaf: int):
     assign = np.empty(max(n, 1), np.int32)
     m = lib.oracle_cluster_references(_ptr(Xc), n, D, leaf, _ptr(reps), _ptr(assign))
     return reps[:m].reshape((m,) + tuple(X.shape[1:])), assign[:n]
+
+
+def unit_normalize(X: np.ndarray) -> np.ndarray:
+    """Unit-variant normalisation of n patches: float32 [n][D]."""
+    lib = _load()
+    Xc = _c(X, np.uint8)
+    n = Xc.shape[0]
+    D = Xc.size // max(n, 1)
+    out = np.empty((n, D), np.float32)
+    lib.oracle_unit_normalize(_ptr(Xc), n, D, _ptr(out))
+    return out
+
+
+def unit_dist(a: np.ndarray, b: np.ndarray) -> float:
+    lib = _load()
+    a32, b32 = _c(a, np.float32), _c(b, np.float32)
+    return float(lib.oracle_unit_dist(_ptr(a32), _ptr(b32), a32.size))
+
+
+def unit_ring_member(A: float, B: float, C: float, p: int, q: int) -> bool:
+    return bool(_load().oracle_unit_ring_member(A, B, C, p, q))
+
+
+def riann_unit_frame(R: np.ndarray, KP: np.ndarray, frame: np.ndarray, prev: Optional[np.ndarray],
+                     alpha=(1, 4), ring_limit: int = -1, qidx=None):
+    """Unit-normalised float variant of one query step: (annf int32, dist float32, count uint32)."""
+    lib = _load()
+    f = _frame3(frame)
+    H, W, C = f.shape
+    Rc, Kc = _c(R, np.uint8), _c(KP, np.uint8)
+    assert Rc.shape[-1] == C
+    q = None if qidx is None else _c(qidx, np.int64)
+    pv = None if prev is None else _c(prev, np.int32)
+    shape = (len(q),) if q is not None else (H - 7, W - 7)
+    annf = np.empty(shape, np.int32)
+    dist = np.empty(shape, np.float32)
+    count = np.empty(shape, np.uint32)
+    lib.oracle_riann_unit(_ptr(f), H, W, C, _ptr(Rc), Rc.shape[0], _ptr(Kc), Kc.shape[0], _ptr(pv),
+                          alpha[0], alpha[1], ring_limit, _ptr(q), 0 if q is None else len(q),
+                          _ptr(annf), _ptr(dist), _ptr(count))
+    return annf, dist, count
 
 
 def stack_frames(f0: np.ndarray, f1: np.ndarray, f2: np.ndarray) -> np.ndarray:

@@ -17,6 +17,7 @@
  */
 #include "riann_oracle.h"
 
+#include <math.h>
 #include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
@@ -409,6 +410,133 @@ int32_t oracle_cluster_references(const uint8_t* X, int32_t n, int32_t D, int32_
   }
   free(perm); free(tmp); free(vals); free(stack);
   return nclusters;
+}
+
+/*
+ * Unit-normalised float variant (Sec. 3.4: references scaled to length 1;
+ * Alg. 1: the query patch is normalised at run time).  Every step is an IEEE
+ * single-precision operation in a fixed order (this file is compiled with
+ * -ffp-contract=off, so nothing is fused unless written as fmaf):
+ *   normalise  s = sum of v_i^2 (exact integer); v'_i = v_i / sqrtf(s)
+ *              (the zero patch stays zero)
+ *   distance   d(a, b) = sqrtf(acc), acc = fmaf(t_i, t_i, acc) over
+ *              i = 0 .. D-1 in order, t_i = a_i - b_i, acc starting at 0
+ *   ring m     |A - B| <= T with A = d(k'_m, r'), B = d(k'_m, q'),
+ *              T = (p * C) / q, C = d(q', r'_p)
+ *   then S, the routing test and the argmin as in the integer step, on
+ *   these float distances (ties: lower index).
+ */
+static void unit_normalize(const uint8_t* v, int32_t D, float* out) {
+  uint32_t s = 0;
+  for (int32_t i = 0; i < D; ++i) s += (uint32_t)v[i] * v[i];
+  if (s == 0) {
+    for (int32_t i = 0; i < D; ++i) out[i] = 0.f;
+    return;
+  }
+  const float nv = sqrtf((float)s);
+  for (int32_t i = 0; i < D; ++i) out[i] = (float)v[i] / nv;
+}
+
+static float unit_dist(const float* a, const float* b, int32_t D) {
+  float acc = 0.f;
+  for (int32_t i = 0; i < D; ++i) {
+    const float t = a[i] - b[i];
+    acc = fmaf(t, t, acc);
+  }
+  return sqrtf(acc);
+}
+
+void oracle_unit_normalize(const uint8_t* X, int32_t n, int32_t D, float* out) {
+  for (int32_t r = 0; r < n; ++r) unit_normalize(X + (int64_t)r * D, D, out + (int64_t)r * D);
+}
+
+float oracle_unit_dist(const float* a, const float* b, int32_t D) { return unit_dist(a, b, D); }
+
+int oracle_unit_ring_member(float A, float B, float C, int32_t p, int32_t q) {
+  const float T = ((float)p * C) / (float)q;
+  return fabsf(A - B) <= T;
+}
+
+static void unit_brute_force(const float* qn, const float* Rf, int32_t n, int32_t D, int32_t* bi, float* bd) {
+  *bi = 0;
+  *bd = unit_dist(qn, Rf, D);
+  for (int32_t r = 1; r < n; ++r) {
+    const float d = unit_dist(qn, Rf + (int64_t)r * D, D);
+    if (d < *bd) { *bd = d; *bi = r; }
+  }
+}
+
+void oracle_riann_unit(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                       const uint8_t* R, int32_t n, const uint8_t* KP, int32_t K,
+                       const int32_t* prev, int32_t alpha_num, int32_t alpha_den, int32_t ring_limit,
+                       const int64_t* qidx, int64_t nq,
+                       int32_t* annf, float* dist, uint32_t* count) {
+  const int32_t D = PATCH * PATCH * C;
+  const int32_t Wq = W - PATCH + 1;
+  const int64_t Q = (int64_t)(H - PATCH + 1) * Wq;
+  const int64_t N = qidx ? nq : Q;
+  float* Rf = (float*)malloc(sizeof(float) * (size_t)n * D);
+  float* Kf = (float*)malloc(sizeof(float) * (size_t)K * D);
+  float* A = (float*)malloc(sizeof(float) * (size_t)n * K);
+  oracle_unit_normalize(R, n, D, Rf);
+  oracle_unit_normalize(KP, K, D, Kf);
+  for (int32_t r = 0; r < n; ++r)
+    for (int32_t m = 0; m < K; ++m) A[(int64_t)r * K + m] = unit_dist(Kf + (int64_t)m * D, Rf + (int64_t)r * D, D);
+#pragma omp parallel
+  {
+    uint8_t q[PATCH * PATCH * 3];
+    float qn[PATCH * PATCH * 3];
+    float* B = (float*)malloc(sizeof(float) * (size_t)K);
+    uint32_t* ring_size = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)K);
+    uint8_t* in_s = (uint8_t*)malloc((size_t)n);
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < N; ++i) {
+      const int64_t qi = query_at(qidx, i);
+      extract_query(frame, W, C, (int32_t)(qi / Wq), (int32_t)(qi % Wq), q);
+      unit_normalize(q, D, qn);
+      int32_t bi;
+      float bd;
+      if (!prev) {
+        unit_brute_force(qn, Rf, n, D, &bi, &bd);
+        annf[i] = bi; if (dist) dist[i] = bd; if (count) count[i] = (uint32_t)n;
+        continue;
+      }
+      const int32_t rp = prev[qi];
+      const float Cd = unit_dist(qn, Rf + (int64_t)rp * D, D);
+      for (int32_t m = 0; m < K; ++m) {
+        B[m] = unit_dist(Kf + (int64_t)m * D, qn, D);
+        ring_size[m] = 0;
+      }
+      uint32_t s_size = 0;
+      for (int32_t r = 0; r < n; ++r) {
+        int inside = 1;
+        for (int32_t m = 0; m < K; ++m) {
+          const int mem = oracle_unit_ring_member(A[(int64_t)r * K + m], B[m], Cd, alpha_num, alpha_den);
+          ring_size[m] += (uint32_t)mem;
+          inside &= mem;
+        }
+        in_s[r] = (uint8_t)inside;
+        s_size += (uint32_t)inside;
+      }
+      uint32_t ns = ring_size[0];
+      for (int32_t m = 1; m < K; ++m) if (ring_size[m] < ns) ns = ring_size[m];
+      if (ring_limit >= 0 && ns > (uint32_t)ring_limit) {
+        unit_brute_force(qn, Rf, n, D, &bi, &bd);
+        annf[i] = bi; if (dist) dist[i] = bd; if (count) count[i] = (uint32_t)n;
+        continue;
+      }
+      bi = rp;
+      bd = Cd;
+      for (int32_t r = 0; r < n; ++r) {
+        if (!in_s[r]) continue;
+        const float d = unit_dist(qn, Rf + (int64_t)r * D, D);
+        if (d < bd || (d == bd && r < bi)) { bd = d; bi = r; }
+      }
+      annf[i] = bi; if (dist) dist[i] = bd; if (count) count[i] = s_size;
+    }
+    free(B); free(ring_size); free(in_s);
+  }
+  free(Rf); free(Kf); free(A);
 }
 
 /* A sorted list splits into three runs around a ring: references below it

@@ -101,6 +101,22 @@ void oracle_riann_knn(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
 int32_t oracle_cluster_references(const uint8_t* X, int32_t n, int32_t D, int32_t leaf,
                                   uint8_t* reps, int32_t* assign);
 
+/* ---- unit-normalised float variant (Sec. 3.4 / Alg. 1: unit-length patches) ----
+ * IEEE single precision in a fixed order:
+ *   normalise  v'_i = v_i / sqrtf(sum v_i^2) (the zero patch stays zero)
+ *   distance   d(a, b) = sqrtf(acc), acc = fmaf(t_i, t_i, acc) for i = 0..D-1, t_i = a_i - b_i
+ *   ring m     |A - B| <= (p * C) / q  (A = d(k'_m, r'), B = d(k'_m, q'), C = d(q', r'_p))
+ * and S, routing and the argmin of oracle_riann_definitional on those
+ * distances; dist receives the float distance of the answer. */
+void oracle_unit_normalize(const uint8_t* X, int32_t n, int32_t D, float* out);
+float oracle_unit_dist(const float* a, const float* b, int32_t D);
+int oracle_unit_ring_member(float A, float B, float C, int32_t p, int32_t q);
+void oracle_riann_unit(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
+                       const uint8_t* R, int32_t n, const uint8_t* KP, int32_t K,
+                       const int32_t* prev, int32_t alpha_num, int32_t alpha_den, int32_t ring_limit,
+                       const int64_t* qidx, int64_t nq,
+                       int32_t* annf, float* dist, uint32_t* count);
+
 /* Reconstruction by patch replacement (Sec. 4: "replacing each patch with
  * its match and averaging overlapping patches").  out[y][x][c] = rounded
  * average over the query patches (py, px) that cover (y, x) -- py <= y < py+8,

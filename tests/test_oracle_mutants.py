@@ -18,6 +18,7 @@ import test_oracle_reconstruct as rpins
 import test_oracle_anchor as apins
 import test_oracle_knn as kpins
 import test_oracle_cluster as cpins
+import test_oracle_unit as upins
 
 SRC = os.path.join(os.path.dirname(os.path.abspath(oracle.__file__)), "riann_oracle.c")
 
@@ -66,6 +67,14 @@ MUTANTS = {
     "cluster_tie_high_coordinate": ("if (v > best_v) { best_v = v; best_d = d; }", "if (v >= best_v && v) { best_v = v; best_d = d; }"),
     "cluster_no_strict_fallback": ("strict = nle == cnt;", "strict = 0;"),
     "cluster_leaf_off_by_one": ("if (cnt > leaf) {", "if (cnt >= leaf) {"),
+    # unit-normalised float variant
+    "unit_query_not_normalised": ("unit_normalize(q, D, qn);\n      int32_t bi;",
+                                  "for (int32_t u = 0; u < D; ++u) qn[u] = (float)q[u];\n      int32_t bi;"),
+    "unit_alpha_inverted": ("const float T = ((float)p * C) / (float)q;", "const float T = ((float)q * C) / (float)p;"),
+    "unit_distance_not_rooted": ("  return sqrtf(acc);\n}", "  return acc;\n}"),
+    "unit_ring_tie_high": ("if (d < bd || (d == bd && r < bi)) { bd = d; bi = r; }\n      }\n      annf[i] = bi; if (dist) dist[i] = bd; if (count) count[i] = s_size;",
+                           "if (d < bd || (d == bd && r > bi)) { bd = d; bi = r; }\n      }\n      annf[i] = bi; if (dist) dist[i] = bd; if (count) count[i] = s_size;"),
+    "unit_brute_tie_high": ("if (d < *bd) { *bd = d; *bi = r; }", "if (d <= *bd) { *bd = d; *bi = r; }"),
     "cluster_right_first": ("stack[2 * top] = b + nl; stack[2 * top + 1] = e; ++top;     /* right, processed after left */\n    stack[2 * top] = b; stack[2 * top + 1] = b + nl; ++top;",
                             "stack[2 * top] = b; stack[2 * top + 1] = b + nl; ++top;\n    stack[2 * top] = b + nl; stack[2 * top + 1] = e; ++top;"),
 }
@@ -116,7 +125,12 @@ def _pins_fail() -> bool:
                cpins.test_few_patches_one_cluster, cpins.test_identical_patches_do_not_split,
                cpins.test_two_separated_groups, cpins.test_single_varying_coordinate_gives_value_ranges,
                cpins.test_split_on_largest_variance, cpins.test_tied_variance_splits_lowest_coordinate,
-               cpins.test_all_at_or_below_the_median_splits_strictly]
+               cpins.test_all_at_or_below_the_median_splits_strictly,
+               upins.test_normalisation_matches_float64, lambda: upins.test_distance_matches_float64(64),
+               upins.test_ring_predicate_on_exact_values,
+               lambda: upins.test_scale_invariance_bit_exact((1, 4), -1),
+               lambda: upins.test_frame0_is_float_brute_force(1), upins.test_wide_rings_reduce_to_brute_force,
+               upins.test_alpha_one_is_near_exact_nn]
     for c in checks:
         try:
             c()
@@ -134,8 +148,8 @@ def test_pins_catch_mutant(name, tmp_path):
     c_path = tmp_path / "mutant.c"
     c_path.write_text(mutated)
     so = tmp_path / "mutant.so"
-    subprocess.run(["gcc", "-std=c99", "-O2", "-fopenmp", "-fPIC", "-shared", "-I",
-                    os.path.dirname(SRC), "-o", str(so), str(c_path)], check=True)
+    subprocess.run(["gcc", "-std=c99", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off", "-I",
+                    os.path.dirname(SRC), "-o", str(so), str(c_path), "-lm"], check=True)
     with oracle.use_library(str(so)):
         assert _pins_fail(), f"no pin caught the planted mistake {name}"
 
