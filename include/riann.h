@@ -93,6 +93,7 @@ riann_params riann_default_params(int32_t n);
 typedef struct {
   int32_t n, K, channels, dim;   /* dim = 64 * channels */
   size_t device_bytes;           /* bytes of device memory the index holds */
+  int32_t unit;                  /* 1: unit-normalised float index (riann_build_unit_index) */
 } riann_index_info_t;
 
 /*
@@ -110,6 +111,29 @@ typedef struct {
 int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t channels,
                                 const uint8_t* d_keypoints, int32_t K,
                                 riann_stream_t stream, riann_index_t* out);
+
+/*
+ * Unit-normalised float variant (Sec. 3.4: representatives scaled to length
+ * 1; Alg. 1: the query normalised at run time).  Same arguments as
+ * riann_build_reference_index.  Every distance of the method is then the L2
+ * distance between unit-length patches, in IEEE single precision with a fixed
+ * order of operations:
+ *   normalise  v'_i = v_i / sqrt(sum v_i^2) (correctly rounded; the zero
+ *              patch stays zero)
+ *   distance   d(a, b) = sqrt(acc), acc = fma(t_i, t_i, acc) for
+ *              i = 0 .. D-1 in (dy, dx, c) order, t_i = a_i - b_i, from 0
+ *   ring m     |fl(A - B)| <= T, T = fl(fl(alpha_num * C) / alpha_den)
+ *   answer     argmin of d over S u {r_p} (lower index on ties); routing and
+ *              count as for the integer index
+ * On such an index riann_annf_frame and riann_exact_nn write d as float32 bit
+ * patterns into d_out_dist; sessions and riann_reconstruct work as usual.
+ * k-NN, batch contexts, servers, the anchor loop and the allocation-free
+ * brute force return RIANN_ERR_UNSUPPORTED.  Its brute force runs on the CUDA
+ * cores (the fixed fp32 order has no tensor-core equivalent).
+ */
+int riann_build_unit_index(const uint8_t* d_patches, int32_t n, int32_t channels,
+                           const uint8_t* d_keypoints, int32_t K,
+                           riann_stream_t stream, riann_index_t* out);
 
 /* Synchronises the device and frees the index and its scratch.  NULL is a no-op. */
 void riann_index_destroy(riann_index_t idx);

@@ -6,6 +6,7 @@ linked into ``paper_1508_07953_gb300/_lib/libriann.so``.  No GPU is needed.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import glob
 import os
 import shutil
 import subprocess
@@ -16,9 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libriann.so")
-SOURCES = ["api.cu", "index_build.cu", "sparse_query.cu", "dense_tc.cu", "server.cu", "reconstruct.cu", "stack.cu", "cluster.cu",
+SOURCES = ["api.cu", "index_build.cu", "sparse_query.cu", "dense_tc.cu", "server.cu", "reconstruct.cu", "stack.cu", "cluster.cu", "unit.cu",
            "anchor.cu"]
-HEADERS = [os.path.join(CSRC, "common.cuh"), os.path.join(ROOT, "include", "riann.h")]
+HEADERS = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "riann.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
                 "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]

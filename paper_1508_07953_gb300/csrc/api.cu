@@ -104,6 +104,9 @@ SparseArgs sparse_args(const Index& ix, const riann_params* p, Workspace& ws, un
   sa.alpha_den = p->alpha_den;
   sa.ring_limit = p->ring_limit;
   sa.depth = p->cap ? p->cap : ix.depth;
+  sa.unit = ix.unit ? 1 : 0;
+  sa.Rf = ix.Rf;
+  sa.KPf = ix.KPf;
   sa.dense_list = ws.dense_list;
   sa.counters = ws.counters;
   sa.status = ix.status;
@@ -139,7 +142,7 @@ cudaError_t run_frame(Index& ix, Workspace& ws, const riann_params* p, cudaStrea
   if (!it.prev) {
     da.list = nullptr;
     da.list_count = nullptr;
-    return launch_dense_tc(da, ix, ws, s);
+    return ix.unit ? launch_dense_unit(da, ix, s) : launch_dense_tc(da, ix, ws, s);
   }
   e = cudaMemsetAsync(ws.counters, 0, sizeof(uint32_t) * 4, s);
   if (e != cudaSuccess) return e;
@@ -154,7 +157,7 @@ cudaError_t run_frame(Index& ix, Workspace& ws, const riann_params* p, cudaStrea
   if (e != cudaSuccess || p->ring_limit < 0) return e;
   da.list = ws.dense_list;
   da.list_count = ws.counters;
-  return launch_dense_tc(da, ix, ws, s);
+  return ix.unit ? launch_dense_unit(da, ix, s) : launch_dense_tc(da, ix, ws, s);
 }
 
 void free_index(Index* ix) {
@@ -170,6 +173,8 @@ void free_index(Index* ix) {
   cudaFree(ix->E);
   cudaFree(ix->RB);
   cudaFree(ix->CW);
+  cudaFree(ix->Rf);
+  cudaFree(ix->KPf);
   cudaFree(ix->status);
   cudaFree(ix->stats);
   for (int k = 0; k < kSlots; ++k)
@@ -366,6 +371,76 @@ cudaError_t enqueue_batch(riann_batch_s* b, const riann_params* p, cudaStream_t 
 
 }  // namespace
 
+namespace {
+
+int build_index(const uint8_t* d_patches, int32_t n, int32_t channels, const uint8_t* d_keypoints, int32_t K,
+                riann_stream_t stream, bool unit, riann_index_t* out) {
+  if (!out) return RIANN_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!d_patches || !d_keypoints || n < 1 || n > (1 << 24) || K < 1 || K > kMaxK ||
+      (channels != 1 && channels != 3))
+    return RIANN_ERR_INVALID_ARG;
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RIANN_ERR_CUDA;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10 || minor != 3) return RIANN_ERR_UNSUPPORTED;
+
+  riann_index_s* ix = new (std::nothrow) riann_index_s();
+  if (!ix) return RIANN_ERR_OOM;
+  ix->device = dev;
+  ix->unit = unit;
+  ix->n = n;
+  ix->K = K;
+  ix->C = channels;
+  ix->D = 64 * channels;
+  ix->n_pad = (n + kDenseTileN - 1) / kDenseTileN * kDenseTileN;
+  ix->Kp = (K + 3) / 4 * 4;
+  ix->G = (K + 3) / 4;
+  ix->nw = (n + 3) / 4 * 4;
+  const int D = ix->D;
+  size_t& tot = ix->device_bytes;
+  cudaError_t e = dalloc(&ix->R, (size_t)n * D, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->KP, (size_t)K * D, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->Rbf, (size_t)ix->n_pad * D, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->RN, (size_t)ix->n_pad * 16, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->rnorm, (size_t)ix->n_pad, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->P, (size_t)n * ix->Kp, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->TA, (size_t)n * K, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->Tid, (size_t)n * K, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->E, (size_t)K * kBuckets, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->RB, (size_t)K * (kBuckets + 1), tot);
+  if (e == cudaSuccess) e = dalloc(&ix->CW, (size_t)K * ix->G * ix->nw, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->status, 1, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->stats, kStats, tot);
+  if (e == cudaSuccess && unit) e = dalloc(&ix->Rf, (size_t)n * D, tot);
+  if (e == cudaSuccess && unit) e = dalloc(&ix->KPf, (size_t)K * D, tot);
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ix->status, 0, sizeof(uint32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * kStats, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ix->R, d_patches, (size_t)n * D, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ix->KP, d_keypoints, (size_t)K * D, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) e = launch_index_build(*ix, s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(s);
+    free_index(ix);
+    return from_cuda(e);
+  }
+  if (!make_row_map(&ix->tmRbf, ix->Rbf, (uint64_t)ix->n_pad, D, dense_ref_rows_per_tile(channels))) {
+    cudaStreamSynchronize(s);
+    free_index(ix);
+    return RIANN_ERR_UNSUPPORTED;
+  }
+  ix->tm_ready = true;
+  *out = ix;
+  return RIANN_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 riann_params riann_default_params(int32_t n) {
@@ -392,68 +467,16 @@ const char* riann_strerror(int code) {
   }
 }
 
+
 int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t channels,
                                 const uint8_t* d_keypoints, int32_t K, riann_stream_t stream,
                                 riann_index_t* out) {
-  if (!out) return RIANN_ERR_INVALID_ARG;
-  *out = nullptr;
-  if (!d_patches || !d_keypoints || n < 1 || n > (1 << 24) || K < 1 || K > kMaxK ||
-      (channels != 1 && channels != 3))
-    return RIANN_ERR_INVALID_ARG;
-  int dev = 0, major = 0, minor = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return RIANN_ERR_CUDA;
-  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  if (major != 10 || minor != 3) return RIANN_ERR_UNSUPPORTED;
+  return build_index(d_patches, n, channels, d_keypoints, K, stream, false, out);
+}
 
-  riann_index_s* ix = new (std::nothrow) riann_index_s();
-  if (!ix) return RIANN_ERR_OOM;
-  ix->device = dev;
-  ix->n = n;
-  ix->K = K;
-  ix->C = channels;
-  ix->D = 64 * channels;
-  ix->n_pad = (n + kDenseTileN - 1) / kDenseTileN * kDenseTileN;
-  ix->Kp = (K + 3) / 4 * 4;
-  ix->G = (K + 3) / 4;
-  ix->nw = (n + 3) / 4 * 4;
-  const int D = ix->D;
-  size_t& tot = ix->device_bytes;
-  cudaError_t e = dalloc(&ix->R, (size_t)n * D, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->KP, (size_t)K * D, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->Rbf, (size_t)ix->n_pad * D, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->RN, (size_t)ix->n_pad * 16, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->rnorm, (size_t)ix->n_pad, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->P, (size_t)n * ix->Kp, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->TA, (size_t)n * K, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->Tid, (size_t)n * K, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->E, (size_t)K * kBuckets, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->RB, (size_t)K * (kBuckets + 1), tot);
-  if (e == cudaSuccess) e = dalloc(&ix->CW, (size_t)K * ix->G * ix->nw, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->status, 1, tot);
-  if (e == cudaSuccess) e = dalloc(&ix->stats, kStats, tot);
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ix->status, 0, sizeof(uint32_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ix->stats, 0, sizeof(unsigned long long) * kStats, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ix->R, d_patches, (size_t)n * D, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(ix->KP, d_keypoints, (size_t)K * D, cudaMemcpyDeviceToDevice, s);
-  if (e == cudaSuccess) e = launch_index_build(*ix, s);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    cudaStreamSynchronize(s);
-    free_index(ix);
-    return from_cuda(e);
-  }
-  if (!make_row_map(&ix->tmRbf, ix->Rbf, (uint64_t)ix->n_pad, D, dense_ref_rows_per_tile(channels))) {
-    cudaStreamSynchronize(s);
-    free_index(ix);
-    return RIANN_ERR_UNSUPPORTED;
-  }
-  ix->tm_ready = true;
-  *out = ix;
-  return RIANN_OK;
+int riann_build_unit_index(const uint8_t* d_patches, int32_t n, int32_t channels, const uint8_t* d_keypoints,
+                           int32_t K, riann_stream_t stream, riann_index_t* out) {
+  return build_index(d_patches, n, channels, d_keypoints, K, stream, true, out);
 }
 
 void riann_index_destroy(riann_index_t idx) {
@@ -469,6 +492,7 @@ int riann_index_info(riann_index_t idx, riann_index_info_t* out) {
   out->channels = idx->C;
   out->dim = idx->D;
   out->device_bytes = idx->device_bytes;
+  out->unit = idx->unit ? 1 : 0;
   return RIANN_OK;
 }
 
@@ -515,6 +539,7 @@ extern "C" {
 int riann_full_create(riann_index_t idx, riann_stream_t stream, riann_full_t* out) {
   if (!idx || !out) return RIANN_ERR_INVALID_ARG;
   *out = nullptr;
+  if (idx->unit) return RIANN_ERR_UNSUPPORTED;
   riann_full_s* f = new (std::nothrow) riann_full_s();
   if (!f) return RIANN_ERR_OOM;
   f->idx = idx;
@@ -657,6 +682,7 @@ int riann_knn_frame(riann_index_t idx, const riann_params* p, riann_stream_t str
       k > RIANN_KNN_MAX || (const void*)d_prev_annf == (const void*)d_out_annf ||
       (const void*)d_prev_annf == (const void*)d_out_knn)
     return RIANN_ERR_INVALID_ARG;
+  if (idx->unit) return RIANN_ERR_UNSUPPORTED;
   Index& ix = *idx;
   std::lock_guard<std::mutex> lock(ix.mu);
   const int64_t Q = (int64_t)(H - 7) * (W - 7);
@@ -697,7 +723,8 @@ int riann_exact_nn(riann_index_t idx, riann_stream_t stream, const uint8_t* d_fr
   DenseArgs da = dense_args(ix, nullptr);
   da.one = make_item(d_frame, nullptr, d_out_annf, d_out_dist, nullptr, H, W, ix.tile_shape);
   da.Q = Q;
-  return from_cuda(launch_dense_tc(da, ix, ix.ws, reinterpret_cast<cudaStream_t>(stream)));
+  cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);
+  return from_cuda(ix.unit ? launch_dense_unit(da, ix, cs) : launch_dense_tc(da, ix, ix.ws, cs));
 }
 
 int riann_frame_stats(riann_index_t idx, riann_stream_t stream, riann_frame_stats_t* out) {
@@ -754,6 +781,7 @@ int64_t riann_exact_nn_noalloc_max_queries(int32_t channels) {
 int riann_exact_nn_noalloc(riann_index_t idx, riann_stream_t stream, const uint8_t* d_frame, int32_t H,
                            int32_t W, int32_t* d_out_annf, uint32_t* d_out_dist) {
   if (!idx || !d_frame || !d_out_annf || !frame_ok(H, W)) return RIANN_ERR_INVALID_ARG;
+  if (idx->unit) return RIANN_ERR_UNSUPPORTED;
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return RIANN_ERR_CUDA;
   if (dev != idx->device) return RIANN_ERR_INVALID_ARG;
@@ -928,6 +956,7 @@ int riann_batch_create(riann_index_t idx, int32_t max_items, int64_t max_queries
   *out = nullptr;
   if (!idx || max_items < 1 || max_items > 4096 || max_queries < 1 || max_queries >= INT32_MAX)
     return RIANN_ERR_INVALID_ARG;
+  if (idx->unit) return RIANN_ERR_UNSUPPORTED;
   riann_batch_s* b = new (std::nothrow) riann_batch_s();
   if (!b) return RIANN_ERR_OOM;
   b->ix = idx;

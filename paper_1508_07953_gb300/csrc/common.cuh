@@ -113,6 +113,11 @@ struct Index {
   uint32_t* status = nullptr;     // device status word (RIANN_DEV_* bits)
   unsigned long long* stats = nullptr;  // [kStats] counters of the last frame
   size_t device_bytes = 0;
+  // unit-normalised float variant: patches scaled to length 1 (fp32, fixed
+  // operation order); P, TA, E hold the bit patterns of the float distances
+  bool unit = false;
+  float* Rf = nullptr;            // [n][D] normalised references
+  float* KPf = nullptr;           // [K][D] normalised key points
 
   // ring-kernel tuning (riann_autotune sets them; these are the defaults)
   int tile_shape = kTile4x32;
@@ -148,6 +153,9 @@ struct SparseArgs {
   int n, K, Kp, G, nw;
   int alpha_num, alpha_den, ring_limit;
   int depth;                      // stage-1 filter depth (1..5)
+  int unit;                       // unit-normalised float variant (Rf, KPf below)
+  const float* Rf;
+  const float* KPf;
   int knn;                        // k of the k-NN variant (0: 1-NN path)
   int32_t* knn_idx;               // k-NN variant: [Q][knn] matches, ascending (dist, index); -1 past |S u {r_p}|
   uint32_t* knn_dist;             // k-NN variant: [Q][knn] their squared distances (nullable; ~0 past the end)
@@ -194,6 +202,11 @@ cudaError_t launch_sparse(const SparseArgs& a, int C, int shape, cudaStream_t s)
 cudaError_t launch_sparse_item(const SparseArgs& a, int C, int shape, int tiles, cudaStream_t s);
 
 cudaError_t launch_index_build(Index& ix, cudaStream_t s);
+
+// unit.cu: unit-normalised float variant -- normalised tables and P (as
+// float bits) for an index with ix.unit set, and its brute force
+cudaError_t launch_unit_tables(Index& ix, cudaStream_t s);
+cudaError_t launch_dense_unit(const DenseArgs& d, Index& ix, cudaStream_t s);
 
 // cluster.cu: Sec. 3.4 reference-set construction (synchronises `s`)
 cudaError_t cluster_references(const uint8_t* X, int n, int C, int leaf, uint8_t* reps, int32_t* assign,

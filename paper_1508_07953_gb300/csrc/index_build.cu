@@ -208,7 +208,10 @@ int sort_chunk() { return kChunk; }
 
 cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
   const int n = ix.n, K = ix.K, D = ix.D;
-  {
+  if (ix.unit) {   // unit-normalised float variant: P holds float bits
+    const cudaError_t e0 = launch_unit_tables(ix, s);
+    if (e0 != cudaSuccess) return e0;
+  } else {
     int64_t tot = (int64_t)n * ix.Kp;
     k_key_distances<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ix.R, ix.KP, n, K, ix.Kp, D, ix.P);
   }

@@ -149,6 +149,7 @@ int riann_server_create(riann_index_t gray, riann_index_t rgb, size_t budget_byt
   riann_index_info_t gi, ci;
   if (gray && (riann_index_info(gray, &gi) || gi.channels != 1)) return RIANN_ERR_INVALID_ARG;
   if (rgb && (riann_index_info(rgb, &ci) || ci.channels != 3)) return RIANN_ERR_INVALID_ARG;
+  if ((gray && gi.unit) || (rgb && ci.unit)) return RIANN_ERR_UNSUPPORTED;
   riann_server_s* s = new (std::nothrow) riann_server_s();
   if (!s) return RIANN_ERR_OOM;
   s->idx[0] = gray;

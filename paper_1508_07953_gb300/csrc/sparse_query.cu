@@ -14,7 +14,7 @@
 // references that pass the filter are then tested exactly against every ring
 // from their row of key-point distances in P (16 MB for n = 65536, K = 64:
 // it stays in L2).
-#include "common.cuh"
+#include "unit.cuh"
 
 namespace riann {
 namespace {
@@ -205,7 +205,9 @@ constexpr int kRowBatch = 4;  // 16-byte words of a distance row loaded per roun
 // from one step to the next.  (A persistent launch taking the tiles of all
 // frames from an atomic counter measured 8 % slower.)  KNN: the k-NN output
 // (the k best of S u {r_p} instead of the argmin), single-frame launches only.
-template <int C, int SHAPE, bool BATCH, bool KNN>
+// UNIT: the unit-normalised float variant (unit.cuh) -- normalised query,
+// float distances and ring bounds as float bit patterns; single-frame only.
+template <int C, int SHAPE, bool BATCH, bool KNN, bool UNIT>
 __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid_constant__ SparseArgs a) {
   constexpr int TY = SHAPE == kTile4x32 ? 4 : 8;
   constexpr int TX = SHAPE == kTile4x32 ? 32 : 16;
@@ -229,6 +231,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   __shared__ int32_t s_queue[kWarps][kQueue];     // stage-1 survivors (seed-run positions)
   __shared__ __align__(16) uint32_t s_q[kWarps][NW];   // the warp's query patch
   __shared__ int32_t s_dense[TY * TX];
+  __shared__ __align__(16) float s_qf[UNIT ? kWarps : 1][UNIT ? D : 4];   // UNIT: the normalised query
   __shared__ int s_next, s_ndense, s_dense_base;
   __shared__ FrameItem s_item;                    // batched launch: this launch's frame
   __shared__ unsigned long long s_stat[3];        // ring-answered queries, scanned entries, sum of |S|
@@ -314,7 +317,25 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       continue;
     }
     uint32_t Cd = 0;
-    {
+    float Cf = 0.f, Tf = 0.f;                       // UNIT: C and the ring half-width T
+    float* qf = s_qf[UNIT ? warp : 0];
+    if (UNIT) {
+      // q' = q / ||q|| (exact integer sum of squares), then C = d(q', r'_p)
+      uint32_t ss = 0;
+      for (int w = lane; w < NW; w += 32) ss = __dp4a(q[w], q[w], ss);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(kFull, ss, o);
+      const float nv = unit_scale(ss);
+      for (int w = lane; w < NW; w += 32) {
+        const uint32_t v = q[w];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) qf[4 * w + j] = unit_coord((v >> (8 * j)) & 0xffu, ss, nv);
+      }
+      __syncwarp();
+      Cf = unit_dist<D>(qf, a.Rf + (int64_t)rp * D);
+      Tf = unit_width(a.alpha_num, a.alpha_den, Cf);
+      Cd = __float_as_uint(Cf);
+    } else {
       const uint4* r4 = reinterpret_cast<const uint4*>(a.R + (int64_t)rp * D);
 #pragma unroll
       for (int v = 0; v < NW / 4; ++v) Cd = sq4(q + 4 * v, __ldg(r4 + v), Cd);
@@ -328,17 +349,24 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     for (int h = 0; h < 2; ++h) {
       const int m = lane + 32 * h;
       if (m < K) {
-        const uint32_t* kp = s_kp + m * KPW;
-        uint32_t B = 0;
+        uint32_t lo, hi;
+        if (UNIT) {
+          const float Bf = unit_dist<D>(a.KPf + (int64_t)m * D, qf);
+          lo = unit_ring_low(Bf, Tf);
+          hi = unit_ring_high(Bf, Tf);
+        } else {
+          const uint32_t* kp = s_kp + m * KPW;
+          uint32_t B = 0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-          const uint32_t d = __vabsdiffu4(q[w], kp[w]);
-          B = __dp4a(d, d, B);
+          for (int w = 0; w < NW; ++w) {
+            const uint32_t d = __vabsdiffu4(q[w], kp[w]);
+            B = __dp4a(d, d, B);
+          }
+          const float cross = 2.f * alpha * sqrtf((float)B * sC);
+          const float base = (float)B + alpha * alpha * sC;
+          lo = ring_low(B, Cd, p2, q2, base - cross);
+          hi = ring_high(B, Cd, p2, q2, base + cross, Amax);
         }
-        const float cross = 2.f * alpha * sqrtf((float)B * sC);
-        const float base = (float)B + alpha * alpha * sC;
-        const uint32_t lo = ring_low(B, Cd, p2, q2, base - cross);
-        const uint32_t hi = ring_high(B, Cd, p2, q2, base + cross, Amax);
         const uint32_t* e = a.E + m * kBuckets;
         const int clo = bucket_code(s_coarse[m], e, lo);
         const int chi = bucket_code(s_coarse[m], e, hi);
@@ -521,10 +549,14 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       unsigned long long key = ~0ull;
       if (alive) {
         ++cnt;
-        const uint4* r4 = reinterpret_cast<const uint4*>(a.R + (int64_t)r * D);
         uint32_t d = 0;
+        if (UNIT) {
+          d = __float_as_uint(unit_dist<D>(qf, a.Rf + (int64_t)r * D));
+        } else {
+          const uint4* r4 = reinterpret_cast<const uint4*>(a.R + (int64_t)r * D);
 #pragma unroll
-        for (int v = 0; v < NW / 4; ++v) d = sq4(q + 4 * v, __ldg(r4 + v), d);
+          for (int v = 0; v < NW / 4; ++v) d = sq4(q + 4 * v, __ldg(r4 + v), d);
+        }
         key = ((unsigned long long)d << 32) | (unsigned)r;
         if (!KNN) best = key < best ? key : best;
       }
@@ -652,9 +684,10 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
 
 template <int C, int SHAPE>
 cudaError_t launch_ring(const SparseArgs& a, bool batch, int grid, cudaStream_t s) {
-  if (batch) k_sparse<C, SHAPE, true, false><<<grid, kWarps * 32, 0, s>>>(a);
-  else if (a.knn > 0) k_sparse<C, SHAPE, false, true><<<grid, kWarps * 32, 0, s>>>(a);
-  else k_sparse<C, SHAPE, false, false><<<grid, kWarps * 32, 0, s>>>(a);
+  if (batch) k_sparse<C, SHAPE, true, false, false><<<grid, kWarps * 32, 0, s>>>(a);
+  else if (a.unit) k_sparse<C, SHAPE, false, false, true><<<grid, kWarps * 32, 0, s>>>(a);
+  else if (a.knn > 0) k_sparse<C, SHAPE, false, true, false><<<grid, kWarps * 32, 0, s>>>(a);
+  else k_sparse<C, SHAPE, false, false, false><<<grid, kWarps * 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,167 @@
+// unit.cu -- unit-normalised float variant (Sec. 3.4 / Alg. 1: unit-length
+// patches): the normalised tables of an index and its brute force.  The
+// arithmetic (fixed-order IEEE fp32) is in unit.cuh.
+#include "unit.cuh"
+
+namespace riann {
+namespace {
+
+// rows of X (n x D bytes) scaled to length 1: one thread per row
+__global__ void k_unit_normalize(const uint8_t* __restrict__ X, int n, int D, float* __restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const uint8_t* x = X + (int64_t)r * D;
+  uint32_t s = 0;
+  for (int i = 0; i < D; ++i) s += (uint32_t)x[i] * x[i];
+  const float nv = unit_scale(s);
+  float* o = out + (int64_t)r * D;
+  for (int i = 0; i < D; ++i) o[i] = unit_coord(x[i], s, nv);
+}
+
+// P[r][m] = bits of d(k'_m, r'), row stride Kp, pad entries 0
+template <int D>
+__global__ void k_unit_key_distances(const float* __restrict__ Rf, const float* __restrict__ KPf, int n, int K,
+                                     int Kp, uint32_t* __restrict__ P) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n * Kp) return;
+  const int r = (int)(t / Kp), m = (int)(t % Kp);
+  P[t] = m < K ? __float_as_uint(unit_dist<D>(KPf + (int64_t)m * D, Rf + (int64_t)r * D)) : 0u;
+}
+
+// Brute force: argmin over all references of d(q', r'), lower index on ties.
+// A CTA takes QB queries (one per thread) and walks the references in tiles
+// of RT staged in shared memory; gray keeps q' in registers, RGB in shared
+// memory (column per query, conflict-free).  A reference whose running sum
+// already exceeds the best one's cannot win (sqrt is monotone and a tie
+// keeps the lower index), so the root is taken only for the others.
+template <int C>
+struct UnitCfg;
+template <>
+struct UnitCfg<1> { static constexpr int QB = 128, RT = 32; };   // 8 KB of reference tile
+template <>
+struct UnitCfg<3> { static constexpr int QB = 32, RT = 16; };    // 24 KB of queries + 12 KB of tile
+
+struct UnitDenseArgs {
+  FrameItem one;
+  const int32_t* list;
+  const uint32_t* list_count;
+  int64_t Q;
+  const float* Rf;
+  int n;
+  unsigned long long* stats;
+};
+
+template <int C>
+__global__ void __launch_bounds__(UnitCfg<C>::QB) k_dense_unit(const UnitDenseArgs a) {
+  constexpr int D = 64 * C, QB = UnitCfg<C>::QB, RT = UnitCfg<C>::RT;
+  constexpr bool QREG = C == 1;
+  __shared__ __align__(16) float s_r[RT][D];
+  __shared__ float s_q[QREG ? 1 : D][QREG ? 1 : QB];
+  const int64_t nq = a.list ? (int64_t)*a.list_count : a.Q;
+  if (!a.list && a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[kStatDenseQueries] = (unsigned long long)nq;
+  const int64_t i = (int64_t)blockIdx.x * QB + threadIdx.x;
+  if ((int64_t)blockIdx.x * QB >= nq) return;   // uniform for the CTA
+  const bool live = i < nq;
+  const FrameItem& it = a.one;
+  int64_t qi = 0;
+  float qv[QREG ? D : 1];
+  if (live) {
+    qi = a.list ? (int64_t)a.list[i] - it.query_begin : i;
+    const int y = (int)(qi / it.Wq), x = (int)(qi % it.Wq);
+    uint32_t s = 0;
+    for (int dy = 0; dy < 8; ++dy)
+      for (int j = 0; j < 8 * C; ++j) {
+        const uint32_t v = it.frame[((int64_t)(y + dy) * it.W + x) * C + j];
+        s += v * v;
+      }
+    const float nv = unit_scale(s);
+#pragma unroll
+    for (int dy = 0; dy < 8; ++dy)
+#pragma unroll
+      for (int j = 0; j < 8 * C; ++j) {
+        const float f = unit_coord(it.frame[((int64_t)(y + dy) * it.W + x) * C + j], s, nv);
+        if (QREG) qv[dy * 8 * C + j] = f;
+        else s_q[QREG ? 0 : dy * 8 * C + j][QREG ? 0 : threadIdx.x] = f;
+      }
+  }
+  float bd = __int_as_float(0x7f800000), bacc = bd;
+  int bi = 0;
+  for (int r0 = 0; r0 < a.n; r0 += RT) {
+    const int nt = min(RT, a.n - r0);
+    __syncthreads();
+    {
+      const float4* src = reinterpret_cast<const float4*>(a.Rf + (int64_t)r0 * D);
+      float4* dst = reinterpret_cast<float4*>(&s_r[0][0]);
+      for (int k = threadIdx.x; k < nt * D / 4; k += QB) dst[k] = __ldg(src + k);
+    }
+    __syncthreads();
+    if (!live) continue;
+    for (int j = 0; j < nt; ++j) {
+      const float4* r4 = reinterpret_cast<const float4*>(s_r[j]);
+      float acc = 0.f;
+#pragma unroll
+      for (int v = 0; v < D / 4; ++v) {
+        const float4 rv = r4[v];
+        if (QREG) {
+          acc = unit_step(acc, qv[QREG ? 4 * v + 0 : 0], rv.x);
+          acc = unit_step(acc, qv[QREG ? 4 * v + 1 : 0], rv.y);
+          acc = unit_step(acc, qv[QREG ? 4 * v + 2 : 0], rv.z);
+          acc = unit_step(acc, qv[QREG ? 4 * v + 3 : 0], rv.w);
+        } else {
+          acc = unit_step(acc, s_q[QREG ? 0 : 4 * v + 0][QREG ? 0 : threadIdx.x], rv.x);
+          acc = unit_step(acc, s_q[QREG ? 0 : 4 * v + 1][QREG ? 0 : threadIdx.x], rv.y);
+          acc = unit_step(acc, s_q[QREG ? 0 : 4 * v + 2][QREG ? 0 : threadIdx.x], rv.z);
+          acc = unit_step(acc, s_q[QREG ? 0 : 4 * v + 3][QREG ? 0 : threadIdx.x], rv.w);
+        }
+      }
+      if (acc <= bacc) {
+        const float d = __fsqrt_rn(acc);
+        if (d < bd) {
+          bd = d;
+          bacc = acc;
+          bi = r0 + j;
+        }
+      }
+    }
+  }
+  if (live) {
+    it.out_annf[qi] = bi;
+    if (it.out_dist) it.out_dist[qi] = __float_as_uint(bd);
+    if (it.out_count) it.out_count[qi] = (uint32_t)a.n;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_unit_tables(Index& ix, cudaStream_t s) {
+  k_unit_normalize<<<(ix.n + 127) / 128, 128, 0, s>>>(ix.R, ix.n, ix.D, ix.Rf);
+  k_unit_normalize<<<(ix.K + 127) / 128, 128, 0, s>>>(ix.KP, ix.K, ix.D, ix.KPf);
+  const int64_t tot = (int64_t)ix.n * ix.Kp;
+  const unsigned blocks = (unsigned)((tot + 255) / 256);
+  if (ix.C == 1) k_unit_key_distances<64><<<blocks, 256, 0, s>>>(ix.Rf, ix.KPf, ix.n, ix.K, ix.Kp, ix.P);
+  else k_unit_key_distances<192><<<blocks, 256, 0, s>>>(ix.Rf, ix.KPf, ix.n, ix.K, ix.Kp, ix.P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_unit(const DenseArgs& d, Index& ix, cudaStream_t s) {
+  UnitDenseArgs u;
+  u.one = d.one;
+  u.list = d.list;
+  u.list_count = d.list_count;
+  u.Q = d.Q;
+  u.Rf = ix.Rf;
+  u.n = ix.n;
+  u.stats = d.stats;
+  prof_begin(ix, kSlotDense, s);
+  if (ix.C == 1) {
+    const int64_t g = (d.Q + UnitCfg<1>::QB - 1) / UnitCfg<1>::QB;
+    k_dense_unit<1><<<(unsigned)(g > 0 ? g : 1), UnitCfg<1>::QB, 0, s>>>(u);
+  } else {
+    const int64_t g = (d.Q + UnitCfg<3>::QB - 1) / UnitCfg<3>::QB;
+    k_dense_unit<3><<<(unsigned)(g > 0 ? g : 1), UnitCfg<3>::QB, 0, s>>>(u);
+  }
+  prof_end(ix, kSlotDense, s);
+  return cudaGetLastError();
+}
+
+}  // namespace riann

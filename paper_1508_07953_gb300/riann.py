@@ -47,7 +47,7 @@ class riann_params(ctypes.Structure):
 
 class riann_index_info_t(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("K", ctypes.c_int32), ("channels", ctypes.c_int32),
-                ("dim", ctypes.c_int32), ("device_bytes", ctypes.c_size_t)]
+                ("dim", ctypes.c_int32), ("device_bytes", ctypes.c_size_t), ("unit", ctypes.c_int32)]
 
 
 class riann_frame_stats_t(ctypes.Structure):
@@ -84,6 +84,7 @@ _lib.riann_default_params.restype = riann_params
 _lib.riann_strerror.argtypes = [ctypes.c_int]
 _lib.riann_strerror.restype = ctypes.c_char_p
 _lib.riann_build_reference_index.argtypes = [_P, _i32, _i32, _P, _i32, _P, ctypes.POINTER(_P)]
+_lib.riann_build_unit_index.argtypes = [_P, _i32, _i32, _P, _i32, _P, ctypes.POINTER(_P)]
 _lib.riann_index_destroy.argtypes = [_P]
 _lib.riann_index_destroy.restype = None
 _lib.riann_index_info.argtypes = [_P, ctypes.POINTER(riann_index_info_t)]
@@ -223,8 +224,9 @@ class RiannIndex:
 
 
 def riann_build_reference_index(patches: torch.Tensor, keypoints: torch.Tensor,
-                                stream: Optional[torch.cuda.Stream] = None) -> RiannIndex:
-    """patches uint8 [n][8][8][C] and keypoints uint8 [K][8][8][C] on the GPU."""
+                                stream: Optional[torch.cuda.Stream] = None, unit: bool = False) -> RiannIndex:
+    """patches uint8 [n][8][8][C] and keypoints uint8 [K][8][8][C] on the GPU.
+    unit=True builds the unit-normalised float index (riann_build_unit_index)."""
     if patches.dim() != 4 or patches.shape[1:3] != (8, 8):
         raise ValueError("patches must be [n][8][8][C]")
     n, C = patches.shape[0], patches.shape[3]
@@ -232,11 +234,19 @@ def riann_build_reference_index(patches: torch.Tensor, keypoints: torch.Tensor,
         raise ValueError("keypoints must be [K][8][8][C] with the patches' C")
     K = keypoints.shape[0]
     h = ctypes.c_void_p(0)
-    _check(_lib.riann_build_reference_index(_dev(patches, (torch.uint8,), "patches"), n, C,
-                                            _dev(keypoints, (torch.uint8,), "keypoints"), K,
-                                            _stream(stream), ctypes.byref(h)),
-           "riann_build_reference_index")
+    fn = _lib.riann_build_unit_index if unit else _lib.riann_build_reference_index
+    _check(fn(_dev(patches, (torch.uint8,), "patches"), n, C, _dev(keypoints, (torch.uint8,), "keypoints"), K,
+              _stream(stream), ctypes.byref(h)),
+           "riann_build_unit_index" if unit else "riann_build_reference_index")
     return RiannIndex(h.value, n, K, C)
+
+
+def riann_build_unit_index(patches: torch.Tensor, keypoints: torch.Tensor,
+                           stream: Optional[torch.cuda.Stream] = None) -> RiannIndex:
+    """Unit-normalised float variant of the index: out_dist of a frame holds
+    float32 distances between unit-length patches (view the int32 output as
+    torch.float32)."""
+    return riann_build_reference_index(patches, keypoints, stream, unit=True)
 
 
 def _frame_dims(frame: torch.Tensor, C: int):
