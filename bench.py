@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--no-anchor", action="store_true", help="skip the Alg. 1 random-anchor block")
     ap.add_argument("--no-other", action="store_true", help="skip the tiny and 720p RGB workloads")
     ap.add_argument("--no-knn", action="store_true", help="skip the k-NN output block")
+    ap.add_argument("--no-unit", action="store_true", help="skip the unit-normalised float block")
     ap.add_argument("--anchor-refs", type=int, default=0,
                     help="anchor block on the first N references only (small cases for profiler captures)")
     ap.add_argument("--batch-ticks", type=int, default=6, help="timed ticks of the 32-stream batched form")
@@ -704,6 +705,94 @@ def run_knn(riann, idx, frames, frames_np, H, W, stream, flush, params, steps, k
     return blk
 
 
+def run_unit(riann, R, KP, frames, frames_np, H, W, stream, flush, steps, cpu):
+    """Unit-normalised float variant (Sec. 3.4 / Alg. 1 unit-length patches)
+    on the same frames: brute-force first frame (timed on its own), warm-up,
+    then `steps` timed frames with the L2 flushed before each; per-kernel
+    event times; optionally the oracle on a sample of positions."""
+    import torch
+    dev = frames[0].device
+    Q = (H - 7) * (W - 7)
+    n, K = R.shape[0], KP.shape[0]
+    idx = riann.riann_build_unit_index(torch.from_numpy(R).to(dev), torch.from_numpy(KP).to(dev), stream=stream)
+    p = riann.riann_default_params(n)
+    out = [torch.empty((H - 7, W - 7), dtype=torch.int32, device=dev) for _ in range(2)]
+    warm = len(frames) - 1 - steps
+    riann.riann_profile_enable(idx, True)
+    with torch.cuda.stream(stream):
+        flush.fill_(3)
+        f0 = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        f0[0].record(stream)
+        riann.riann_annf_frame(idx, p, frames[0], None, out[0], stream=stream)
+        f0[1].record(stream)
+        prev = out[0]
+        for i in range(1, 1 + warm):
+            riann.riann_annf_frame(idx, p, frames[i], prev, out[i % 2], stream=stream)
+            prev = out[i % 2]
+    riann.riann_profile_read(idx, stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ring_ms, dense_ms, byts, pairs = [], [], [], []
+    for j in range(steps):
+        i = 1 + warm + j
+        with torch.cuda.stream(stream):
+            flush.fill_(j & 0xff)
+            ev[j][0].record(stream)
+            riann.riann_annf_frame(idx, p, frames[i], prev, out[i % 2], stream=stream)
+            ev[j][1].record(stream)
+            prev = out[i % 2]
+        ms = riann.riann_profile_read(idx, stream)
+        st = riann.riann_frame_stats(idx, stream)
+        if ms[0] >= 0:
+            ring_ms.append(ms[0])
+            lg = int(np.ceil(np.log2(n + 1)))
+            rq = st["ring_queries"]
+            byts.append(H * W + 16 * Q + rq * 256 + rq * 2 * K * lg * 4 + 8 * st["sum_seed"] + 256 * st["sum_candidates"])
+        if ms[1] >= 0:
+            dense_ms.append(ms[1])
+            pairs.append(st["dense_queries"] * n)
+    stream.synchronize()
+    status = riann.riann_status(idx, stream)
+    idx.close()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    peaks = measured_peaks() or {}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ring_avg = float(np.mean(ring_ms))
+    ach = float(np.mean(byts)) / (ring_avg / 1000.0) / 1e9
+    # brute force: 2 D fp32 lane operations (a subtraction and an fma per
+    # coordinate) per (query, reference) pair, against 152 SMs x 128 fp32
+    # lanes x 2.07 GHz (one lane operation per lane and clock)
+    alu_peak = 152 * 128 * 2.07e9 / 1e12
+    alu = sum(pairs) * 128 / (sum(dense_ms) / 1000.0) / 1e12 if dense_ms and sum(dense_ms) > 0 else None
+    blk = {"workload": "the frames above on a unit-normalised float index (n=65536, K=64): fp32 distances between unit-length patches",
+           "frames": steps, "ms_per_frame": float(np.mean(step_ms)), "queries_per_s": Q / (float(np.mean(step_ms)) / 1000.0),
+           "kernels_ms": {"ring": ring_avg, "dense": float(np.mean(dense_ms)) if dense_ms else None},
+           "frame0_brute_force_ms": f0[0].elapsed_time(f0[1]), "status_bits": status,
+           "roofline": {"bound": "hbm", "kernel": "k_sparse unit variant", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm, "algorithmic_bytes_per_launch": float(np.mean(byts))},
+           "roofline_dense": {"bound": "alu", "kernel": "k_dense_unit_gray (fp32 sub + fma, packed pairs)",
+                              "achieved": alu, "peak": alu_peak, "unit": "T fp32 lane-ops/s",
+                              "frac": alu / alu_peak if alu else None,
+                              "peak_source": "152 SMs x 128 fp32 lanes x 2.07 GHz"}}
+    if cpu:
+        import oracle
+        rng = np.random.default_rng(301)
+        qidx = np.sort(rng.choice(Q, 256, replace=False)).astype(np.int64)
+        pa, _, _ = oracle.riann_unit_frame(R, KP, frames_np[0], None, qidx=qidx)
+        pv = np.zeros(Q, np.int32)
+        t_el, nq = 0.0, 0
+        for t in (1, 2):
+            pv[qidx] = pa
+            t0 = time.perf_counter()
+            pa, _, _ = oracle.riann_unit_frame(R, KP, frames_np[t], pv.reshape(H - 7, W - 7),
+                                              (p.alpha_num, p.alpha_den), p.ring_limit, qidx=qidx)
+            t_el += time.perf_counter() - t0
+            nq += len(qidx)
+        blk["oracle_queries_per_s"] = nq / t_el
+        blk["oracle_cores"] = oracle.num_threads()
+        blk["oracle_sample"] = f"256 positions over 2 frames (definitional), {t_el:.1f} s"
+    return blk
+
+
 def run_ours(args, rank, world, local):
     import torch
     import torch.distributed as dist
@@ -816,6 +905,12 @@ def run_ours(args, rank, world, local):
         knn_line = run_knn(riann, idx, frames, frames_np, H, W, stream, flush, params, min(args.steps, 10),
                            8, R, KP, prev, world == 1 and not args.no_cpu_baseline)
 
+    unit_line = None
+    if not args.no_unit and rank == 0 and not args.crop:
+        us = min(args.steps, 6)           # brute-force start, 3 warm-up frames, `us` timed frames
+        unit_line = run_unit(riann, R, KP, frames[-(4 + us):], frames_np[-(4 + us):], H, W, stream, flush, us,
+                             world == 1 and not args.no_cpu_baseline)
+
     # Alg. 1 with random anchors over the sorted distance matrix (the paper's
     # own loop): same frames, chained from the same brute-force start
     anchor_line = None
@@ -906,6 +1001,8 @@ def run_ours(args, rank, world, local):
         line["reconstruction"] = recon
     if knn_line:
         line["knn"] = knn_line
+    if unit_line:
+        line["unit_float"] = unit_line
     if anchor_line:
         line["anchor_loop"] = anchor_line
     clocks = clk.summary()

@@ -131,6 +131,97 @@ __global__ void __launch_bounds__(UnitCfg<C>::QB) k_dense_unit(const UnitDenseAr
   }
 }
 
+// Gray brute force on packed fp32 pairs: a thread takes two queries (one per
+// half of a float2) and meets every reference value duplicated in both halves
+// of a shared-memory float2, so one sub/fma pair of f32x2 instructions
+// advances both queries' sums.  Each half follows the same order of
+// operations as the scalar path.
+constexpr int kUnitGrayThreads = 128, kUnitGrayRT = 32;
+
+__global__ void __launch_bounds__(kUnitGrayThreads) k_dense_unit_gray(const UnitDenseArgs a) {
+  constexpr int D = 64, QB = 2 * kUnitGrayThreads, RT = kUnitGrayRT;
+  __shared__ __align__(16) float2 s_r[RT][D];
+  const int64_t nq = a.list ? (int64_t)*a.list_count : a.Q;
+  if (!a.list && a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[kStatDenseQueries] = (unsigned long long)nq;
+  const int64_t base = (int64_t)blockIdx.x * QB;
+  if (base >= nq) return;   // uniform for the CTA
+  const FrameItem& it = a.one;
+  int64_t qi[2] = {0, 0};
+  bool live[2];
+  float2 qq[D];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t i = base + h * kUnitGrayThreads + threadIdx.x;
+    live[h] = i < nq;
+    uint32_t s = 0;
+    int y = 0, x = 0;
+    if (live[h]) {
+      qi[h] = a.list ? (int64_t)a.list[i] - it.query_begin : i;
+      y = (int)(qi[h] / it.Wq);
+      x = (int)(qi[h] % it.Wq);
+      for (int dy = 0; dy < 8; ++dy)
+        for (int j = 0; j < 8; ++j) {
+          const uint32_t v = it.frame[(int64_t)(y + dy) * it.W + x + j];
+          s += v * v;
+        }
+    }
+    const float nv = unit_scale(s);
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+      const float f = live[h] ? unit_coord(it.frame[(int64_t)(y + k / 8) * it.W + x + k % 8], s, nv) : 0.f;
+      if (h == 0) qq[k].x = f;
+      else qq[k].y = f;
+    }
+  }
+  float bd0 = __int_as_float(0x7f800000), bd1 = bd0, ba0 = bd0, ba1 = bd0;
+  int bi0 = 0, bi1 = 0;
+  for (int r0 = 0; r0 < a.n; r0 += RT) {
+    const int nt = min(RT, a.n - r0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < nt * D; k += kUnitGrayThreads) {
+      const float v = __ldg(a.Rf + (int64_t)r0 * D + k);
+      s_r[k / D][k % D] = make_float2(v, v);
+    }
+    __syncthreads();
+    // two references per pass (two independent dependency chains per thread);
+    // an odd tail repeats the last reference, which cannot change the result
+    for (int j = 0; j < nt; j += 2) {
+      const int j2 = j + 1 < nt ? j + 1 : j;
+      const float4* ra = reinterpret_cast<const float4*>(s_r[j]);
+      const float4* rb = reinterpret_cast<const float4*>(s_r[j2]);
+      float2 acc = make_float2(0.f, 0.f), acc2 = acc;
+#pragma unroll
+      for (int v = 0; v < D / 2; ++v) {
+        const float4 x = ra[v], y = rb[v];   // values 2v and 2v + 1, each twice
+        acc = unit_step2(acc, qq[2 * v], make_float2(x.x, x.y));
+        acc2 = unit_step2(acc2, qq[2 * v], make_float2(y.x, y.y));
+        acc = unit_step2(acc, qq[2 * v + 1], make_float2(x.z, x.w));
+        acc2 = unit_step2(acc2, qq[2 * v + 1], make_float2(y.z, y.w));
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float2 s2 = u ? acc2 : acc;
+        const int r = r0 + (u ? j2 : j);
+        if (s2.x <= ba0) {
+          const float d = __fsqrt_rn(s2.x);
+          if (d < bd0) { bd0 = d; ba0 = s2.x; bi0 = r; }
+        }
+        if (s2.y <= ba1) {
+          const float d = __fsqrt_rn(s2.y);
+          if (d < bd1) { bd1 = d; ba1 = s2.y; bi1 = r; }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    if (!live[h]) continue;
+    it.out_annf[qi[h]] = h ? bi1 : bi0;
+    if (it.out_dist) it.out_dist[qi[h]] = __float_as_uint(h ? bd1 : bd0);
+    if (it.out_count) it.out_count[qi[h]] = (uint32_t)a.n;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_unit_tables(Index& ix, cudaStream_t s) {
@@ -154,8 +245,8 @@ cudaError_t launch_dense_unit(const DenseArgs& d, Index& ix, cudaStream_t s) {
   u.stats = d.stats;
   prof_begin(ix, kSlotDense, s);
   if (ix.C == 1) {
-    const int64_t g = (d.Q + UnitCfg<1>::QB - 1) / UnitCfg<1>::QB;
-    k_dense_unit<1><<<(unsigned)(g > 0 ? g : 1), UnitCfg<1>::QB, 0, s>>>(u);
+    const int64_t g = (d.Q + 2 * kUnitGrayThreads - 1) / (2 * kUnitGrayThreads);
+    k_dense_unit_gray<<<(unsigned)(g > 0 ? g : 1), kUnitGrayThreads, 0, s>>>(u);
   } else {
     const int64_t g = (d.Q + UnitCfg<3>::QB - 1) / UnitCfg<3>::QB;
     k_dense_unit<3><<<(unsigned)(g > 0 ? g : 1), UnitCfg<3>::QB, 0, s>>>(u);

@@ -22,6 +22,18 @@ __device__ __forceinline__ float unit_step(float acc, float a, float b) {
   return __fmaf_rn(t, t, acc);
 }
 
+// The same step on two independent (a, b) pairs at once: the packed f32x2
+// forms round each half exactly like the scalar _rn operations.
+__device__ __forceinline__ float2 unit_step2(float2 acc, float2 a, float2 b) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rc, rt;\n"
+      " mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+      " sub.rn.f32x2 rt, ra, rb;\n fma.rn.f32x2 rc, rt, rt, rc;\n mov.b64 {%0, %1}, rc;\n}\n"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(acc.x), "f"(acc.y));
+  return r;
+}
+
 __device__ __forceinline__ float unit_scale(uint32_t sumsq) { return __fsqrt_rn((float)sumsq); }
 
 __device__ __forceinline__ float unit_coord(uint32_t v, uint32_t sumsq, float nv) {
