@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(kUnitGrayThreads) k_dense_unit_gray(const Unit
       const float4* ra = reinterpret_cast<const float4*>(s_r[j]);
       const float4* rb = reinterpret_cast<const float4*>(s_r[j2]);
       float2 acc = make_float2(0.f, 0.f), acc2 = acc;
+      bool beaten = false;
 #pragma unroll
       for (int v = 0; v < D / 2; ++v) {
         const float4 x = ra[v], y = rb[v];   // values 2v and 2v + 1, each twice
@@ -197,7 +198,18 @@ __global__ void __launch_bounds__(kUnitGrayThreads) k_dense_unit_gray(const Unit
         acc2 = unit_step2(acc2, qq[2 * v], make_float2(y.x, y.y));
         acc = unit_step2(acc, qq[2 * v + 1], make_float2(x.z, x.w));
         acc2 = unit_step2(acc2, qq[2 * v + 1], make_float2(y.z, y.w));
+        // a running sum never decreases (each step adds t^2 >= 0 and rounds
+        // monotonically): once every partial sum of the warp exceeds its
+        // query's best full sum, neither reference can win -- stop them
+        if (v == 7 || v == 15 || v == 23) {
+          const bool out = (!live[0] || (acc.x > ba0 && acc2.x > ba0)) && (!live[1] || (acc.y > ba1 && acc2.y > ba1));
+          if (__all_sync(0xffffffffu, out)) {
+            beaten = true;
+            break;
+          }
+        }
       }
+      if (beaten) continue;
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const float2 s2 = u ? acc2 : acc;
