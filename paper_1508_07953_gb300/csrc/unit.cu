@@ -173,8 +173,26 @@ __global__ void __launch_bounds__(kUnitGrayThreads) k_dense_unit_gray(const Unit
       else qq[k].y = f;
     }
   }
-  float bd0 = __int_as_float(0x7f800000), bd1 = bd0, ba0 = bd0, ba1 = bd0;
+  // best so far (distance, index) and the largest sum that can still match
+  // it; a routed query starts from its previous match (usually close, so the
+  // early exit below bites from the first tile), frame 0 from nothing
+  float bd0 = __int_as_float(0x7f800000), bd1 = bd0;
   int bi0 = 0, bi1 = 0;
+  if (it.prev) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!live[h]) continue;
+      const int rp = it.prev[qi[h]];
+      if ((unsigned)rp >= (unsigned)a.n) continue;
+      const float* rr = a.Rf + (int64_t)rp * D;
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < D; ++k) acc = unit_step(acc, h ? qq[k].y : qq[k].x, __ldg(rr + k));
+      if (h) { bd1 = __fsqrt_rn(acc); bi1 = rp; }
+      else { bd0 = __fsqrt_rn(acc); bi0 = rp; }
+    }
+  }
+  float ba0 = unit_root_bound(bd0), ba1 = unit_root_bound(bd1);
   for (int r0 = 0; r0 < a.n; r0 += RT) {
     const int nt = min(RT, a.n - r0);
     __syncthreads();
@@ -200,7 +218,8 @@ __global__ void __launch_bounds__(kUnitGrayThreads) k_dense_unit_gray(const Unit
         acc2 = unit_step2(acc2, qq[2 * v + 1], make_float2(y.z, y.w));
         // a running sum never decreases (each step adds t^2 >= 0 and rounds
         // monotonically): once every partial sum of the warp exceeds its
-        // query's best full sum, neither reference can win -- stop them
+        // query's bound (no larger sum has a root that beats or ties the
+        // best), neither reference can win -- stop them
         if (v == 7 || v == 15 || v == 23) {
           const bool out = (!live[0] || (acc.x > ba0 && acc2.x > ba0)) && (!live[1] || (acc.y > ba1 && acc2.y > ba1));
           if (__all_sync(0xffffffffu, out)) {
@@ -216,11 +235,11 @@ __global__ void __launch_bounds__(kUnitGrayThreads) k_dense_unit_gray(const Unit
         const int r = r0 + (u ? j2 : j);
         if (s2.x <= ba0) {
           const float d = __fsqrt_rn(s2.x);
-          if (d < bd0) { bd0 = d; ba0 = s2.x; bi0 = r; }
+          if (d < bd0 || (d == bd0 && r < bi0)) { bd0 = d; bi0 = r; ba0 = unit_root_bound(d); }
         }
         if (s2.y <= ba1) {
           const float d = __fsqrt_rn(s2.y);
-          if (d < bd1) { bd1 = d; ba1 = s2.y; bi1 = r; }
+          if (d < bd1 || (d == bd1 && r < bi1)) { bd1 = d; bi1 = r; ba1 = unit_root_bound(d); }
         }
       }
     }

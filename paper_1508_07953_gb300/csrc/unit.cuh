@@ -57,6 +57,16 @@ __device__ __forceinline__ float unit_dist(const float* a, const float* b) {
   return __fsqrt_rn(acc);
 }
 
+// Largest running sum whose rounded root is at most d: a sum above it has a
+// root above d (the root is monotone), so it can neither beat nor tie d.
+__device__ __forceinline__ float unit_root_bound(float d) {
+  if (!(d < __int_as_float(0x7f800000))) return d;   // +inf: nothing is excluded
+  uint32_t a = __float_as_uint(__fmul_rn(d, d));
+  while (a > 0u && __fsqrt_rn(__uint_as_float(a)) > d) --a;
+  while (__fsqrt_rn(__uint_as_float(a + 1)) <= d) ++a;
+  return __uint_as_float(a);
+}
+
 __device__ __forceinline__ float unit_width(int p, int q, float C) {
   return __fdiv_rn(__fmul_rn((float)p, C), (float)q);
 }
