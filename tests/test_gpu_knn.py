@@ -161,3 +161,25 @@ def test_720p_rgb_sampled(rt):
 
 def test_1080p_scene_cut_sampled(rt):
     _sampled(rt, synth.WORKLOADS["1080p"], 39, 42, 8, 150, 32)
+
+
+def test_bad_prev_sets_status_and_empty_lists(rt):
+    R, KP, frame, prev = synth.random_case(604, 64, 4, 1, 12, 12)
+    prev[0, 0] = 64
+    prev[2, 3] = -1
+    idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
+    a, kn, kd, c = rt.knn(idx, _dev(frame), _dev(prev), 3, _params(rt, 64))
+    assert rt.riann_status(idx) & rt.RIANN_DEV_BAD_PREV
+    kn = kn.cpu().numpy()
+    kd = kd.cpu().numpy().view(np.uint32)
+    for (y, x) in ((0, 0), (2, 3)):
+        assert (kn[y, x] == -1).all() and (kd[y, x] == 0xFFFFFFFF).all() and a.cpu().numpy()[y, x] == -1
+    # every other query matches the oracle on a valid copy of the field
+    ok = prev.copy()
+    ok[0, 0] = 0
+    ok[2, 3] = 0
+    o = oracle.riann_knn(oracle.Index(R, KP), frame, ok, 3, alpha=(1, 4), ring_limit=8)
+    mask = np.ones(prev.shape, bool)
+    mask[0, 0] = mask[2, 3] = False
+    assert np.array_equal(kn[mask], o[0][mask])
+    idx.close()

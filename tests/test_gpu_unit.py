@@ -139,3 +139,20 @@ def test_unsupported_forms(rt):
         rt.riann_batch_create(idx, 2, 100)
     assert e.value.code == rt.RIANN_ERR_UNSUPPORTED
     idx.close()
+
+
+def test_bad_prev_sets_status(rt):
+    R, KP, frame, prev = synth.random_case(831, 64, 4, 1, 12, 12)
+    prev[1, 1] = 1000
+    idx = rt.riann_build_unit_index(_dev(R), _dev(KP))
+    a, d, c = rt.annf(idx, _dev(frame), _dev(prev), _params(rt, 64, (1, 4), -1))
+    assert rt.riann_status(idx) & rt.RIANN_DEV_BAD_PREV
+    a = a.cpu().numpy()
+    assert a[1, 1] == -1
+    ok = prev.copy()
+    ok[1, 1] = 0
+    oa, od, oc = oracle.riann_unit_frame(R, KP, frame, ok, (1, 4), -1)
+    mask = np.ones(prev.shape, bool)
+    mask[1, 1] = False
+    assert np.array_equal(a[mask], oa[mask])
+    idx.close()
