@@ -29,17 +29,13 @@ __global__ void k_unit_key_distances(const float* __restrict__ Rf, const float* 
 }
 
 // Brute force: argmin over all references of d(q', r'), lower index on ties.
-// A CTA takes QB queries (one per thread) and walks the references in tiles
-// of RT staged in shared memory; gray keeps q' in registers, RGB in shared
-// memory (column per query, conflict-free).  A reference whose running sum
-// already exceeds the best one's cannot win (sqrt is monotone and a tie
-// keeps the lower index), so the root is taken only for the others.
-template <int C>
-struct UnitCfg;
-template <>
-struct UnitCfg<1> { static constexpr int QB = 128, RT = 32; };   // 8 KB of reference tile
-template <>
-struct UnitCfg<3> { static constexpr int QB = 32, RT = 16; };    // 24 KB of queries + 12 KB of tile
+// RGB (D = 192): a CTA takes 32 queries (one per thread, q' in shared memory,
+// a column per query: conflict-free) and walks the references in tiles of 16
+// staged in shared memory.  A reference whose running sum already exceeds
+// the best one's cannot win (the root is monotone and a tie keeps the lower
+// index), so the root is taken only for the others.  Gray has its own
+// packed-pair kernel below.
+constexpr int kUnitRgbQB = 32, kUnitRgbRT = 16;   // 24 KB of queries + 12 KB of tile
 
 struct UnitDenseArgs {
   FrameItem one;
@@ -51,12 +47,10 @@ struct UnitDenseArgs {
   unsigned long long* stats;
 };
 
-template <int C>
-__global__ void __launch_bounds__(UnitCfg<C>::QB) k_dense_unit(const UnitDenseArgs a) {
-  constexpr int D = 64 * C, QB = UnitCfg<C>::QB, RT = UnitCfg<C>::RT;
-  constexpr bool QREG = C == 1;
+__global__ void __launch_bounds__(kUnitRgbQB) k_dense_unit_rgb(const UnitDenseArgs a) {
+  constexpr int C = 3, D = 64 * C, QB = kUnitRgbQB, RT = kUnitRgbRT;
   __shared__ __align__(16) float s_r[RT][D];
-  __shared__ float s_q[QREG ? 1 : D][QREG ? 1 : QB];
+  __shared__ float s_q[D][QB];
   const int64_t nq = a.list ? (int64_t)*a.list_count : a.Q;
   if (!a.list && a.stats && blockIdx.x == 0 && threadIdx.x == 0) a.stats[kStatDenseQueries] = (unsigned long long)nq;
   const int64_t i = (int64_t)blockIdx.x * QB + threadIdx.x;
@@ -64,7 +58,6 @@ __global__ void __launch_bounds__(UnitCfg<C>::QB) k_dense_unit(const UnitDenseAr
   const bool live = i < nq;
   const FrameItem& it = a.one;
   int64_t qi = 0;
-  float qv[QREG ? D : 1];
   if (live) {
     qi = a.list ? (int64_t)a.list[i] - it.query_begin : i;
     const int y = (int)(qi / it.Wq), x = (int)(qi % it.Wq);
@@ -75,14 +68,9 @@ __global__ void __launch_bounds__(UnitCfg<C>::QB) k_dense_unit(const UnitDenseAr
         s += v * v;
       }
     const float nv = unit_scale(s);
-#pragma unroll
     for (int dy = 0; dy < 8; ++dy)
-#pragma unroll
-      for (int j = 0; j < 8 * C; ++j) {
-        const float f = unit_coord(it.frame[((int64_t)(y + dy) * it.W + x) * C + j], s, nv);
-        if (QREG) qv[dy * 8 * C + j] = f;
-        else s_q[QREG ? 0 : dy * 8 * C + j][QREG ? 0 : threadIdx.x] = f;
-      }
+      for (int j = 0; j < 8 * C; ++j)
+        s_q[dy * 8 * C + j][threadIdx.x] = unit_coord(it.frame[((int64_t)(y + dy) * it.W + x) * C + j], s, nv);
   }
   float bd = __int_as_float(0x7f800000), bacc = bd;
   int bi = 0;
@@ -102,17 +90,10 @@ __global__ void __launch_bounds__(UnitCfg<C>::QB) k_dense_unit(const UnitDenseAr
 #pragma unroll
       for (int v = 0; v < D / 4; ++v) {
         const float4 rv = r4[v];
-        if (QREG) {
-          acc = unit_step(acc, qv[QREG ? 4 * v + 0 : 0], rv.x);
-          acc = unit_step(acc, qv[QREG ? 4 * v + 1 : 0], rv.y);
-          acc = unit_step(acc, qv[QREG ? 4 * v + 2 : 0], rv.z);
-          acc = unit_step(acc, qv[QREG ? 4 * v + 3 : 0], rv.w);
-        } else {
-          acc = unit_step(acc, s_q[QREG ? 0 : 4 * v + 0][QREG ? 0 : threadIdx.x], rv.x);
-          acc = unit_step(acc, s_q[QREG ? 0 : 4 * v + 1][QREG ? 0 : threadIdx.x], rv.y);
-          acc = unit_step(acc, s_q[QREG ? 0 : 4 * v + 2][QREG ? 0 : threadIdx.x], rv.z);
-          acc = unit_step(acc, s_q[QREG ? 0 : 4 * v + 3][QREG ? 0 : threadIdx.x], rv.w);
-        }
+        acc = unit_step(acc, s_q[4 * v + 0][threadIdx.x], rv.x);
+        acc = unit_step(acc, s_q[4 * v + 1][threadIdx.x], rv.y);
+        acc = unit_step(acc, s_q[4 * v + 2][threadIdx.x], rv.z);
+        acc = unit_step(acc, s_q[4 * v + 3][threadIdx.x], rv.w);
       }
       if (acc <= bacc) {
         const float d = __fsqrt_rn(acc);
@@ -279,8 +260,8 @@ cudaError_t launch_dense_unit(const DenseArgs& d, Index& ix, cudaStream_t s) {
     const int64_t g = (d.Q + 2 * kUnitGrayThreads - 1) / (2 * kUnitGrayThreads);
     k_dense_unit_gray<<<(unsigned)(g > 0 ? g : 1), kUnitGrayThreads, 0, s>>>(u);
   } else {
-    const int64_t g = (d.Q + UnitCfg<3>::QB - 1) / UnitCfg<3>::QB;
-    k_dense_unit<3><<<(unsigned)(g > 0 ? g : 1), UnitCfg<3>::QB, 0, s>>>(u);
+    const int64_t g = (d.Q + kUnitRgbQB - 1) / kUnitRgbQB;
+    k_dense_unit_rgb<<<(unsigned)(g > 0 ? g : 1), kUnitRgbQB, 0, s>>>(u);
   }
   prof_end(ix, kSlotDense, s);
   return cudaGetLastError();
