@@ -10,7 +10,7 @@
 // byte (dy, dx, c) of each such patch's match.  The average is rounded half
 // up to 8 bits in integers: (2 sum + count) / (2 count).  Gray: the CTA also
 // stages the 585 matched rows (64 B each, padded to 68 B so that the 32
-// patches a warp reads at one (dy, dx) fall in distinct banks) with coalesced
+// patches a warp reads at one (dy, dx) fall in distinct banks) with 16-byte
 // loads and gathers bytes from shared memory.  RGB (192-byte rows): the
 // gathers go to global memory, where each row is reused from L1.
 #include "reconstruct.cuh"
@@ -44,11 +44,18 @@ __global__ void __launch_bounds__(kTY * kTX) k_reconstruct(const ReconArgs a) {
   }
   __syncthreads();
   if (C == 1) {
-    const uint32_t* R32 = reinterpret_cast<const uint32_t*>(a.R);
-    for (int i = threadIdx.x; i < kPY * kPX * 16; i += blockDim.x) {
-      const int p = i >> 4, w = i & 15;
+    // one 16-byte load per quarter row (rows are 64-byte aligned); the
+    // shared rows keep their 68-byte stride, so the words are stored singly
+    const uint4* R4 = reinterpret_cast<const uint4*>(a.R);
+    for (int i = threadIdx.x; i < kPY * kPX * 4; i += blockDim.x) {
+      const int p = i >> 2, c = i & 3;
       const int32_t r = s_f[p / kPX][p % kPX];
-      s_rows[p][w] = r >= 0 ? __ldg(R32 + (int64_t)r * 16 + w) : 0u;
+      const uint4 v = r >= 0 ? __ldg(R4 + (int64_t)r * 4 + c) : make_uint4(0u, 0u, 0u, 0u);
+      uint32_t* d = &s_rows[p][4 * c];
+      d[0] = v.x;
+      d[1] = v.y;
+      d[2] = v.z;
+      d[3] = v.w;
     }
     __syncthreads();
   }
