@@ -629,7 +629,7 @@ def run_anchor(riann, idx, frames, H, W, stream, flush, steps: int, warm: int = 
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_knn(riann, idx, frames, frames_np, H, W, stream, flush, params, steps, k, R, KP, ref_field, cpu):
-    """k-NN output (Sec. 6, k best of the argmin's candidate set) on the same
+    """k-NN output (Sec. 7, k best of the argmin's candidate set) on the same
     frames: brute-force first frame, warm-up, then `steps` timed frames with
     the L2 flushed before each; per-kernel event times; optionally the oracle
     on a sample of positions."""

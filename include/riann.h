@@ -23,7 +23,7 @@
  *       count = n
  *   else field(q) = argmin over S u {r_p} of ||q - r||^2, count = |S|
  *   ties go to the lower reference index.  With no previous field (frame 0,
- *   Alg. 1 "Initialize") every query is answered by brute force.
+ *   Alg. 1's initialisation step) every query is answered by brute force.
  * Membership is decided exactly in integers, so results are bit-reproducible.
  *
  * Memory ownership: the caller owns every buffer it passes in; the library
@@ -74,7 +74,8 @@ enum {
 
 typedef struct {
   /* Ring half-width eps = (alpha_num / alpha_den) * dist(q, r_p)
-   * (Sec. 3.2: "epsilon = alpha * dist(r_i, q)", alpha = 0.25 in the paper).
+   * (Sec. 3.2: the ring half-width is alpha times the distance from the query
+   * to its previous match; the paper uses alpha = 0.25).
    * 1 <= alpha_den <= 8, 0 <= alpha_num <= 8 * alpha_den. */
   int32_t alpha_num;
   int32_t alpha_den;
@@ -97,8 +98,8 @@ typedef struct {
 } riann_index_info_t;
 
 /*
- * Pre-processing (Sec. 3.3 "at the pre-processing stage we compute ... a
- * sorted list of its distances"; Sec. 3.4 "Building a reference model").
+ * Pre-processing (Sec. 3.3: every anchor keeps its distances to the
+ * references as a sorted list, computed once; Sec. 3.4: the reference model).
  * Copies the n reference patches and K key points, computes every
  * key-point-to-reference distance and, per key point, the references sorted by
  * (distance, index); also a bf16 copy of R for the brute-force path.
@@ -157,7 +158,7 @@ int riann_index_tables(riann_index_t idx, riann_stream_t stream,
  * frame loop: every query patch of the frame).
  *   d_frame       device uint8 [H][W][channels]; 8 <= H, W; (H-7)*(W-7) < 2^31
  *   d_prev_annf   device int32 [H-7][W-7], the previous field; NULL = frame 0
- *                 (every query answered by brute force, Alg. 1 "Initialize")
+ *                 (every query answered by brute force, Alg. 1's initialisation)
  *   d_out_annf    device int32 [H-7][W-7] (required; may not alias d_prev_annf)
  *   d_out_dist    device uint32 [H-7][W-7], squared distance of the match (nullable)
  *   d_out_count   device uint32 [H-7][W-7], |S| or n for brute force (nullable)
@@ -170,8 +171,8 @@ int riann_annf_frame(riann_index_t idx, const riann_params* p, riann_stream_t st
                      uint32_t* d_out_dist, uint32_t* d_out_count);
 
 /*
- * k-NN variant of riann_annf_frame (Sec. 6: the method can return several
- * close matches instead of one).  The candidate set of a query is the one the
+ * k-NN variant of riann_annf_frame (Sec. 7: the method can return more than
+ * one match per query).  The candidate set of a query is the one the
  * argmin of riann_annf_frame ranges over -- S u {r_p} (r_p counted once) for a
  * ring-answered query, all n references for frame 0 and for queries routed to
  * brute force -- and the output is its k smallest entries in ascending
@@ -242,7 +243,7 @@ int riann_stack_frames(riann_stream_t stream, const uint8_t* d_f0, const uint8_t
 
 /*
  * Brute-force exact nearest neighbour field (the dense tensor-core path on its
- * own; Alg. 1 "Initialize" replaced by exact NN).  Arguments as riann_annf_frame.
+ * own; Alg. 1's initialisation replaced by exact NN).  Arguments as riann_annf_frame.
  */
 int riann_exact_nn(riann_index_t idx, riann_stream_t stream,
                    const uint8_t* d_frame, int32_t H, int32_t W,
@@ -307,7 +308,7 @@ int riann_profile_read(riann_index_t idx, riann_stream_t stream, float* ms, int3
  * buffered, plus the scratch of one frame, so sessions on different CUDA
  * streams run concurrently.  The first frame of a session (and the first
  * after riann_session_reset, e.g. at a known scene cut) is answered by brute
- * force (Alg. 1 "Initialize").  Results are identical to chaining
+ * force (Alg. 1's initialisation).  Results are identical to chaining
  * riann_annf_frame calls by hand.
  * ------------------------------------------------------------------------ */
 typedef struct riann_session_s* riann_session_t;
@@ -481,8 +482,8 @@ int riann_server_stream_counts(riann_server_t s, int32_t stream_id, int64_t* sub
                                int64_t* completed);
 
 /* ------------------------------------------------------------------------
- * Reconstruction (Sec. 4: "reconstruct the video by replacing each patch with
- * its match and averaging overlapping patches", error
+ * Reconstruction (Sec. 4: the video is rebuilt by replacing every patch with
+ * its match and averaging where patches overlap; error
  * E = ||f_GT - f_R||_2 / ||f_GT||_2).
  *
  * d_annf: device int32 [H-7][W-7], a field over this index (entries outside
@@ -547,7 +548,8 @@ int riann_anchor_frame(riann_full_t f, const riann_anchor_params* p, riann_strea
                        int32_t* d_out_annf, uint32_t* d_out_dist, uint32_t* d_out_count,
                        uint32_t* d_out_rings);
 
-/* Alg. 1 "Initialize: ANNF^(0)(x,y) ~ Uniform[1,|R|]" (0-based): writes the
+/* Alg. 1's random initial field (each entry uniform over the references;
+ * 0-based here): writes the
  * int32 [H-7][W-7] field d_out_annf, entry q = (x * n) >> 32 with x the first
  * word of Philox4x32-10 at counter (q, 0, frame_id, 1), key (seed low, seed
  * high).  Asynchronous on `stream`. */

@@ -273,7 +273,7 @@ def stack_frames(f0: np.ndarray, f1: np.ndarray, f2: np.ndarray) -> np.ndarray:
 def riann_knn(index: Index, frame: np.ndarray, prev: Optional[np.ndarray], k: int,
               alpha=(1, 4), ring_limit: int = -1, qidx=None):
     """k-NN output of one RIANN query step: (knn [.., k] int32, knn_dist [.., k]
-    uint32, count), the k best of the argmin's candidate set (Sec. 6)."""
+    uint32, count), the k best of the argmin's candidate set (Sec. 7)."""
     lib = _load()
     f = _frame3(frame)
     H, W, C = f.shape

@@ -103,8 +103,8 @@ static int cmp_entry(const void* x, const void* y) {
   return 0;
 }
 
-/* Sorted lists (Sec. 3.3: "for each reference patch a sorted list of its
- * distances", here one list per key point), ascending by (distance, index). */
+/* Sorted lists (Sec. 3.3 keeps, per anchor, its distances to the references
+ * in sorted order; here one list per key point), ascending by (distance, index). */
 void oracle_sort_tables(const uint32_t* P, int32_t n, int32_t K, uint32_t* TA, int32_t* Tid) {
 #pragma omp parallel for schedule(static)
   for (int32_t m = 0; m < K; ++m) {
@@ -235,8 +235,8 @@ void oracle_riann_definitional(const uint8_t* frame, int32_t H, int32_t W, int32
 }
 
 /*
- * k-NN output (Sec. 6: the method can return several closest matches, not
- * only one).  The candidate set of a query is the set Alg. 1 takes its argmin
+ * k-NN output (Sec. 7: the method can return more than one match per
+ * query).  The candidate set of a query is the set Alg. 1 takes its argmin
  * over, with the readings of oracle_riann_definitional: S u {r_p} (r_p once)
  * when some ring holds at most ring_limit references, otherwise (and for
  * frame 0) all of R.  The output is that set sorted by (distance, index),
@@ -703,7 +703,7 @@ static int cmp_u64(const void* x, const void* y) {
   return u < v ? -1 : (u > v ? 1 : 0);
 }
 
-/* Sec. 3.4: "calculate the pairwise distance matrix and sort it". */
+/* Sec. 3.4: the pairwise distances, each row sorted. */
 void oracle_full_tables(const uint8_t* R, int32_t n, int32_t D, uint64_t* T) {
 #pragma omp parallel for schedule(dynamic, 16)
   for (int32_t i = 0; i < n; ++i) {

@@ -65,7 +65,7 @@ void oracle_riann_definitional(const uint8_t* frame, int32_t H, int32_t W, int32
                                int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* nseed);
 
 /* RIANN query step, indexed mode: ring bounds by binary search on the sorted
- * per-key lists (Sec. 3.3, "two binary searches"), candidates enumerated from
+ * per-key lists (Sec. 3.3: two binary searches per ring), candidates enumerated from
  * the smallest ring and filtered by the other rings. */
 void oracle_riann_indexed(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
                           const uint8_t* R, int32_t n,
@@ -76,7 +76,7 @@ void oracle_riann_indexed(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
                           const int64_t* qidx, int64_t nq,
                           int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* nseed);
 
-/* k-NN output (Sec. 6, "several closest matches"): the set the argmin of
+/* k-NN output (Sec. 7: more than one match per query): the set the argmin of
  * oracle_riann_definitional ranges over -- S u {r_p} (r_p once), or all of R
  * for frame 0 / rings too wide -- sorted by (dist, index) and cut to its first
  * k entries: knn[i*k + j], knn_dist[i*k + j] (nullable); -1 / UINT32_MAX past
@@ -117,8 +117,8 @@ void oracle_riann_unit(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
                        const int64_t* qidx, int64_t nq,
                        int32_t* annf, float* dist, uint32_t* count);
 
-/* Reconstruction by patch replacement (Sec. 4: "replacing each patch with
- * its match and averaging overlapping patches").  out[y][x][c] = rounded
+/* Reconstruction by patch replacement (Sec. 4: every patch is replaced by
+ * its match and the overlaps are averaged).  out[y][x][c] = rounded
  * average over the query patches (py, px) that cover (y, x) -- py <= y < py+8,
  * px <= x < px+8, inside the query grid, with annf[py][px] in [0, n) -- of
  * byte (y-py, x-px, c) of their matched reference patch.  Reading taken here:
@@ -135,7 +135,7 @@ void oracle_reconstruct(const uint8_t* R, int32_t n, int32_t C, const int32_t* a
  * as 1, 2, 3", SC'11): counter ctr[4] and key key[2] -> out[4]. */
 void oracle_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out);
 
-/* Sec. 3.3 / Sec. 3.4 "sorted distance matrix": T[i*n + j] = (A << 32) | id,
+/* Sec. 3.3 / Sec. 3.4, the sorted matrix of pairwise distances: T[i*n + j] = (A << 32) | id,
  * row i holding every reference sorted ascending by (A = ||r_i - r_id||^2, id). */
 void oracle_full_tables(const uint8_t* R, int32_t n, int32_t D, uint64_t* T);
 
@@ -161,7 +161,8 @@ void oracle_riann_anchor(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
                          const int64_t* qidx, int64_t nq,
                          int32_t* annf, uint32_t* dist, uint32_t* count, uint32_t* rings);
 
-/* Alg. 1 "Initialize: ANNF^(0)(x,y) ~ Uniform[1,|R|]", 0-based: entry q =
+/* Alg. 1's random initial field (each entry uniform over the references;
+ * 0-based here): entry q =
  * (x * n) >> 32, x the first word of Philox4x32-10 with counter
  * (q, 0, frame_id, 1) and key (seed low, seed high). */
 void oracle_random_field(int32_t H, int32_t W, int32_t n, uint64_t seed, uint32_t frame_id, int32_t* annf);

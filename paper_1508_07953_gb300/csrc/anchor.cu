@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
   }
 }
 
-// Alg. 1 "Initialize": entry q = (x * n) >> 32, x from Philox4x32-10 with counter (q, 0, frame id, 1).
+// Alg. 1's random initial field: entry q = (x * n) >> 32, x from Philox4x32-10 with counter (q, 0, frame id, 1).
 __global__ void k_random_field(int64_t Q, int n, uint32_t key0, uint32_t key1, uint32_t frame_id, int32_t* out) {
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < Q; q += (int64_t)gridDim.x * blockDim.x) {
     uint32_t x;

@@ -610,7 +610,7 @@ int riann_anchor_frame(riann_full_t f, const riann_anchor_params* p, riann_strea
   Index& ix = *f->idx;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const int64_t Q = (int64_t)(H - 7) * (W - 7);
-  if (!d_prev) {   // no previous field: brute force (Alg. 1 "Initialize" read as exact NN)
+  if (!d_prev) {   // no previous field: brute force (Alg. 1's initialisation read as exact NN)
     int rc = riann_exact_nn(f->idx, stream, d_frame, H, W, d_out_annf, d_out_dist);
     if (rc) return rc;
     cudaError_t e = d_out_count ? launch_fill_u32(d_out_count, Q, (uint32_t)ix.n, s) : cudaSuccess;

@@ -35,7 +35,7 @@ enum TileShape { kTile4x32 = 0, kTile8x16 = 1, kTileShapes = 2 };
 __host__ __device__ constexpr uint32_t max_sqdist(int dim) { return (uint32_t)dim * 255u * 255u; }
 
 // One frame of a launch: its pixels, its previous field (nullptr: every query
-// is answered by brute force, Alg. 1 "Initialize"), its outputs, and its place
+// is answered by brute force, Alg. 1's initialisation step), its outputs, and its place
 // in the launch's tile and query numbering (a single-frame launch has one item
 // with both offsets 0).  Global query id = query_begin + y * Wq + x.
 struct FrameItem {

@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     const int y = ty0 + ly, x = tx0 + lx;
     if (y >= it.Hq || x >= it.Wq) continue;
     const int64_t qi = (int64_t)y * it.Wq + x;
-    if (!it.prev) {   // no previous field: brute force (Alg. 1 "Initialize")
+    if (!it.prev) {   // no previous field: brute force (Alg. 1's initialisation step)
       if (lane == 0) s_dense[atomicAdd(&s_ndense, 1)] = (int32_t)(it.query_begin + qi);
       continue;
     }

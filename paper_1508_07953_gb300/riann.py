@@ -338,7 +338,7 @@ def riann_knn_frame(index: RiannIndex, params: riann_params, frame: torch.Tensor
                     out_knn: torch.Tensor, out_knn_dist: Optional[torch.Tensor] = None,
                     out_count: Optional[torch.Tensor] = None,
                     stream: Optional[torch.cuda.Stream] = None) -> None:
-    """k-NN query step (Sec. 6): out_knn / out_knn_dist [H-7][W-7][k], the k best
+    """k-NN query step (Sec. 7): out_knn / out_knn_dist [H-7][W-7][k], the k best
     of the argmin's candidate set in ascending (distance, index) order."""
     H, W = _frame_dims(frame, index.C)
     Q = (H - 7) * (W - 7)

@@ -25,7 +25,7 @@ from typing import Optional, Sequence
 
 import numpy as np
 
-PATCH = 8  # patch side (Sec. 4: "Patches are of size 8x8")
+PATCH = 8  # patch side (Sec. 4 uses 8x8 patches)
 
 
 # ----------------------------------------------------------------------------

@@ -1,4 +1,4 @@
-"""k-NN output (Sec. 6) on the GPU vs the CPU oracle, bit-exact.
+"""k-NN output (Sec. 7) on the GPU vs the CPU oracle, bit-exact.
 
 Covers the ring kernel's k-NN variant (warp-wide best-k list over S u {r_p})
 and the tensor-core brute force's best-8 lists (frame 0, routed queries,

@@ -1,4 +1,4 @@
-"""Pins of the oracle's k-NN output (Sec. 6: several closest matches per query).
+"""Pins of the oracle's k-NN output (Sec. 7: more than one match per query).
 
 Each check derives the expected lists independently of ``oracle_riann_knn``:
 numpy brute force with an explicit (distance, index) sort, the pinned argmin
