@@ -595,7 +595,7 @@ def run_anchor(riann, idx, frames, H, W, stream, flush, steps: int, warm: int = 
                       "exact_nn_agreement": float((exact == prev).double().mean()),
                       "fixed_key_exact_nn_agreement": float((exact == fprev).double().mean())}
     # Alg. 1 from its own start: a random field (Uniform over R), then the loop
-    # on the next frames; the paper reports convergence "after very few frames"
+    # on the next frames; Sec. 3.4 reports that a random start converges within a few frames
     conv = {"ms": [], "E_anchor_loop": [], "E_exact_nn": [], "exact_nn_agreement": []}
     rf = torch.empty_like(prev)
     riann.riann_random_field(H, W, idx.n, 0xBADC0DE, 0, rf, stream=stream)
