@@ -364,13 +364,15 @@ int riann_session_copy_outputs(riann_session_t s, riann_stream_t stream, int32_t
 
 /* ------------------------------------------------------------------------
  * Batched form: the frames of many sessions (of one index, of any sizes)
- * answered by one persistent ring-intersection launch whose CTAs take query
- * tiles of all frames from a device work counter, followed by one brute-force
- * pass over the union of the queries it routed.  The launch sequence is
- * captured once as a CUDA graph and replayed every call (unless created with
- * RIANN_BATCH_NO_GRAPH); frame and field pointers travel in a pinned
- * descriptor table the graph copies in.  Results are identical to running
- * each session alone.
+ * answered by one ring-intersection launch per frame, spread over four
+ * streams forked from and joined back to the caller's, followed by one
+ * brute-force pass over the union of the queries they routed.  The launch
+ * sequence is captured once as a CUDA graph and replayed every call (unless
+ * created with RIANN_BATCH_NO_GRAPH); frame and field pointers travel in a
+ * pinned descriptor table the graph copies in, and the graph is re-captured
+ * only when a slot receives a larger frame than it has held (or the
+ * parameters or tuning change).  Results are identical to running each
+ * session alone.
  * ------------------------------------------------------------------------ */
 typedef struct riann_batch_s* riann_batch_t;
 #define RIANN_BATCH_NO_GRAPH 0x1
