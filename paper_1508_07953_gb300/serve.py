@@ -1,4 +1,4 @@
-"""Real-time driver of the served form (continuous batching of video streams).
+"""Real-time front end of the served form (continuous batching of video streams).
 
 Streams arrive as a Poisson process, live for a uniformly drawn time and send
 frames at a fixed rate; each frame's arrival time is its nominal capture time.
