@@ -215,8 +215,8 @@ int riann_knn_frame(riann_index_t idx, const riann_params* p, riann_stream_t str
  *                 0 .. *out_count - 1 receive the representatives
  *   d_out_assign  device int32 [n], cluster of each input patch (nullable)
  *   out_count     host: number of clusters
- * Synchronous: allocates its scratch (4 x 4 + 1 bytes per patch plus two
- * node lists), builds the tree level by level (one launch and one small
+ * Synchronous: takes its scratch from the stream-ordered memory pool (4 x 4 +
+ * 1 bytes per patch plus two node lists), builds the tree level by level (one launch and one small
  * device-to-host read per level) and returns when the outputs are written.
  */
 int riann_cluster_references(riann_stream_t stream, const uint8_t* d_patches, int32_t n, int32_t channels,

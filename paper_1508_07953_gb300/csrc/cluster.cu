@@ -25,18 +25,18 @@
 namespace riann {
 namespace {
 
-constexpr int kSplitThreads = 256;
-
-template <int D>
-__global__ void __launch_bounds__(kSplitThreads) k_split(const uint8_t* __restrict__ X, int32_t* perm,
+// threads per node: 1024 while a level has fewer nodes than two per SM (the
+// top levels, where a few large nodes would leave the GPU idle), else 256
+template <int D, int T>
+__global__ void __launch_bounds__(T) k_split(const uint8_t* __restrict__ X, int32_t* perm,
                                                          int32_t* tmp, uint8_t* leaf_start,
                                                          const int2* __restrict__ segs_in, int2* segs_out,
                                                          uint32_t* n_out, int leaf) {
-  constexpr int G = kSplitThreads / D;   // threads per coordinate in the sums
+  constexpr int G = T / D;   // threads per coordinate in the sums
   __shared__ unsigned long long s1[D], s2[D];
   __shared__ uint32_t hist[256];
   __shared__ int s_dim, s_m, s_strict, s_nl;
-  __shared__ uint32_t s_wl[kSplitThreads / 32], s_wr[kSplitThreads / 32];
+  __shared__ uint32_t s_wl[T / 32], s_wr[T / 32];
   const int2 sg = segs_in[blockIdx.x];
   const int b = sg.x, e = sg.y, cnt = e - b;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kSplitThreads) k_split(const uint8_t* __restri
     __syncthreads();
     int offl = 0, offr = 0, totl = 0, totr = 0;
 #pragma unroll
-    for (int w = 0; w < kSplitThreads / 32; ++w) {
+    for (int w = 0; w < T / 32; ++w) {
       const int a = (int)s_wl[w], c = (int)s_wr[w];
       if (w < warp) {
         offl += a;
@@ -226,7 +226,8 @@ cudaError_t run_tree(const uint8_t* X, int n, int leaf, int32_t* perm, int32_t* 
   while (e == cudaSuccess && nseg > 0) {
     e = cudaMemsetAsync(cnts, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) break;
-    k_split<D><<<nseg, kSplitThreads, 0, s>>>(X, perm, tmp, leaf_start, in, out, cnts, leaf);
+    if (nseg < 2u * (uint32_t)sm_count()) k_split<D, 1024><<<nseg, 1024, 0, s>>>(X, perm, tmp, leaf_start, in, out, cnts, leaf);
+    else k_split<D, 256><<<nseg, 256, 0, s>>>(X, perm, tmp, leaf_start, in, out, cnts, leaf);
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&nseg, cnts, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -250,31 +251,30 @@ cudaError_t run_tree(const uint8_t* X, int n, int leaf, int32_t* perm, int32_t* 
 
 cudaError_t cluster_references(const uint8_t* X, int n, int C, int leaf, uint8_t* reps, int32_t* assign,
                                int32_t* out_count, cudaStream_t s) {
+  // scratch from the stream-ordered pool: repeated calls reuse it without a
+  // device-wide allocation or free
   int32_t *perm = nullptr, *tmp = nullptr, *leaf_begin = nullptr;
   uint8_t* leaf_start = nullptr;
   int2 *segs0 = nullptr, *segs1 = nullptr;
   uint32_t* cnts = nullptr;
-  cudaError_t e = cudaMalloc(&perm, sizeof(int32_t) * (size_t)n);
-  if (e == cudaSuccess) e = cudaMalloc(&tmp, sizeof(int32_t) * (size_t)n);
-  if (e == cudaSuccess) e = cudaMalloc(&leaf_begin, sizeof(int32_t) * (size_t)n);
-  if (e == cudaSuccess) e = cudaMalloc(&leaf_start, (size_t)n);
-  if (e == cudaSuccess) e = cudaMalloc(&segs0, sizeof(int2) * (size_t)n);
-  if (e == cudaSuccess) e = cudaMalloc(&segs1, sizeof(int2) * (size_t)n);
-  if (e == cudaSuccess) e = cudaMalloc(&cnts, sizeof(uint32_t) * 2);
+  cudaError_t e = cudaMallocAsync((void**)&perm, sizeof(int32_t) * (size_t)n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&tmp, sizeof(int32_t) * (size_t)n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&leaf_begin, sizeof(int32_t) * (size_t)n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&leaf_start, (size_t)n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&segs0, sizeof(int2) * (size_t)n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&segs1, sizeof(int2) * (size_t)n, s);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&cnts, sizeof(uint32_t) * 2, s);
   if (e == cudaSuccess)
     e = C == 1 ? run_tree<64>(X, n, leaf, perm, tmp, leaf_start, segs0, segs1, cnts, leaf_begin, reps, assign,
                               out_count, s)
                : run_tree<192>(X, n, leaf, perm, tmp, leaf_start, segs0, segs1, cnts, leaf_begin, reps, assign,
                                out_count, s);
-  cudaStreamSynchronize(s);
-  cudaFree(perm);
-  cudaFree(tmp);
-  cudaFree(leaf_begin);
-  cudaFree(leaf_start);
-  cudaFree(segs0);
-  cudaFree(segs1);
-  cudaFree(cnts);
-  return e;
+  if (e != cudaSuccess) cudaGetLastError();
+  for (void* p : {(void*)perm, (void*)tmp, (void*)leaf_begin, (void*)leaf_start, (void*)segs0, (void*)segs1,
+                  (void*)cnts})
+    if (p) cudaFreeAsync(p, s);
+  const cudaError_t e2 = cudaStreamSynchronize(s);
+  return e != cudaSuccess ? e : e2;
 }
 
 }  // namespace riann
