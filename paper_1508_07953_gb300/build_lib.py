@@ -62,7 +62,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     objs = [os.path.join(OBJ, s.replace(".cu", ".o")) for s in SOURCES]
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        run([cc, *ARCH, "-shared", "-o", tmp, *objs])
+        run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "reconstruct.cuh"
 #include "anchor.cuh"
+#include "trace.h"
 
 namespace riann {
 
@@ -129,6 +130,7 @@ DenseArgs dense_args(const Index& ix, unsigned long long* stats) {
 cudaError_t run_frame(Index& ix, Workspace& ws, const riann_params* p, cudaStream_t s, const FrameItem& it,
                       unsigned long long* stats, int k = 0, int32_t* knn_idx = nullptr,
                       uint32_t* knn_dist = nullptr) {
+  NvtxRange range(k ? "riann k-NN frame" : "riann frame");
   cudaError_t e = cudaSuccess;
   if (stats) e = cudaMemsetAsync(stats, 0, sizeof(unsigned long long) * kStats, s);
   if (e != cudaSuccess) return e;
@@ -603,6 +605,7 @@ int riann_anchor_frame(riann_full_t f, const riann_anchor_params* p, riann_strea
                        const uint8_t* d_frame, int32_t H, int32_t W, const int32_t* d_prev,
                        int32_t* d_out_annf, uint32_t* d_out_dist, uint32_t* d_out_count,
                        uint32_t* d_out_rings) {
+  NvtxRange range("riann anchor-loop frame");
   if (!f || !p || !d_frame || !d_out_annf || !frame_ok(H, W) || p->alpha_den < 1 || p->alpha_den > 8 ||
       p->alpha_num < 0 || p->alpha_num > 8 * p->alpha_den || p->L < 1 || p->max_rings < 0 || p->max_rings > 4096 ||
       (const void*)d_prev == (const void*)d_out_annf)
@@ -997,6 +1000,7 @@ void riann_batch_destroy(riann_batch_t b) {
 int riann_batch_run(riann_batch_t b, const riann_params* p, riann_stream_t stream, riann_session_t* sessions,
                     const uint8_t* const* d_frames, int32_t n) {
   if (!b || !params_ok(p) || !sessions || !d_frames || n < 1 || n > b->max_items) return RIANN_ERR_INVALID_ARG;
+  NvtxRange range("riann batched step");
   std::lock_guard<std::mutex> lock(b->mu);
   Index& ix = *b->ix;
   cudaStream_t cs = reinterpret_cast<cudaStream_t>(stream);

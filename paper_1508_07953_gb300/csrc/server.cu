@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "trace.h"
 
 namespace {
 
@@ -283,6 +284,7 @@ int riann_server_submit(riann_server_t s, int32_t id, const uint8_t* h_frame, in
 
 int riann_server_step(riann_server_t s, riann_stream_t stream, int32_t wait, int32_t* launched) {
   if (!s) return RIANN_ERR_INVALID_ARG;
+  riann::NvtxRange range("riann served tick");
   std::lock_guard<std::mutex> lock(s->mu);
   if (launched) *launched = 0;
   if (!finish_tick(s, wait != 0)) return RIANN_OK;   // still running: nothing started

@@ -245,3 +245,31 @@ def test_1080p_across_scene_cut_sampled(rt):
     n = synth.WORKLOADS["1080p"].n
     # the cut frame sends far more queries to brute force (count = n) than a steady frame
     assert (g[2][2] == n).mean() > 0.25 and (g[2][2] == n).mean() > 3 * (g[1][2] == n).mean()
+
+
+def test_candidates_grow_with_temporal_change(rt):
+    # Fig. 5 (diagnostic, not parity): regions that move faster give larger
+    # rings, so more candidates per query and more queries routed to brute force
+    w = synth.WORKLOADS["720p_rgb"]
+    R = synth.workload_reference(w)
+    KP = synth.workload_keypoints(w, R)
+    video = synth.Video(w.video)
+    frames = [video.frame(t) for t in (1, 2, 3)]
+    g = gpu_chain(rt, R, KP, frames, make_params(rt, len(R)))
+    count = g[2][2].astype(np.int64)                       # frame 3
+    _, vel, _ = video._scene(0)
+    reg = w.video.region
+    Hq, Wq = count.shape
+    speed = np.hypot(vel[..., 0], vel[..., 1])
+    sp = speed[np.arange(Hq)[:, None] // reg, np.arange(Wq)[None, :] // reg]
+    ring = count < len(R)
+    means, routed = [], []
+    for s in sorted(set(np.round(w.video.speeds, 3))):
+        m = np.isclose(sp, s)
+        if m.sum() < 1000:
+            continue
+        means.append(count[m & ring].mean())
+        routed.append(1.0 - ring[m].mean())
+    assert len(means) >= 3
+    assert means[-1] > 2 * means[0] and routed[-1] > routed[0]
+    assert all(b >= a * 0.9 for a, b in zip(means, means[1:]))   # rising, up to noise
