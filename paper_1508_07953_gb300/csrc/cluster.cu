@@ -27,11 +27,48 @@ namespace {
 
 // threads per node: 1024 while a level has fewer nodes than two per SM (the
 // top levels, where a few large nodes would leave the GPU idle), else 256
+// Coordinate sums of the few large nodes of a top level, spread over many
+// CTAs: CTA (node, c) sums slice c of the node into 64-bit atomics.
+template <int D>
+__global__ void __launch_bounds__(256) k_node_sums(const uint8_t* __restrict__ X, const int32_t* __restrict__ perm,
+                                                   const int2* __restrict__ segs, int leaf,
+                                                   unsigned long long* __restrict__ gsum) {
+  constexpr int G = 256 / D;
+  __shared__ unsigned long long s1[D], s2[D];
+  const int2 sg = segs[blockIdx.x];
+  const int b = sg.x, cnt = sg.y - sg.x, tid = threadIdx.x;
+  if (cnt <= leaf) return;   // k_split makes it a leaf without the sums
+  const int per = (cnt + gridDim.y - 1) / gridDim.y;
+  const int lo = blockIdx.y * per, hi = min(cnt, lo + per);
+  if (lo >= hi) return;
+  for (int i = tid; i < D; i += blockDim.x) s1[i] = s2[i] = 0ull;
+  __syncthreads();
+  if (tid < G * D) {
+    const int g = tid / D, d = tid % D;
+    unsigned long long a1 = 0, a2 = 0;
+    for (int i = lo + g; i < hi; i += G) {
+      const unsigned x = __ldg(X + (int64_t)perm[b + i] * D + d);
+      a1 += x;
+      a2 += x * x;
+    }
+    atomicAdd(&s1[d], a1);
+    atomicAdd(&s2[d], a2);
+  }
+  __syncthreads();
+  unsigned long long* out = gsum + (size_t)blockIdx.x * 2 * D;
+  for (int i = tid; i < D; i += blockDim.x) {
+    atomicAdd(out + i, s1[i]);
+    atomicAdd(out + D + i, s2[i]);
+  }
+}
+
+// gsum (nullable): the node's coordinate sums, already computed by k_node_sums
 template <int D, int T>
 __global__ void __launch_bounds__(T) k_split(const uint8_t* __restrict__ X, int32_t* perm,
                                                          int32_t* tmp, uint8_t* leaf_start,
                                                          const int2* __restrict__ segs_in, int2* segs_out,
-                                                         uint32_t* n_out, int leaf) {
+                                                         uint32_t* n_out, int leaf,
+                                                         const unsigned long long* __restrict__ gsum) {
   constexpr int G = T / D;   // threads per coordinate in the sums
   __shared__ unsigned long long s1[D], s2[D];
   __shared__ uint32_t hist[256];
@@ -44,19 +81,28 @@ __global__ void __launch_bounds__(T) k_split(const uint8_t* __restrict__ X, int3
     if (tid == 0) leaf_start[b] = 1;
     return;
   }
-  for (int i = tid; i < D; i += blockDim.x) s1[i] = s2[i] = 0ull;
   for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0u;
-  __syncthreads();
-  if (tid < G * D) {
-    const int g = tid / D, d = tid % D;
-    unsigned long long a1 = 0, a2 = 0;
-    for (int i = g; i < cnt; i += G) {
-      const unsigned x = __ldg(X + (int64_t)perm[b + i] * D + d);
-      a1 += x;
-      a2 += x * x;
+  if (gsum) {
+    const unsigned long long* src = gsum + (size_t)blockIdx.x * 2 * D;
+    for (int i = tid; i < D; i += blockDim.x) {
+      s1[i] = src[i];
+      s2[i] = src[D + i];
     }
-    atomicAdd(&s1[d], a1);
-    atomicAdd(&s2[d], a2);
+    __syncthreads();
+  } else {
+    for (int i = tid; i < D; i += blockDim.x) s1[i] = s2[i] = 0ull;
+    __syncthreads();
+    if (tid < G * D) {
+      const int g = tid / D, d = tid % D;
+      unsigned long long a1 = 0, a2 = 0;
+      for (int i = g; i < cnt; i += G) {
+        const unsigned x = __ldg(X + (int64_t)perm[b + i] * D + d);
+        a1 += x;
+        a2 += x * x;
+      }
+      atomicAdd(&s1[d], a1);
+      atomicAdd(&s2[d], a2);
+    }
   }
   __syncthreads();
   if (warp == 0) {
@@ -214,7 +260,7 @@ __global__ void k_iota(int32_t* p, int n) {
 template <int D>
 cudaError_t run_tree(const uint8_t* X, int n, int leaf, int32_t* perm, int32_t* tmp, uint8_t* leaf_start,
                      int2* segs0, int2* segs1, uint32_t* cnts, int32_t* leaf_begin, uint8_t* reps, int32_t* assign,
-                     int32_t* out_count, cudaStream_t s) {
+                     int32_t* out_count, unsigned long long* gsum, cudaStream_t s) {
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)sm_count() * 8);
   k_iota<<<blocks, 256, 0, s>>>(perm, n);
   cudaError_t e = cudaMemsetAsync(leaf_start, 0, (size_t)n, s);
@@ -226,8 +272,17 @@ cudaError_t run_tree(const uint8_t* X, int n, int leaf, int32_t* perm, int32_t* 
   while (e == cudaSuccess && nseg > 0) {
     e = cudaMemsetAsync(cnts, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) break;
-    if (nseg < 2u * (uint32_t)sm_count()) k_split<D, 1024><<<nseg, 1024, 0, s>>>(X, perm, tmp, leaf_start, in, out, cnts, leaf);
-    else k_split<D, 256><<<nseg, 256, 0, s>>>(X, perm, tmp, leaf_start, in, out, cnts, leaf);
+    const uint32_t few = 2u * (uint32_t)sm_count();   // gsum holds this many nodes
+    if (nseg < few) {
+      // top levels: the sums over many CTAs, then one 1024-thread CTA per node
+      e = cudaMemsetAsync(gsum, 0, sizeof(unsigned long long) * 2 * D * nseg, s);
+      if (e != cudaSuccess) break;
+      const unsigned slices = (4u * (uint32_t)sm_count() + nseg - 1) / nseg;
+      k_node_sums<D><<<dim3(nseg, slices), 256, 0, s>>>(X, perm, in, leaf, gsum);
+      k_split<D, 1024><<<nseg, 1024, 0, s>>>(X, perm, tmp, leaf_start, in, out, cnts, leaf, gsum);
+    } else {
+      k_split<D, 256><<<nseg, 256, 0, s>>>(X, perm, tmp, leaf_start, in, out, cnts, leaf, nullptr);
+    }
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpyAsync(&nseg, cnts, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -257,6 +312,7 @@ cudaError_t cluster_references(const uint8_t* X, int n, int C, int leaf, uint8_t
   uint8_t* leaf_start = nullptr;
   int2 *segs0 = nullptr, *segs1 = nullptr;
   uint32_t* cnts = nullptr;
+  unsigned long long* gsum = nullptr;   // coordinate sums of a top level's nodes
   cudaError_t e = cudaMallocAsync((void**)&perm, sizeof(int32_t) * (size_t)n, s);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&tmp, sizeof(int32_t) * (size_t)n, s);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&leaf_begin, sizeof(int32_t) * (size_t)n, s);
@@ -265,13 +321,15 @@ cudaError_t cluster_references(const uint8_t* X, int n, int C, int leaf, uint8_t
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&segs1, sizeof(int2) * (size_t)n, s);
   if (e == cudaSuccess) e = cudaMallocAsync((void**)&cnts, sizeof(uint32_t) * 2, s);
   if (e == cudaSuccess)
+    e = cudaMallocAsync((void**)&gsum, sizeof(unsigned long long) * 2 * 192 * 2 * (size_t)sm_count(), s);
+  if (e == cudaSuccess)
     e = C == 1 ? run_tree<64>(X, n, leaf, perm, tmp, leaf_start, segs0, segs1, cnts, leaf_begin, reps, assign,
-                              out_count, s)
+                              out_count, gsum, s)
                : run_tree<192>(X, n, leaf, perm, tmp, leaf_start, segs0, segs1, cnts, leaf_begin, reps, assign,
-                               out_count, s);
+                               out_count, gsum, s);
   if (e != cudaSuccess) cudaGetLastError();
   for (void* p : {(void*)perm, (void*)tmp, (void*)leaf_begin, (void*)leaf_start, (void*)segs0, (void*)segs1,
-                  (void*)cnts})
+                  (void*)cnts, (void*)gsum})
     if (p) cudaFreeAsync(p, s);
   const cudaError_t e2 = cudaStreamSynchronize(s);
   return e != cudaSuccess ? e : e2;
