@@ -16,8 +16,10 @@
 // (the values are bytes: no sort), and partitions its range stably with warp
 // ballots into a scratch copy; the children go to the next level's node list.
 // A leaf marks its first position.  Leaves are then enumerated in position
-// order (k_leaf_scan), and k_reps takes one warp per leaf: lower medians by a
-// binary search over the 256 byte values with ballot counts.
+// order (block counts, a scan, ordered writes), and k_reps takes one warp per
+// leaf: lower medians by ranking each coordinate's values across the lanes
+// (small leaves) or by a binary search over the 256 byte values with ballot
+// counts.
 #include <algorithm>
 
 #include "common.cuh"
@@ -197,31 +199,63 @@ __global__ void __launch_bounds__(T) k_split(const uint8_t* __restrict__ X, int3
   }
 }
 
-// Leaves in position order: leaf_begin[k] = first position of leaf k, *count = leaves.
-__global__ void __launch_bounds__(1024) k_leaf_scan(const uint8_t* __restrict__ leaf_start, int n,
-                                                    int32_t* leaf_begin, uint32_t* count) {
-  __shared__ uint32_t s_w[32];
+// Leaves in position order: leaf_begin[k] = first position of leaf k, *count
+// = leaves.  Three steps over blocks of 1024 positions: each block counts its
+// leaf starts, one CTA scans the block counts, each block writes its starts
+// at its offset (ballots and a shared scan keep them in order).
+constexpr int kScanBlock = 1024;
+
+__global__ void __launch_bounds__(kScanBlock) k_leaf_count(const uint8_t* __restrict__ leaf_start, int n,
+                                                           uint32_t* __restrict__ block_count) {
+  const int i = blockIdx.x * kScanBlock + threadIdx.x;
+  const int c = __syncthreads_count(i < n && leaf_start[i]);
+  if (threadIdx.x == 0) block_count[blockIdx.x] = (uint32_t)c;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_leaf_offsets(uint32_t* block_count, int nb, uint32_t* count) {
+  __shared__ uint32_t s_w[kScanBlock / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int base = 0;
-  for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+  uint32_t base = 0;
+  for (int c0 = 0; c0 < nb; c0 += kScanBlock) {
     const int i = c0 + tid;
-    const bool f = i < n && leaf_start[i];
-    const unsigned bal = __ballot_sync(0xffffffffu, f);
-    if (lane == 0) s_w[warp] = __popc(bal);
-    __syncthreads();
-    int off = 0, tot = 0;
-    for (int w = 0; w < 32; ++w) {
-      if (w < warp) off += (int)s_w[w];
-      tot += (int)s_w[w];
+    const uint32_t v = i < nb ? block_count[i] : 0u;
+    uint32_t x = v;   // inclusive warp scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    if (f) leaf_begin[base + off + __popc(bal & ((1u << lane) - 1u))] = i;
+    if (lane == 31) s_w[warp] = x;
+    __syncthreads();
+    uint32_t off = 0, tot = 0;
+    for (int w = 0; w < kScanBlock / 32; ++w) {
+      if (w < warp) off += s_w[w];
+      tot += s_w[w];
+    }
+    if (i < nb) block_count[i] = base + off + x - v;   // exclusive offset, in place
     base += tot;
     __syncthreads();
   }
-  if (tid == 0) *count = (uint32_t)base;
+  if (tid == 0) *count = base;
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_leaf_write(const uint8_t* __restrict__ leaf_start, int n,
+                                                           const uint32_t* __restrict__ block_off,
+                                                           int32_t* __restrict__ leaf_begin) {
+  __shared__ uint32_t s_w[kScanBlock / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i = blockIdx.x * kScanBlock + tid;
+  const bool f = i < n && leaf_start[i];
+  const unsigned bal = __ballot_sync(0xffffffffu, f);
+  if (lane == 0) s_w[warp] = __popc(bal);
+  __syncthreads();
+  uint32_t off = block_off[blockIdx.x];
+  for (int w = 0; w < warp; ++w) off += s_w[w];
+  if (f) leaf_begin[off + __popc(bal & ((1u << lane) - 1u))] = i;
 }
 
 // One warp per leaf: its members' cluster id and its per-coordinate lower median.
+constexpr int kSmallLeaf = 8;   // leaves up to this size rank their values per coordinate
 template <int D>
 __global__ void __launch_bounds__(256) k_reps(const uint8_t* __restrict__ X, const int32_t* __restrict__ perm,
                                               const int32_t* __restrict__ leaf_begin, const uint32_t* count,
@@ -234,6 +268,29 @@ __global__ void __launch_bounds__(256) k_reps(const uint8_t* __restrict__ X, con
   if (assign)
     for (int i = lane; i < cnt; i += 32) assign[perm[start + i]] = k;
   const int r = (cnt - 1) / 2;
+  if (cnt <= kSmallLeaf) {
+    // small leaf: lanes on coordinates; each lane ranks the leaf's values of
+    // its coordinates (value, then member order) and keeps the one of rank r
+    int32_t pm[kSmallLeaf];
+#pragma unroll
+    for (int j = 0; j < kSmallLeaf; ++j) pm[j] = j < cnt ? perm[start + j] : 0;
+    for (int d = lane; d < D; d += 32) {
+      int v[kSmallLeaf];
+#pragma unroll
+      for (int j = 0; j < kSmallLeaf; ++j) v[j] = j < cnt ? (int)__ldg(X + (int64_t)pm[j] * D + d) : 0;
+      int med = 0;
+#pragma unroll
+      for (int j = 0; j < kSmallLeaf; ++j) {
+        int rank = 0;
+#pragma unroll
+        for (int i = 0; i < kSmallLeaf; ++i)
+          rank += (i < cnt) && (v[i] < v[j] || (v[i] == v[j] && i < j));
+        if (j < cnt && rank == r) med = v[j];
+      }
+      reps[(int64_t)k * D + d] = (uint8_t)med;
+    }
+    return;
+  }
   const int32_t p0 = lane < cnt ? perm[start + lane] : 0;   // the first 32 members, kept in a register
   for (int d = 0; d < D; ++d) {
     const int x0 = lane < cnt ? (int)__ldg(X + (int64_t)p0 * D + d) : 256;
@@ -289,7 +346,11 @@ cudaError_t run_tree(const uint8_t* X, int n, int leaf, int32_t* perm, int32_t* 
     std::swap(in, out);
   }
   if (e != cudaSuccess) return e;
-  k_leaf_scan<<<1, 1024, 0, s>>>(leaf_start, n, leaf_begin, cnts + 1);
+  const int nb = (n + kScanBlock - 1) / kScanBlock;
+  uint32_t* block_count = reinterpret_cast<uint32_t*>(segs0);   // the node lists are free now
+  k_leaf_count<<<nb, kScanBlock, 0, s>>>(leaf_start, n, block_count);
+  k_leaf_offsets<<<1, kScanBlock, 0, s>>>(block_count, nb, cnts + 1);
+  k_leaf_write<<<nb, kScanBlock, 0, s>>>(leaf_start, n, block_count, leaf_begin);
   uint32_t L = 0;
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&L, cnts + 1, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
