@@ -156,3 +156,21 @@ def test_bad_prev_sets_status(rt):
     mask[1, 1] = False
     assert np.array_equal(a[mask], oa[mask])
     idx.close()
+
+
+@pytest.mark.parametrize("alpha,limit", [((0, 1), -1), ((1, 4), -1), ((1, 1), 30)])
+def test_zero_patches_and_alpha_zero(rt, alpha, limit):
+    # all-zero query patches and references (a zero patch stays zero), and
+    # alpha = 0, where a ring holds only the references at exactly B
+    R, KP, frame, prev = synth.random_case(832, 500, 12, 1, 30, 40)
+    R[:3] = 0
+    R[100:140] = R[:40]                         # duplicates: ties by index
+    frame[4:20, 6:22] = 0                       # a block of zero queries
+    prev[5:9, 7:11] = 1                         # their previous match: a zero reference
+    idx = rt.riann_build_unit_index(_dev(R), _dev(KP))
+    g = rt.annf(idx, _dev(frame), _dev(prev), _params(rt, 500, alpha, limit))
+    assert rt.riann_status(idx) == 0
+    _cmp(g, oracle.riann_unit_frame(R, KP, frame, prev, alpha, limit), what=f"alpha {alpha}")
+    g0 = rt.annf(idx, _dev(frame), None)
+    _cmp(g0, oracle.riann_unit_frame(R, KP, frame, None), what="frame 0")
+    idx.close()
