@@ -591,10 +591,18 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         unsigned bits = 0;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const bool ok = j0 + u >= jlo && j0 + u < jhi && codes_pass(v0[u], lo0, hi0, any0) &&
+          const bool ok = codes_pass(v0[u], lo0, hi0, any0) &&
                           (ns1 < 2 || codes_pass(v1[u], lo1, hi1, any1)) &&
                           (ns1 < 3 || codes_pass(v2[u], lo2, hi2, any2));
           bits |= (ok ? 1u : 0u) << u;
+        }
+        // only the first and the last chunk hold entries outside [jlo, jhi)
+        // (a warp-uniform test: the middle chunks skip the range check)
+        if (base < jlo || base + 128 > jhi) {
+          unsigned inr = 0;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) inr |= (j0 + u >= jlo && j0 + u < jhi ? 1u : 0u) << u;
+          bits &= inr;
         }
         // deeper stage 1 (depth 4..5): the next groups by estimated
         // selectivity, one 16-byte load per lane for its four entries, only
