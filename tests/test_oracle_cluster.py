@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
+from conftest import read_fixture
 
 
 def _members(assign, m):
@@ -92,3 +93,33 @@ def test_all_at_or_below_the_median_splits_strictly():
     reps, assign = oracle.cluster_references(X, 6)
     assert len(reps) == 2 and list(assign) == [1, 0, 1, 1, 0, 1, 1, 1]
     assert reps[0][0] == 3 and reps[1][0] == 9
+
+
+GOLDEN = ["cluster_constant_patches.txt", "cluster_strict_median.txt", "cluster_largest_variance.txt",
+          "cluster_tied_variance.txt", "cluster_variance_not_mean.txt"]
+
+
+def _golden_patches(fx, key):
+    """[m][64] uint8 patches of a fixture: constant values, or `fill` with the
+    listed coordinates set per patch."""
+    if "coords" not in fx:
+        return np.stack([np.full(64, int(v), np.uint8) for v in fx[key].split()])
+    coords = [int(c) for c in fx["coords"].split()]
+    out = []
+    for t in fx[key].split():
+        p = np.full(64, int(fx["fill"]), np.uint8)
+        p[coords] = [int(v) for v in t.split(",")]
+        out.append(p)
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("name", GOLDEN)
+def test_golden_fixture(name):
+    """Hand-worked trees (tests/golden/cluster_*.txt)."""
+    fx = read_fixture(name)
+    X = _golden_patches(fx, "values" if "values" in fx else "patches")
+    reps, assign = oracle.cluster_references(X.reshape(-1, 8, 8), int(fx["leaf"]))
+    want = _golden_patches(fx, "expect_reps")
+    assert reps.shape == (len(want), 8, 8)
+    assert np.array_equal(reps.reshape(len(want), 64), want)
+    assert assign.tolist() == [int(x) for x in fx["expect_assign"].split()]

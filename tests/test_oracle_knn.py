@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 import synth
+from conftest import read_fixture
 
 
 def np_sorted_lists(frame, R):
@@ -33,6 +34,31 @@ def cut(d_sorted, i_sorted, k):
     ids[..., :kk] = i_sorted[..., :kk]
     ds[..., :kk] = d_sorted[..., :kk]
     return ids, ds
+
+
+GOLDEN = ["knn_1d_two_keys.txt", "knn_1d_limit_bruteforce.txt", "knn_1d_limit_equal.txt",
+          "knn_1d_prev_kept.txt"]
+
+
+@pytest.mark.parametrize("name", GOLDEN)
+def test_golden_fixture(name):
+    """Hand-worked lists on constant gray patches (tests/golden/knn_*.txt)."""
+    fx = read_fixture(name)
+    assert int(fx["channels"]) == 1
+
+    def patches(s):
+        return np.stack([np.full((8, 8, 1), int(v), np.uint8) for v in s.split()])
+
+    R, KP = patches(fx["ref_values"]), patches(fx["key_values"])
+    frame = np.full((8, 8), int(fx["query_value"]), np.uint8)
+    prev = np.array([[int(fx["prev"])]], np.int32)
+    k = int(fx["k"])
+    alpha = tuple(int(x) for x in fx["alpha"].split())
+    knn, kd, count = oracle.riann_knn(oracle.Index(R, KP), frame, prev, k, alpha=alpha,
+                                      ring_limit=int(fx["ring_limit"]))
+    assert knn.ravel().tolist() == [int(x) for x in fx["expect_knn"].split()]
+    assert kd.ravel().tolist() == [int(x) for x in fx["expect_knn_dist"].split()]
+    assert count.ravel().tolist() == [int(fx["expect_count"])]
 
 
 @pytest.mark.parametrize("n,C,H,W,k", [(300, 1, 12, 20, 8), (5, 1, 9, 9, 8), (257, 3, 10, 13, 3), (1, 1, 8, 8, 2)])

@@ -120,6 +120,8 @@ def _pins_fail() -> bool:
                kpins.test_routing_at_the_limit_follows_the_argmin_step,
                lambda: kpins.test_matches_set_assembled_from_the_ring_predicate((1, 2)),
                kpins.test_lists_are_sorted_unique_and_padded,
+               *[lambda n=n: kpins.test_golden_fixture(n) for n in kpins.GOLDEN],
+               *[lambda n=n: cpins.test_golden_fixture(n) for n in cpins.GOLDEN],
                lambda: cpins.test_partition_sizes_and_medians(1000, 64, 16, 0),
                lambda: cpins.test_partition_sizes_and_medians(64, 64, 64, 2),
                cpins.test_few_patches_one_cluster, cpins.test_identical_patches_do_not_split,
