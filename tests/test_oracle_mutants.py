@@ -75,6 +75,11 @@ MUTANTS = {
     "unit_ring_tie_high": ("if (d < bd || (d == bd && r < bi)) { bd = d; bi = r; }\n      }\n      annf[i] = bi; if (dist) dist[i] = bd; if (count) count[i] = s_size;",
                            "if (d < bd || (d == bd && r > bi)) { bd = d; bi = r; }\n      }\n      annf[i] = bi; if (dist) dist[i] = bd; if (count) count[i] = s_size;"),
     "unit_brute_tie_high": ("if (d < *bd) { *bd = d; *bi = r; }", "if (d <= *bd) { *bd = d; *bi = r; }"),
+    "unit_ring_strict_edge": ("return fabsf(A - B) <= T;", "return fabsf(A - B) < T;"),
+    "unit_zero_patch_unguarded": ("  if (s == 0) {\n    for (int32_t i = 0; i < D; ++i) out[i] = 0.f;",
+                                  "  if (0) {\n    for (int32_t i = 0; i < D; ++i) out[i] = 0.f;"),
+    "unit_routing_off_by_one": ("if (ring_limit >= 0 && ns > (uint32_t)ring_limit) {\n        unit_brute_force",
+                                "if (ring_limit >= 0 && ns >= (uint32_t)ring_limit) {\n        unit_brute_force"),
     "cluster_right_first": ("stack[2 * top] = b + nl; stack[2 * top + 1] = e; ++top;     /* right, processed after left */\n    stack[2 * top] = b; stack[2 * top + 1] = b + nl; ++top;",
                             "stack[2 * top] = b; stack[2 * top + 1] = b + nl; ++top;\n    stack[2 * top] = b + nl; stack[2 * top + 1] = e; ++top;"),
 }
@@ -132,7 +137,9 @@ def _pins_fail() -> bool:
                upins.test_ring_predicate_on_exact_values,
                lambda: upins.test_scale_invariance_bit_exact((1, 4), -1),
                lambda: upins.test_frame0_is_float_brute_force(1), upins.test_wide_rings_reduce_to_brute_force,
-               upins.test_alpha_one_is_near_exact_nn]
+               upins.test_alpha_one_is_near_exact_nn,
+               *[lambda c=c: upins.test_golden_16_pixel_sets(c)
+                 for c in ("limit_-1", "limit_5", "limit_6", "zero_query_limit_-1")]]
     for c in checks:
         try:
             c()

@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 import synth
+from conftest import read_fixture
 
 
 def f64_unit(X):
@@ -120,3 +121,38 @@ def test_alpha_one_is_near_exact_nn():
     d64 = np.sqrt(((Qn[:, None, :] - Rn[None, :, :]) ** 2).sum(-1))
     got = d64[np.arange(len(Qn)), a.ravel()]
     assert (got - d64.min(1)).max() <= 1e-5                          # triangle inequality, up to rounding
+
+
+def _set_patch(spec):
+    """8x8x1 gray patch, 200 on the listed pixels (row-major; ranges inclusive), 0 elsewhere."""
+    p = np.zeros(64, np.uint8)
+    for part in spec.split(","):
+        lo, _, hi = part.strip().partition("-")
+        p[int(lo): int(hi or lo) + 1] = 200
+    return p.reshape(8, 8, 1)
+
+
+def _f32_sqrt(num, den):
+    # float64 sqrt then rounding to float32 is the correctly rounded float32
+    # sqrt (53 >= 2 * 24 + 2 bits; no double-rounding error for sqrt)
+    return np.float32(np.sqrt(np.float64(num) / np.float64(den)))
+
+
+@pytest.mark.parametrize("case", ["limit_-1", "limit_5", "limit_6", "zero_query_limit_-1"])
+def test_golden_16_pixel_sets(case):
+    """Hand-worked unit-length step on exactly representable patches
+    (tests/golden/unit_16_pixel_sets.txt)."""
+    fx = read_fixture("unit_16_pixel_sets.txt")
+    R = np.stack([_set_patch(s) for s in fx["refs"].split(";")])
+    KP = np.stack([_set_patch(s) for s in fx["keys"].split(";")])
+    zero = case.startswith("zero")
+    frame = np.zeros((8, 8, 1), np.uint8) if zero else _set_patch(fx["query"])
+    limit = int(case.rsplit("_", 1)[1])
+    prev = np.array([[int(fx["prev"])]], np.int32)
+    alpha = tuple(int(x) for x in fx["alpha"].split())
+    annf, dist, count = oracle.riann_unit_frame(R, KP, frame, prev, alpha=alpha, ring_limit=limit)
+    e_annf, e_d2, e_count = fx["expect_" + case].split()
+    num, _, den = e_d2.partition("/")
+    assert annf.ravel().tolist() == [int(e_annf)]
+    assert dist.ravel()[0].view(np.uint32) == _f32_sqrt(int(num), int(den or 1)).view(np.uint32)
+    assert count.ravel().tolist() == [int(e_count)]
