@@ -1,11 +1,12 @@
 """The hand-worked fixtures of tests/golden/ through the CUDA path.
 
 The same small cases that pin the oracle by hand (constant or 16-pixel
-patches whose ring sets, lists, trees and averages are derived in each
-file's header) run here through the C-ABI: ring steps (Sec. 3.2, Alg. 1),
-k-NN lists (Sec. 7), the unit-length variant (Sec. 3.4), the regression-tree
-clustering (Sec. 3.4), the random-anchor loop (Alg. 1) and the Sec. 4
-reconstruction.  Expected values come from the fixture files alone.
+patches and constant volumes, whose ring sets, lists, trees and averages
+are derived in each file's header) run here through the C-ABI: ring steps
+(Sec. 3.2, Alg. 1), k-NN lists (Sec. 7), the unit-length variant (Sec. 3.4),
+the regression-tree clustering (Sec. 3.4), 3-D spatio-temporal volumes
+(Sec. 1), the random-anchor loop (Alg. 1) and the Sec. 4 reconstruction.
+Expected values come from the fixture files alone.
 """
 import numpy as np
 import pytest
@@ -13,6 +14,7 @@ import pytest
 import test_oracle_cluster as cluster_pins
 import test_oracle_knn as knn_pins
 import test_oracle_pins as pins
+import test_oracle_spatiotemporal as st_pins
 import test_oracle_unit as unit_pins
 from conftest import read_fixture
 
@@ -142,4 +144,16 @@ def test_reconstruct_fixture(rt):
     rt.riann_reconstruct(idx, _dev(annf), _dev(frame), out, err2)
     assert (out.cpu().numpy()[:, :, 0] == np.array(d["expect_row"], np.uint8)[None]).all()
     assert err2.cpu().numpy().tolist() == d["expect_err2"]
+    idx.close()
+
+
+def test_spatiotemporal_fixture(rt):
+    frames, R, KP, prev, alpha, limit, fx = st_pins.golden_case()
+    st = rt.riann_stack_frames(*(_dev(f) for f in frames))
+    idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
+    for key, pv in (("expect_ring", _dev(prev)), ("expect_first_frame", None)):
+        a, d, c = rt.annf(idx, st, pv, _params(rt, len(R), alpha, limit))
+        got = [a.item(), d.cpu().numpy().view(np.uint32).item(), c.cpu().numpy().view(np.uint32).item()]
+        assert got == [int(x) for x in fx[key].split()], key
+    assert rt.riann_status(idx) == 0
     idx.close()

@@ -9,6 +9,7 @@ import numpy as np
 
 import oracle
 import synth
+from conftest import read_fixture
 
 
 def _frames(seed=3, H=20, W=27):
@@ -46,3 +47,27 @@ def test_reference_volumes_are_spatiotemporal_cuts():
     d_t = np.abs(R[..., 0].astype(int) - R[..., 1].astype(int)).mean()
     d_x = np.abs(R[:20, ..., 0].astype(int) - R[20:, ..., 0].astype(int)).mean()
     assert d_t < d_x
+
+
+def golden_case():
+    """(frames, R, KP, prev, alpha, ring_limit, fixture) of
+    tests/golden/spatiotemporal_constant_frames.txt."""
+    fx = read_fixture("spatiotemporal_constant_frames.txt")
+
+    def vols(s):
+        return np.stack([np.broadcast_to(np.array([int(v) for v in t.split(",")], np.uint8), (8, 8, 3))
+                         for t in s.split()])
+
+    frames = [np.full((8, 8), int(v), np.uint8) for v in fx["frame_values"].split()]
+    prev = np.array([[int(fx["prev"])]], np.int32)
+    alpha = tuple(int(x) for x in fx["alpha"].split())
+    return frames, vols(fx["ref_volumes"]), vols(fx["key_volumes"]), prev, alpha, int(fx["ring_limit"]), fx
+
+
+def test_golden_constant_frames():
+    frames, R, KP, prev, alpha, limit, fx = golden_case()
+    st = oracle.stack_frames(*frames)
+    idx = oracle.Index(R, KP)
+    for key, pv in (("expect_ring", prev), ("expect_first_frame", None)):
+        a, d, c, _ = oracle.riann_frame(idx, st, pv, alpha=alpha, ring_limit=limit, mode="definitional")
+        assert [int(a.ravel()[0]), int(d.ravel()[0]), int(c.ravel()[0])] == [int(x) for x in fx[key].split()]
