@@ -503,6 +503,28 @@ int riann_server_stream_counts(riann_server_t s, int32_t stream_id, int64_t* sub
 int riann_reconstruct(riann_index_t idx, riann_stream_t stream, const int32_t* d_annf, int32_t H, int32_t W,
                       const uint8_t* d_frame, uint8_t* d_out, unsigned long long* d_err2);
 
+/*
+ * Effects by patch replacement (Sec. 5: an effect or transformation -- e.g.
+ * denoising, colourisation, artistic styles -- is applied once to every
+ * reference patch at pre-processing time; at run time each query patch is
+ * replaced by the transformed version of its match and the overlaps are
+ * averaged).  The same reconstruction as riann_reconstruct, with the matched
+ * rows read from a caller-supplied table instead of the index's references:
+ *   d_payload  device uint8 [n][8][8][channels], row r = T(reference r)
+ *              (n of this index), 16-byte aligned; owned by the caller and
+ *              read during the call's kernel only
+ *   channels   1 or 3, independent of the index's channel count (a gray
+ *              index with an RGB payload colours a gray video)
+ *   d_out, d_frame  uint8 [H][W][channels]; d_annf, d_err2 as
+ *              riann_reconstruct (d_frame is then the target f_GT of the
+ *              effect, e.g. the clean or coloured frame)
+ * RIANN_ERR_INVALID_ARG for a null table, channels other than 1 or 3, a
+ * table address that is not 16-byte aligned, or the riann_reconstruct cases.
+ */
+int riann_reconstruct_payload(riann_index_t idx, riann_stream_t stream, const uint8_t* d_payload, int32_t channels,
+                              const int32_t* d_annf, int32_t H, int32_t W, const uint8_t* d_frame, uint8_t* d_out,
+                              unsigned long long* d_err2);
+
 /* ------------------------------------------------------------------------
  * Alg. 1 with random anchors, as the paper runs it (Sec. 3.2, 3.3, Alg. 1):
  * the candidate set starts as the ring around the previous match r_i

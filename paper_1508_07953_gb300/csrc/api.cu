@@ -663,6 +663,27 @@ int riann_reconstruct(riann_index_t idx, riann_stream_t stream, const int32_t* d
   return from_cuda(launch_reconstruct(a, idx->C, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+int riann_reconstruct_payload(riann_index_t idx, riann_stream_t stream, const uint8_t* d_payload, int32_t channels,
+                              const int32_t* d_annf, int32_t H, int32_t W, const uint8_t* d_frame, uint8_t* d_out,
+                              unsigned long long* d_err2) {
+  if (!idx || !d_payload || (channels != 1 && channels != 3) || !d_annf || !frame_ok(H, W) ||
+      (d_err2 && !d_frame))
+    return RIANN_ERR_INVALID_ARG;
+  // gray rows are read 16 bytes at a time
+  if (reinterpret_cast<uintptr_t>(d_payload) % 16 != 0) return RIANN_ERR_INVALID_ARG;
+  ReconArgs a;
+  a.annf = d_annf;
+  a.R = d_payload;
+  a.n = idx->n;
+  a.H = H;
+  a.W = W;
+  a.frame = d_frame;
+  a.out = d_out;
+  a.err2 = d_err2;
+  a.status = idx->status;
+  return from_cuda(launch_reconstruct(a, channels, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int riann_annf_frame(riann_index_t idx, const riann_params* p, riann_stream_t stream,
                      const uint8_t* d_frame, int32_t H, int32_t W, const int32_t* d_prev_annf,
                      int32_t* d_out_annf, uint32_t* d_out_dist, uint32_t* d_out_count) {

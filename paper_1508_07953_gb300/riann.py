@@ -139,6 +139,7 @@ _lib.riann_server_stream_counts.argtypes = [_P, _i32, ctypes.POINTER(_i64), ctyp
                                             ctypes.POINTER(_i64)]
 _lib.riann_status.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_uint32)]
 _lib.riann_reconstruct.argtypes = [_P, _P, _P, _i32, _i32, _P, _P, _P]
+_lib.riann_reconstruct_payload.argtypes = [_P, _P, _P, _i32, _P, _i32, _i32, _P, _P, _P]
 
 
 class riann_anchor_params(ctypes.Structure):
@@ -370,6 +371,29 @@ def riann_reconstruct(index: RiannIndex, annf: torch.Tensor, frame: Optional[tor
                                   _dev(frame, (torch.uint8,), "frame", n), _dev(out, (torch.uint8,), "out", n),
                                   _dev(err2, (torch.int64, torch.uint64), "err2", 2)),
            "riann_reconstruct")
+
+
+def riann_reconstruct_payload(index: RiannIndex, payload: torch.Tensor, annf: torch.Tensor,
+                              frame: Optional[torch.Tensor] = None, out: Optional[torch.Tensor] = None,
+                              err2: Optional[torch.Tensor] = None,
+                              stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Sec. 5 effects (asynchronous): the reconstruction of riann_reconstruct
+    with the matched rows taken from payload, uint8 [n][8][8][C'] on the
+    device (row r = T(reference r), C' in {1, 3}); frame and out have C'
+    channels."""
+    if annf.dim() != 2:
+        raise ValueError("annf must be [H-7][W-7]")
+    if payload.dim() != 4 or tuple(payload.shape[:3]) != (index.n, 8, 8) or payload.shape[3] not in (1, 3):
+        raise ValueError("payload must be uint8 [n][8][8][C'] with the index's n and C' in {1, 3}")
+    C = int(payload.shape[3])
+    H, W = annf.shape[0] + 7, annf.shape[1] + 7
+    n = H * W * C
+    _check(_lib.riann_reconstruct_payload(index.handle, _stream(stream),
+                                          _dev(payload, (torch.uint8,), "payload", index.n * 64 * C), C,
+                                          _dev(annf, _I32, "annf", (H - 7) * (W - 7)), H, W,
+                                          _dev(frame, (torch.uint8,), "frame", n), _dev(out, (torch.uint8,), "out", n),
+                                          _dev(err2, (torch.int64, torch.uint64), "err2", 2)),
+           "riann_reconstruct_payload")
 
 
 def reconstruct(index: RiannIndex, annf: torch.Tensor, frame: Optional[torch.Tensor] = None):
