@@ -12,6 +12,14 @@
  * special case; the membership test vs high-precision decimal square roots and
  * exact-boundary perfect squares; hand-worked constant-patch fixtures under
  * tests/golden/; definitional == indexed; key-point permutation invariance.
+ * The other functions have pins of their own (tests/test_oracle_*.py): k-NN
+ * lists vs sorted numpy brute force and hand-worked lists; the random-anchor
+ * loop vs Philox known-answer vectors, its special cases and an independent
+ * Python implementation; reconstruction vs a scatter formulation and closed
+ * forms; clustering vs numpy medians and hand-worked trees; the unit-length
+ * variant vs float64 and a hand-worked step on exactly representable
+ * patches; 3-D volumes vs plain slicing.  tests/test_oracle_mutants.py plants
+ * one mistake at a time in this file and checks that a pin fails.
  * The full alpha = 1/4 output has no external pin (the paper prints no values):
  * parity unpinned against the paper's own outputs.
  */
