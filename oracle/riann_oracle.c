@@ -651,7 +651,9 @@ void oracle_riann_indexed(const uint8_t* frame, int32_t H, int32_t W, int32_t C,
 
 /* Sec. 4 reconstruction, written as its definition: for every output pixel,
  * the query patches that cover it are those with top-left corner
- * y-7 <= py <= y and x-7 <= px <= x inside the query grid. */
+ * y-7 <= py <= y and x-7 <= px <= x inside the query grid.  R is the table
+ * the matched rows are read from: the references themselves (Sec. 4), or a
+ * transformed copy T(R) for an effect by patch replacement (Sec. 5). */
 void oracle_reconstruct(const uint8_t* R, int32_t n, int32_t C, const int32_t* annf, int32_t H, int32_t W,
                         const uint8_t* frame, uint8_t* out, unsigned long long* err2) {
   const int32_t Hq = H - 7, Wq = W - 7, D = 64 * C;
