@@ -51,6 +51,13 @@ MUTANTS = {
     "anchor_not_verified": ("if (Ba < bd || (Ba == bd && a < bi)) { bd = Ba; bi = a; }", ""),
     "anchor_draw_modulo": ("S[(int32_t)(((uint64_t)x[0] * (uint64_t)ns) >> 32)]", "S[(int32_t)(x[0] % (uint32_t)ns)]"),
     "anchor_loop_strict": ("while (ns >= L && (int32_t)t < max_rings)", "while (ns > L && (int32_t)t < max_rings)"),
+    # index tables (Sec. 3.3 pre-processing)
+    "tables_ties_high_index": ("if (u->id != v->id) return u->id < v->id ? -1 : 1;",
+                               "if (u->id != v->id) return u->id > v->id ? -1 : 1;"),
+    "tables_descending": ("if (u->a != v->a) return u->a < v->a ? -1 : 1;",
+                          "if (u->a != v->a) return u->a > v->a ? -1 : 1;"),
+    "key_distances_first_key_only": ("P[(int64_t)r * K + m] = sqdist(KP + (int64_t)m * D, R + (int64_t)r * D, D);",
+                                     "P[(int64_t)r * K + m] = sqdist(KP, R + (int64_t)r * D, D);"),
     "philox_multiplier": ("(uint64_t)0xD2511F53u * c0", "(uint64_t)0xD2511F55u * c0"),
     # k-NN output
     "knn_prev_dropped": ("if (all || in_s[r] || r == rp) {", "if (all || in_s[r]) {"),
@@ -93,7 +100,8 @@ def _pins_fail() -> bool:
             checks.append(lambda name=name, mode=mode: pins.test_golden_fixture(name, mode))
     checks += [pins.test_exact_nn_vs_numpy_random_with_ties, pins.test_exact_nn_vs_numpy_rgb,
                pins.test_ring_member_exact_equalities_by_construction, pins.test_alpha_zero_profile_match,
-               pins.test_frame0_is_brute_force]
+               pins.test_frame0_is_brute_force, lambda: pins.test_index_tables_vs_numpy(1),
+               lambda: pins.test_index_tables_vs_numpy(3)]
 
     def alpha_one():
         w = synth.WORKLOADS["tiny"]

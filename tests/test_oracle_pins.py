@@ -295,8 +295,26 @@ def test_count_bounded_by_smallest_ring(tiny):
 
 
 # --------------------------------------------------------------------------
-# the two oracle modes agree
+# the index tables; the two oracle modes agree
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("C", [1, 3])
+def test_index_tables_vs_numpy(C):
+    """Sec. 3.3 pre-processing: P = squared distances of every reference to
+    every key point, and per key the references sorted by (distance, index),
+    derived here with numpy (int64 sums, lexsort)."""
+    R, KP, _, _ = synth.random_case(40 + C, 301, 6, C, 8, 8)
+    R[200:260] = R[0:60]                       # equal distances: ties by index
+    idx = oracle.Index(R, KP)
+    Rm = R.reshape(len(R), -1).astype(np.int64)
+    Km = KP.reshape(len(KP), -1).astype(np.int64)
+    P = ((Rm[:, None, :] - Km[None, :, :]) ** 2).sum(-1)             # [n][K]
+    assert np.array_equal(idx.P.reshape(len(R), len(KP)).astype(np.int64), P)
+    for m in range(len(KP)):
+        order = np.lexsort((np.arange(len(R)), P[:, m]))
+        assert np.array_equal(idx.Tid[m], order)
+        assert np.array_equal(idx.TA[m].astype(np.int64), P[order, m])
+
+
 @pytest.mark.parametrize("C", [1, 3])
 @pytest.mark.parametrize("alpha", [(1, 4), (1, 2), (0, 1), (1, 1), (7, 8)])
 def test_definitional_equals_indexed_random(C, alpha):
