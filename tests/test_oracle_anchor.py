@@ -131,6 +131,20 @@ def test_no_loop_is_first_ring_argmin():
         assert d.reshape(-1)[qi] <= dq[ri]
 
 
+@pytest.mark.parametrize("alpha,L", [((1, 4), 20), ((1, 4), 2), ((1, 2), 10 ** 6)])
+def test_exact_previous_match_is_kept(alpha, L):
+    # Alg. 1 keeps r_i among the candidates of the final argmin, so a query
+    # whose previous match is already its exact NN (lowest index among equal
+    # distances) returns it, whatever the rings and anchors hold
+    w = synth.WORKLOADS["tiny"]
+    R = synth.workload_reference(w)[:900]
+    frame = synth.Video(w.video).frames(0, 2)[1][:36, :44]
+    fi = oracle.FullIndex(R)
+    ea, ed, _ = oracle.exact_nn(frame, R)
+    a, d, c, k = oracle.riann_anchor_frame(fi, frame, ea, alpha=alpha, L=L, seed=5, frame_id=1)
+    assert np.array_equal(a, ea) and np.array_equal(d, ed)
+
+
 def test_identical_references_stop_at_the_ring_cap():
     # every reference equals the query: each anchor's ring keeps all of S, so
     # only the cap ends the loop; the answer is the lowest index at distance 0

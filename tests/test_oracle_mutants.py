@@ -58,6 +58,11 @@ MUTANTS = {
                           "if (u->a != v->a) return u->a > v->a ? -1 : 1;"),
     "key_distances_first_key_only": ("P[(int64_t)r * K + m] = sqdist(KP + (int64_t)m * D, R + (int64_t)r * D, D);",
                                      "P[(int64_t)r * K + m] = sqdist(KP, R + (int64_t)r * D, D);"),
+    "full_tables_unsorted": ("    qsort(row, (size_t)n, sizeof(uint64_t), cmp_u64);\n", "\n"),
+    "anchor_lower_edge_dropped": ("  if (p < q) {\n    const uint64_t lo = (uint64_t)(q - p) * (uint64_t)(q - p);",
+                                  "  if (0) {\n    const uint64_t lo = (uint64_t)(q - p) * (uint64_t)(q - p);"),
+    "anchor_first_match_not_a_candidate": ("      uint32_t bd = Bi;\n", "      uint32_t bd = 0xffffffffu;\n"),
+    "random_field_counter_word3": ("{(uint32_t)q, 0u, frame_id, 1u}", "{(uint32_t)q, 0u, frame_id, 0u}"),
     "philox_multiplier": ("(uint64_t)0xD2511F53u * c0", "(uint64_t)0xD2511F55u * c0"),
     # k-NN output
     "knn_prev_dropped": ("if (all || in_s[r] || r == rp) {", "if (all || in_s[r]) {"),
@@ -121,7 +126,9 @@ def _pins_fail() -> bool:
                lambda: rpins.test_identity_field_reproduces_frame(23, 17, 3),
                lambda: rpins.test_matches_scatter_formulation(13, 29, 1, 50),
                rpins.test_constant_references_closed_form, rpins.test_golden_two_patches_round_half_up,
-               apins.test_philox_known_answers, apins.test_alpha_one_is_exact_nn, apins.test_no_loop_is_first_ring_argmin,
+               apins.test_philox_known_answers, apins.test_alpha_one_is_exact_nn,
+               apins.test_full_tables_are_sorted_distance_rows, apins.test_random_field_definition_and_range,
+               lambda: apins.test_exact_previous_match_is_kept((1, 4), 20), apins.test_no_loop_is_first_ring_argmin,
                apins.test_identical_references_stop_at_the_ring_cap, apins.test_golden_candidate_set_of_exactly_L,
                lambda: apins.test_matches_independent_implementation((1, 4), 3),
                lambda: apins.test_matches_independent_implementation((1, 2), 5),
