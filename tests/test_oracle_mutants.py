@@ -87,6 +87,7 @@ MUTANTS = {
     "unit_ring_tie_high": ("if (d < bd || (d == bd && r < bi)) { bd = d; bi = r; }\n      }\n      annf[i] = bi; if (dist) dist[i] = bd; if (count) count[i] = s_size;",
                            "if (d < bd || (d == bd && r > bi)) { bd = d; bi = r; }\n      }\n      annf[i] = bi; if (dist) dist[i] = bd; if (count) count[i] = s_size;"),
     "unit_brute_tie_high": ("if (d < *bd) { *bd = d; *bi = r; }", "if (d <= *bd) { *bd = d; *bi = r; }"),
+    "unit_prev_not_verified": ("      bi = rp;\n      bd = Cd;\n", "      bi = rp;\n      bd = INFINITY;\n"),
     "unit_ring_strict_edge": ("return fabsf(A - B) <= T;", "return fabsf(A - B) < T;"),
     "unit_zero_patch_unguarded": ("  if (s == 0) {\n    for (int32_t i = 0; i < D; ++i) out[i] = 0.f;",
                                   "  if (0) {\n    for (int32_t i = 0; i < D; ++i) out[i] = 0.f;"),
@@ -153,6 +154,7 @@ def _pins_fail() -> bool:
                lambda: upins.test_scale_invariance_bit_exact((1, 4), -1),
                lambda: upins.test_frame0_is_float_brute_force(1), upins.test_wide_rings_reduce_to_brute_force,
                upins.test_alpha_one_is_near_exact_nn,
+               lambda: upins.test_exact_previous_match_is_kept((1, 4), -1),
                *[lambda c=c: upins.test_golden_16_pixel_sets(c)
                  for c in ("limit_-1", "limit_5", "limit_6", "zero_query_limit_-1")]]
     for c in checks:

@@ -98,6 +98,19 @@ def test_frame0_is_float_brute_force(C):
     assert (count == 400).all()
 
 
+@pytest.mark.parametrize("alpha,limit", [((1, 4), -1), ((1, 2), 50), ((1, 16), -1)])
+def test_exact_previous_match_is_kept(alpha, limit):
+    # r_p is always a candidate of the final argmin (Alg. 1 verifies it), so a
+    # field that is already the float exact NN (lowest index among equal
+    # distances; pinned above) comes back unchanged, with the same distances
+    R, KP, frame, _ = synth.random_case(91, 500, 6, 1, 18, 25)
+    R[300:] = R[:200]
+    e_annf, e_dist, _ = oracle.riann_unit_frame(R, KP, frame, None)
+    annf, dist, _ = oracle.riann_unit_frame(R, KP, frame, e_annf, alpha=alpha, ring_limit=limit)
+    assert np.array_equal(annf, e_annf)
+    assert np.array_equal(dist.view(np.uint32), e_dist.view(np.uint32))
+
+
 def test_wide_rings_reduce_to_brute_force():
     # alpha = 8: T = 8 C exceeds every |A - B| <= 2 once C > 1/4, so S = R
     R, KP, frame, prev = synth.random_case(74, 300, 5, 1, 12, 18)
