@@ -34,6 +34,16 @@ MUTANTS = {
                              "if (d < bd || (d == bd && r > bi)) { bd = d; bi = r; }\n      }\n      annf[i] = bi;\n      if (dist) dist[i] = bd;\n      if (count) count[i] = s_size;\n    }\n    free(B); free(ring_size); free(in_all);"),
     "prev_not_verified": ("int32_t bi = rp;                                /* r_p is always verified */\n      uint32_t bd = Cd;",
                           "int32_t bi = rp;                                /* r_p is always verified */\n      uint32_t bd = 0xffffffffu;"),
+    "ring_argmin_takes_worse_lower_index": (
+        "if (!in_all[r]) continue;\n        uint32_t d = sqdist(q, R + (int64_t)r * D, D);\n"
+        "        if (d < bd || (d == bd && r < bi)) { bd = d; bi = r; }",
+        "if (!in_all[r]) continue;\n        uint32_t d = sqdist(q, R + (int64_t)r * D, D);\n"
+        "        if (d < bd || (d != bd && r < bi)) { bd = d; bi = r; }"),
+    "indexed_argmin_takes_worse_lower_index": (
+        "++s_size;\n        uint32_t d = sqdist(q, R + (int64_t)r * D, D);\n"
+        "        if (d < bd || (d == bd && r < bi)) { bd = d; bi = r; }",
+        "++s_size;\n        uint32_t d = sqdist(q, R + (int64_t)r * D, D);\n"
+        "        if (d < bd || (d != bd && r < bi)) { bd = d; bi = r; }"),
     "limit_off_by_one": ("if (ring_limit >= 0 && ns > (uint32_t)ring_limit) {   /* rings too wide: brute force */",
                          "if (ring_limit >= 0 && ns >= (uint32_t)ring_limit) {   /* rings too wide: brute force */"),
     "count_first_ring_only": ("        in_all[r] = (uint8_t)inside;\n        s_size += (uint32_t)inside;",
@@ -123,7 +133,16 @@ def _pins_fail() -> bool:
             pins.test_definitional_equals_indexed_random(1, a)
             pins.test_definitional_equals_indexed_random(3, a)
 
-    checks += [alpha_one, modes_agree,
+    def modes_agree_on_a_chain():
+        # previous matches from a video chain are good ones, unlike random
+        # fields: r_p then often beats members of S with lower indices
+        w = synth.WORKLOADS["tiny"]
+        R = synth.workload_reference(w)[:1024]
+        KP = synth.keypoints_kmeanspp(R, 8, 11)[1]
+        frames = synth.Video(w.video).frames(0, 3)[:, :48, :64]
+        pins.test_definitional_equals_indexed_tiny_workload((R, KP, frames, oracle.Index(R, KP)))
+
+    checks += [alpha_one, modes_agree, modes_agree_on_a_chain,
                lambda: rpins.test_identity_field_reproduces_frame(23, 17, 3),
                lambda: rpins.test_matches_scatter_formulation(13, 29, 1, 50),
                rpins.test_constant_references_closed_form, rpins.test_golden_two_patches_round_half_up,
