@@ -145,6 +145,24 @@ def test_exact_previous_match_is_kept(alpha, L):
     assert np.array_equal(a, ea) and np.array_equal(d, ed)
 
 
+def test_ties_at_the_minimum_go_to_the_lowest_index():
+    # every reference is the query (128 everywhere) with one pixel raised by
+    # 10, so all lie at squared distance 100 from it and 200 from each other;
+    # r_i = 0.  Rings (alpha = 1/2) around any of them hold every other one,
+    # so anchors are drawn until fewer than L remain, each tying with r_i.
+    # The answer is r_i = 0, the lowest index at the minimum.
+    n = 40
+    R = np.full((n, 64), 128, np.uint8)
+    R[np.arange(n), np.arange(n)] = 138
+    R = R.reshape(n, 8, 8, 1)
+    frame = np.full((8, 8, 1), 128, np.uint8)
+    prev = np.zeros((1, 1), np.int32)
+    fi = oracle.FullIndex(R)
+    for seed in (1, 2, 3):
+        a, d, c, k = oracle.riann_anchor_frame(fi, frame, prev, alpha=(1, 2), L=4, seed=seed)
+        assert (a.item(), d.item(), c.item(), k.item()) == (0, 100, 3, 36)
+
+
 def test_identical_references_stop_at_the_ring_cap():
     # every reference equals the query: each anchor's ring keeps all of S, so
     # only the cap ends the loop; the answer is the lowest index at distance 0

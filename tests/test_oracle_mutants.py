@@ -73,6 +73,16 @@ MUTANTS = {
                                   "  if (0) {\n    const uint64_t lo = (uint64_t)(q - p) * (uint64_t)(q - p);"),
     "anchor_first_match_not_a_candidate": ("      uint32_t bd = Bi;\n", "      uint32_t bd = 0xffffffffu;\n"),
     "random_field_counter_word3": ("{(uint32_t)q, 0u, frame_id, 1u}", "{(uint32_t)q, 0u, frame_id, 0u}"),
+    "anchor_tie_takes_later_anchor": ("if (Ba < bd || (Ba == bd && a < bi)) { bd = Ba; bi = a; }",
+                                      "if (Ba <= bd || (Ba == bd && a < bi)) { bd = Ba; bi = a; }"),
+    "anchor_final_tie_takes_later": ("if (d < bd || (d == bd && S[k] < bi)) { bd = d; bi = S[k]; }",
+                                     "if (d <= bd || (d == bd && S[k] < bi)) { bd = d; bi = S[k]; }"),
+    "recon_entry_n_inside": ("if (r < 0 || r >= n) continue;",
+                             "if (r < 0 || r > n) continue;"),
+    "knn_limit_zero_not_routed": ("all = ring_limit >= 0 && ns > (uint32_t)ring_limit;",
+                                  "all = ring_limit > 0 && ns > (uint32_t)ring_limit;"),
+    "unit_limit_zero_not_routed": ("if (ring_limit >= 0 && ns > (uint32_t)ring_limit) {\n        unit_brute_force",
+                                   "if (ring_limit > 0 && ns > (uint32_t)ring_limit) {\n        unit_brute_force"),
     "philox_multiplier": ("(uint64_t)0xD2511F53u * c0", "(uint64_t)0xD2511F55u * c0"),
     # k-NN output
     "knn_prev_dropped": ("if (all || in_s[r] || r == rp) {", "if (all || in_s[r]) {"),
@@ -146,8 +156,10 @@ def _pins_fail() -> bool:
                lambda: rpins.test_identity_field_reproduces_frame(23, 17, 3),
                lambda: rpins.test_matches_scatter_formulation(13, 29, 1, 50),
                rpins.test_constant_references_closed_form, rpins.test_golden_two_patches_round_half_up,
+               rpins.test_invalid_field_contributes_nothing,
                apins.test_philox_known_answers, apins.test_alpha_one_is_exact_nn,
                apins.test_full_tables_are_sorted_distance_rows, apins.test_random_field_definition_and_range,
+               apins.test_ties_at_the_minimum_go_to_the_lowest_index,
                lambda: apins.test_exact_previous_match_is_kept((1, 4), 20), apins.test_no_loop_is_first_ring_argmin,
                apins.test_identical_references_stop_at_the_ring_cap, apins.test_golden_candidate_set_of_exactly_L,
                lambda: apins.test_matches_independent_implementation((1, 4), 3),
@@ -156,6 +168,7 @@ def _pins_fail() -> bool:
                lambda: kpins.test_frame0_is_sorted_brute_force(5, 1, 9, 9, 8),
                lambda: kpins.test_k1_is_the_argmin_step((1, 2), 40),
                lambda: kpins.test_k1_is_the_argmin_step((0, 1), -1),
+               lambda: kpins.test_k1_is_the_argmin_step((1, 1), 0),
                kpins.test_routed_queries_are_sorted_brute_force, kpins.test_alpha_one_prefix_is_exact_knn,
                kpins.test_routing_at_the_limit_follows_the_argmin_step,
                lambda: kpins.test_matches_set_assembled_from_the_ring_predicate((1, 2)),
@@ -174,6 +187,7 @@ def _pins_fail() -> bool:
                lambda: upins.test_frame0_is_float_brute_force(1), upins.test_wide_rings_reduce_to_brute_force,
                upins.test_alpha_one_is_near_exact_nn,
                lambda: upins.test_exact_previous_match_is_kept((1, 4), -1),
+               upins.test_ring_limit_zero_routes_every_nonempty_ring,
                *[lambda c=c: upins.test_golden_16_pixel_sets(c)
                  for c in ("limit_-1", "limit_5", "limit_6", "zero_query_limit_-1")]]
     for c in checks:

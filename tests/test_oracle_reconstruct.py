@@ -72,6 +72,12 @@ def test_invalid_field_contributes_nothing():
     R = np.full((2, 64), 9, np.uint8)
     out, _ = oracle.reconstruct(R, np.full((2, 3), 5, np.int32))
     assert (out == 0).all()
+    # n itself and -1 are outside [0, n) too (the row after the table holds
+    # 200s, so reading it would show)
+    table = np.full((3, 64), 9, np.uint8)
+    table[2] = 200
+    out, _ = oracle.reconstruct(table[:2], np.array([[2, -1, 2]], np.int32))
+    assert (out == 0).all()
 
 
 def load_golden(name):

@@ -111,6 +111,19 @@ def test_exact_previous_match_is_kept(alpha, limit):
     assert np.array_equal(dist.view(np.uint32), e_dist.view(np.uint32))
 
 
+def test_ring_limit_zero_routes_every_nonempty_ring():
+    # ring_limit = 0: a query goes to brute force unless some ring is empty;
+    # with alpha = 1 every ring holds the exact NN (triangle inequality, up
+    # to rounding), so nearly every query is routed and answered as frame 0
+    R, KP, frame, prev = synth.random_case(93, 300, 4, 1, 14, 19)
+    a, d, c = oracle.riann_unit_frame(R, KP, frame, prev, (1, 1), 0)
+    a0, d0, _ = oracle.riann_unit_frame(R, KP, frame, None)
+    routed = c == 300
+    assert routed.mean() > 0.9
+    assert np.array_equal(a[routed], a0[routed])
+    assert np.array_equal(d[routed].view(np.uint32), d0[routed].view(np.uint32))
+
+
 def test_wide_rings_reduce_to_brute_force():
     # alpha = 8: T = 8 C exceeds every |A - B| <= 2 once C > 1/4, so S = R
     R, KP, frame, prev = synth.random_case(74, 300, 5, 1, 12, 18)
