@@ -8,7 +8,6 @@ pins are run against it; every mutant must make at least one pin fail.
 import os
 import subprocess
 
-import numpy as np
 import pytest
 
 import oracle
