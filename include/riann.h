@@ -504,12 +504,12 @@ int riann_reconstruct(riann_index_t idx, riann_stream_t stream, const int32_t* d
                       const uint8_t* d_frame, uint8_t* d_out, unsigned long long* d_err2);
 
 /*
- * Effects by patch replacement (Sec. 5: an effect or transformation -- e.g.
- * denoising, colourisation, artistic styles -- is applied once to every
- * reference patch at pre-processing time; at run time each query patch is
- * replaced by the transformed version of its match and the overlaps are
- * averaged).  The same reconstruction as riann_reconstruct, with the matched
- * rows read from a caller-supplied table instead of the index's references:
+ * Effects by patch replacement (Sec. 5: an image operation such as
+ * denoising, colouring or an artistic style is run once, offline, on the
+ * reference patches; online, every query patch takes the processed copy of
+ * the reference it matched and overlapping patches are averaged).  The same
+ * reconstruction as riann_reconstruct, with the matched rows read from a
+ * caller-supplied table instead of the index's references:
  *   d_payload  device uint8 [n][8][8][channels], row r = T(reference r)
  *              (n of this index), 16-byte aligned; owned by the caller and
  *              read during the call's kernel only
