@@ -271,7 +271,9 @@ typedef struct {
  *     queries ((H-7)*(W-7)) are rejected with RIANN_ERR_TOO_LARGE.
  *   - The first call on a device looks up the array's device address and
  *     builds its TMA descriptors; make that first call before any stream
- *     capture.
+ *     capture.  Until that set-up has succeeded on a device, a call made
+ *     while `stream` is capturing is refused with RIANN_ERR_INVALID_ARG (the
+ *     next call outside a capture retries the set-up).
  *   - All calls share the array: calls that overlap on the GPU (e.g. on two
  *     streams at once) race and must be serialised by the caller.
  *   - The current device must be the index's device.
@@ -283,6 +285,23 @@ int riann_exact_nn_noalloc(riann_index_t idx, riann_stream_t stream,
 /* Largest query count (H-7)*(W-7) riann_exact_nn_noalloc accepts for 1 or 3
  * channels (0 for other values). */
 int64_t riann_exact_nn_noalloc_max_queries(int32_t channels);
+
+/*
+ * Failure-detection check of the brute-force kernel's bounded waits (the paper
+ * has no counterpart).  Runs riann_exact_nn on the frame with its TMA producer
+ * withholding every reference tile, so that the MMA issuer's wait for the
+ * first one -- a barrier that nothing will complete -- runs out after
+ * `spin_cycles` clock cycles (1000 <= spin_cycles <= 2e9; about 1 s is the
+ * limit every call of the library uses).  The kernel then sets
+ * RIANN_DEV_TIMEOUT in the index's status word, releases its tensor memory and
+ * returns; the device context stays usable and later calls on the index are
+ * unaffected.  d_out_annf receives no defined values.  Asynchronous on
+ * `stream`: read the bit with riann_status.  Errors as riann_exact_nn, plus
+ * RIANN_ERR_INVALID_ARG for spin_cycles out of range and RIANN_ERR_UNSUPPORTED
+ * on a unit-normalised index.
+ */
+int riann_test_wait_expiry(riann_index_t idx, riann_stream_t stream, const uint8_t* d_frame, int32_t H, int32_t W,
+                           int32_t* d_out_annf, int64_t spin_cycles);
 
 /* Synchronises `stream` and reads the counters. */
 int riann_frame_stats(riann_index_t idx, riann_stream_t stream, riann_frame_stats_t* out);

@@ -4,6 +4,7 @@
 // line "r_i = ANNF^(t-1)(x, y)"), batch contexts replayed as CUDA graphs, and
 // the ring-kernel autotuner.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -16,15 +17,24 @@
 
 namespace riann {
 
+// SM count of the current device (cached per device).
 int sm_count() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
+  constexpr int kDevices = 64;
+  static std::atomic<int> cached[kDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) {
+    int v = 0;
     cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-    cached = v > 0 ? v : 1;
+    return v > 0 ? v : 1;
   }
-  return cached;
+  int c = cached[dev].load(std::memory_order_relaxed);
+  if (!c) {
+    int v = 0;
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    c = v > 0 ? v : 1;
+    cached[dev].store(c, std::memory_order_relaxed);
+  }
+  return c;
 }
 
 void prof_begin(Index& ix, int slot, cudaStream_t s) {
@@ -96,6 +106,8 @@ SparseArgs sparse_args(const Index& ix, const riann_params* p, Workspace& ws, un
   sa.E = ix.E;
   sa.RB = ix.RB;
   sa.CW = ix.CW;
+  sa.CE = ix.CE;
+  sa.Ke = ix.Ke;
   sa.n = ix.n;
   sa.K = ix.K;
   sa.Kp = ix.Kp;
@@ -175,6 +187,7 @@ void free_index(Index* ix) {
   cudaFree(ix->E);
   cudaFree(ix->RB);
   cudaFree(ix->CW);
+  cudaFree(ix->CE);
   cudaFree(ix->Rf);
   cudaFree(ix->KPf);
   cudaFree(ix->status);
@@ -400,6 +413,7 @@ int build_index(const uint8_t* d_patches, int32_t n, int32_t channels, const uin
   ix->Kp = (K + 3) / 4 * 4;
   ix->G = (K + 3) / 4;
   ix->nw = (n + 3) / 4 * 4;
+  ix->Ke = (K + 15) / 16 * 16;
   const int D = ix->D;
   size_t& tot = ix->device_bytes;
   cudaError_t e = dalloc(&ix->R, (size_t)n * D, tot);
@@ -413,6 +427,7 @@ int build_index(const uint8_t* d_patches, int32_t n, int32_t channels, const uin
   if (e == cudaSuccess) e = dalloc(&ix->E, (size_t)K * kBuckets, tot);
   if (e == cudaSuccess) e = dalloc(&ix->RB, (size_t)K * (kBuckets + 1), tot);
   if (e == cudaSuccess) e = dalloc(&ix->CW, (size_t)K * ix->G * ix->nw, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->CE, (size_t)K * n * ix->Ke, tot);
   if (e == cudaSuccess) e = dalloc(&ix->status, 1, tot);
   if (e == cudaSuccess) e = dalloc(&ix->stats, kStats, tot);
   if (e == cudaSuccess && unit) e = dalloc(&ix->Rf, (size_t)n * D, tot);
@@ -751,6 +766,24 @@ int riann_exact_nn(riann_index_t idx, riann_stream_t stream, const uint8_t* d_fr
   return from_cuda(ix.unit ? launch_dense_unit(da, ix, cs) : launch_dense_tc(da, ix, ix.ws, cs));
 }
 
+int riann_test_wait_expiry(riann_index_t idx, riann_stream_t stream, const uint8_t* d_frame, int32_t H, int32_t W,
+                           int32_t* d_out_annf, int64_t spin_cycles) {
+  if (!idx || !d_frame || !d_out_annf || !frame_ok(H, W) || spin_cycles < 1000 || spin_cycles > 2000000000LL)
+    return RIANN_ERR_INVALID_ARG;
+  if (idx->unit) return RIANN_ERR_UNSUPPORTED;
+  Index& ix = *idx;
+  std::lock_guard<std::mutex> lock(ix.mu);
+  const int64_t Q = (int64_t)(H - 7) * (W - 7);
+  int rc = ensure_workspace(ix.ws, ix, Q);
+  if (rc) return rc;
+  DenseArgs da = dense_args(ix, nullptr);
+  da.one = make_item(d_frame, nullptr, d_out_annf, nullptr, nullptr, H, W, ix.tile_shape);
+  da.Q = Q;
+  da.spin_limit = spin_cycles;
+  da.withhold = 1;
+  return from_cuda(launch_dense_tc(da, ix, ix.ws, reinterpret_cast<cudaStream_t>(stream)));
+}
+
 int riann_frame_stats(riann_index_t idx, riann_stream_t stream, riann_frame_stats_t* out) {
   if (!idx || !out) return RIANN_ERR_INVALID_ARG;
   unsigned long long v[kStats];
@@ -817,6 +850,7 @@ int riann_exact_nn_noalloc(riann_index_t idx, riann_stream_t stream, const uint8
   cudaError_t e = launch_exact_nn_noalloc(da, *idx, reinterpret_cast<cudaStream_t>(stream));
   if (e == cudaErrorInvalidValue) return RIANN_ERR_TOO_LARGE;
   if (e == cudaErrorNotSupported) return RIANN_ERR_UNSUPPORTED;
+  if (e == cudaErrorStreamCaptureUnsupported) return RIANN_ERR_INVALID_ARG;
   return from_cuda(e);
 }
 

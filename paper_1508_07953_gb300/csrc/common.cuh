@@ -106,8 +106,12 @@ struct Index {
   // inside a ring's code range lies inside the ring.
   uint32_t* E = nullptr;          // [K][kBuckets] bucket edges (UINT32_MAX past the end)
   uint32_t* RB = nullptr;         // [K][kBuckets + 1] first rank of each bucket in TA[m]; RB[m][256] = n
-  uint32_t* CW = nullptr;         // [K][G][nw] in key m's sorted order, codes of keys 4g..4g+3 (one byte
-                                  // each); rows padded to nw = n rounded up to 4 (16-byte aligned rows)
+  uint32_t* CW = nullptr;         // [K][G][nw] in key m's sorted order, filter codes of keys 4g..4g+3 (one
+                                  // byte each: 0x80 | (code >> 1)); rows padded to nw = n rounded up to 4
+                                  // (16-byte aligned rows)
+  uint8_t* CE = nullptr;          // [K][n][Ke] in key m's sorted order, the filter codes of every key of an
+                                  // entry (the bytes of CW), rows of Ke = K rounded up to 16 bytes (pad 0x80)
+  int Ke = 0;
   int G = 0;                      // ceil(K / 4) = Kp / 4
   int nw = 0;                     // n rounded up to 4
   uint32_t* status = nullptr;     // device status word (RIANN_DEV_* bits)
@@ -150,7 +154,8 @@ struct SparseArgs {
   const uint32_t* E;
   const uint32_t* RB;
   const uint32_t* CW;
-  int n, K, Kp, G, nw;
+  const uint8_t* CE;
+  int n, K, Kp, G, nw, Ke;
   int alpha_num, alpha_den, ring_limit;
   int depth;                      // stage-1 filter depth (1..5)
   int unit;                       // unit-normalised float variant (Rf, KPf below)
@@ -179,6 +184,8 @@ struct DenseArgs {
   int knn;                        // k of the k-NN output (0: argmin only); single frame only
   int32_t* knn_idx;               // [Q][knn]
   uint32_t* knn_dist;             // [Q][knn], nullable
+  long long spin_limit;           // bound of the kernel's waits in clock cycles (0: the default, about 1 s)
+  int withhold;                   // test hook (riann_test_wait_expiry): no reference tile is loaded
 };
 
 // Record the start/end event of a profiled kernel slot (no-op when profiling is off).

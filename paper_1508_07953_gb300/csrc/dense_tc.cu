@@ -40,7 +40,7 @@ namespace {
 constexpr int kM = 128;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = (4 + kEpiWarps) * 32;
-constexpr long long kSpinLimit = 2000000000LL;   // clock cycles (about 1 s)
+constexpr long long kSpinLimit = 2000000000LL;   // clock cycles (about 1 s): the default bound of every wait
 constexpr unsigned kFull = 0xffffffffu;
 
 template <int C>
@@ -81,6 +81,9 @@ struct TcArgs {
   unsigned long long* best;       // [rows] packed (dist << 32 | index), pre-set to ~0
   unsigned long long* lists;      // k-NN: [work items][kM][2 halves][kKnnMax] packed, ascending
   uint32_t* status;
+  long long spin_limit;           // bound of every wait, in clock cycles
+  int withhold;                   // test hook: the producer loads no reference tile, so the first
+                                  // wait for one runs out after spin_limit (RIANN_DEV_TIMEOUT)
 };
 
 // k-NN: insert score s of column c into the ascending list (s < its last
@@ -133,11 +136,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait for the phase with the given parity; false on timeout/abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          long long limit) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kSpinLimit) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       return false;
     }
@@ -274,6 +278,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
   volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long lim = a.spin_limit;
   const int64_t Qd = a.count ? (int64_t)*a.count : a.Qfix;
   const int64_t n_qt = (Qd + kM - 1) / kM;
   const int n_rt = a.n_pad / G::BN;
@@ -326,14 +331,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
         const int qt = (int)(it / nsplit), part = (int)(it % nsplit);
         const int rt0 = part * per, rt1 = min(n_rt, rt0 + per);
         if (!first) {
-          if (!(ok = mbar_wait(aempty, a_phase, s_abort))) break;
+          if (!(ok = mbar_wait(aempty, a_phase, s_abort, lim))) break;
           a_phase ^= 1;
         }
         first = false;
         mbar_expect_tx(afull, G::ATOMS * kM * 128);
         for (int at = 0; at < G::ATOMS; ++at) tma_load_2d(sA + at * kM * 128, &a.tmA, afull, 64 * at, qt * kM);
+        if (a.withhold) {
+          // test hook: no reference tile follows; wait (bounded) for the query
+          // tile to land so that no copy is in flight when the CTA leaves
+          ok = mbar_wait(afull, 0, s_abort, lim);
+          ok = false;
+          break;
+        }
         for (int rt = rt0; rt < rt1; ++rt) {
-          if (!(ok = mbar_wait(&empty[stage], phase ^ 1, s_abort))) break;
+          if (!(ok = mbar_wait(&empty[stage], phase ^ 1, s_abort, lim))) break;
           mbar_expect_tx(&full[stage], G::ATOMS * G::BN * 128 + norm_bytes<C>());
           for (int at = 0; at < G::ATOMS; ++at)
             tma_load_2d(sB + (stage * G::ATOMS + at) * G::BN * 128, &a.tmB, &full[stage], 64 * at, rt * G::BN);
@@ -347,13 +359,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
       }
       // tail: every stage released and the last query tile consumed before exit
       for (int s = 0; s < G::STAGES && ok; ++s) {
-        ok = mbar_wait(&empty[stage], phase ^ 1, s_abort);
+        ok = mbar_wait(&empty[stage], phase ^ 1, s_abort, lim);
         if (++stage == G::STAGES) {
           stage = 0;
           phase ^= 1;
         }
       }
-      if (ok && !first) mbar_wait(aempty, a_phase, s_abort);
+      if (ok && !first) mbar_wait(aempty, a_phase, s_abort, lim);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -364,11 +376,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
       for (int64_t it = blockIdx.x; it < n_items && ok; it += gridDim.x) {
         const int part = (int)(it % nsplit);
         const int rt0 = part * per, rt1 = min(n_rt, rt0 + per);
-        if (!(ok = mbar_wait(afull, a_phase, s_abort))) break;
+        if (!(ok = mbar_wait(afull, a_phase, s_abort, lim))) break;
         a_phase ^= 1;
         for (int rt = rt0; rt < rt1; ++rt) {
-          if (!(ok = mbar_wait(&full[stage], phase, s_abort))) break;
-          if (!(ok = mbar_wait(&tempty[acc], acc_phase ^ 1, s_abort))) break;
+          if (!(ok = mbar_wait(&full[stage], phase, s_abort, lim))) break;
+          if (!(ok = mbar_wait(&tempty[acc], acc_phase ^ 1, s_abort, lim))) break;
           tc_fence_after();
           const uint32_t d = tmem + (uint32_t)(acc * G::BN);
 #pragma unroll
@@ -423,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
 #pragma unroll
           for (int j = 0; j < 8; ++j) rn[j] = __ldg(reinterpret_cast<const float4*>(a.rnorm + colt) + j);
         }
-        ok = mbar_wait(&tfull[acc], acc_phase, s_abort);
+        ok = mbar_wait(&tfull[acc], acc_phase, s_abort, lim);
         if (!__all_sync(kFull, ok)) {
           ok = false;
           break;
@@ -669,14 +681,25 @@ __global__ void k_dense_knn_finish(KnnFinishArgs a) {
   }
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel on each
+// device: set once per (device, instantiation), under a lock.
+constexpr int kAttrDevices = 64;
+
 template <int C, bool KNN>
 cudaError_t launch_tc(const TcArgs& t, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_dense_tc<C, KNN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<C>());
-    if (e != cudaSuccess) return e;
-    attr = true;
+  static std::mutex mu;
+  static bool attr[kAttrDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kAttrDevices) return cudaErrorInvalidDevice;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!attr[dev]) {
+      e = cudaFuncSetAttribute(k_dense_tc<C, KNN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<C>());
+      if (e != cudaSuccess) return e;
+      attr[dev] = true;
+    }
   }
   k_dense_tc<C, KNN><<<sm_count(), kThreads, smem_bytes<C>(), s>>>(t);
   return cudaGetLastError();
@@ -757,6 +780,8 @@ cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, Workspace& ws, cudaSt
   t.best = ws.best;
   t.lists = ws.knn_lists;
   t.status = ix.status;
+  t.spin_limit = d.spin_limit > 0 ? d.spin_limit : kSpinLimit;
+  t.withhold = d.withhold;
   const bool knn = d.knn > 0;
   if (knn && (!ws.knn_lists || dense_knn_list_entries(d.Q) > ws.knn_cap)) return cudaErrorInvalidValue;
   prof_begin(ix, kSlotDense, s);
@@ -811,7 +836,9 @@ cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, Workspace& ws, cudaSt
 // that name is only a stand-in for the device symbol.  The device address is
 // looked up once per device (cudaGetSymbolAddress, with that device current)
 // on the first call made on that device, together with the TMA descriptors
-// over it.  That first call should therefore come before any stream capture.
+// over it.  That first call must therefore come before any stream capture: a
+// call made while `s` is capturing, before the set-up has succeeded on its
+// device, is refused (and a failed set-up is retried by the next call).
 // All calls share the array and it keeps the last call's contents; the
 // per-query best slots are reset by every call before use.  Calls that overlap
 // on the GPU (e.g. issued on two streams) race on the array.
@@ -840,8 +867,8 @@ NoallocLayout noalloc_layout(int C) {
 }
 
 struct NoallocDevice {
-  std::once_flag once;
-  cudaError_t err = cudaSuccess;
+  std::mutex mu;
+  bool ready = false;              // set-up succeeded on this device
   unsigned char* base = nullptr;   // device address of g_noalloc_scratch
   CUtensorMap map[2];              // [0] gray rows (D = 64), [1] RGB rows (D = 192)
   bool map_ok[2] = {false, false};
@@ -861,17 +888,25 @@ cudaError_t launch_exact_nn_noalloc(const DenseArgs& d, Index& ix, cudaStream_t 
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
   NoallocDevice& nd = g_noalloc_dev[dev];
-  std::call_once(nd.once, [&nd] {
-    void* p = nullptr;
-    nd.err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (nd.err != cudaSuccess) return;
-    nd.base = static_cast<unsigned char*>(p);
-    for (int k = 0; k < 2; ++k) {
-      const int C = k ? 3 : 1;
-      nd.map_ok[k] = make_row_map(&nd.map[k], nd.base, (uint64_t)noalloc_layout(C).rows, 64 * C, kM);
+  {
+    std::lock_guard<std::mutex> lock(nd.mu);
+    if (!nd.ready) {
+      // the set-up's runtime calls must not run inside a stream capture
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      e = cudaStreamIsCapturing(s, &cap);
+      if (e != cudaSuccess) return e;
+      if (cap != cudaStreamCaptureStatusNone) return cudaErrorStreamCaptureUnsupported;
+      void* p = nullptr;
+      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) return e;
+      nd.base = static_cast<unsigned char*>(p);
+      for (int k = 0; k < 2; ++k) {
+        const int C = k ? 3 : 1;
+        nd.map_ok[k] = make_row_map(&nd.map[k], nd.base, (uint64_t)noalloc_layout(C).rows, 64 * C, kM);
+      }
+      nd.ready = true;
     }
-  });
-  if (nd.err != cudaSuccess) return nd.err;
+  }
   const int C = ix.C;
   const int k = C == 1 ? 0 : 1;
   if (!nd.map_ok[k] || !ix.tm_ready) return cudaErrorNotSupported;
@@ -910,6 +945,8 @@ cudaError_t launch_exact_nn_noalloc(const DenseArgs& d, Index& ix, cudaStream_t 
   t.best = best;
   t.lists = nullptr;
   t.status = ix.status;
+  t.spin_limit = kSpinLimit;
+  t.withhold = 0;
   e = C == 1 ? launch_tc<1, false>(t, s) : launch_tc<3, false>(t, s);
   if (e != cudaSuccess) return e;
 

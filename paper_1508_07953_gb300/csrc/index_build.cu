@@ -167,8 +167,11 @@ __global__ void k_codes(const uint32_t* __restrict__ P, const uint32_t* __restri
   code[t] = (uint8_t)(lo - 1);                 // lo >= 1: e[0] is the smallest distance
 }
 
-// CW[m][g][j]: codes of keys 4g..4g+3 of reference Tid[m][j] (byte i = key 4g+i;
-// keys past K read as 0).
+// CW[m][g][j]: the filter codes of keys 4g..4g+3 of reference Tid[m][j], one
+// byte each (byte i = key 4g+i): 0x80 | (code >> 1), the 7-bit code of 128
+// buckets (every other edge of E) with bit 7 set, so that the ring kernel
+// tests four keys with two subtractions and no borrow between bytes.  Keys
+// past K read as 0x80 (code 0).
 __global__ void k_pack_codes(const int32_t* __restrict__ Tid, const uint8_t* __restrict__ code, int n, int K,
                              int G, int nw, uint32_t* __restrict__ CW) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -180,10 +183,24 @@ __global__ void k_pack_codes(const int32_t* __restrict__ Tid, const uint8_t* __r
     uint32_t w = 0;
     for (int i = 0; i < 4; ++i) {
       const int k = 4 * g + i;
-      if (k < K) w |= (uint32_t)c[k] << (8 * i);
+      w |= (0x80u | (k < K ? (uint32_t)(c[k] >> 1) : 0u)) << (8 * i);
     }
     CW[((int64_t)m * G + g) * nw + j] = w;
   }
+}
+
+// CE[m][j][k]: the filter code of key k of reference Tid[m][j] (the same byte
+// as in CW), every key of an entry in one row of Ke bytes (K rounded up to 16,
+// padding bytes 0x80), so that one 16-byte load per lane reads 16 keys of a
+// gathered entry.
+__global__ void k_pack_entry_codes(const int32_t* __restrict__ Tid, const uint8_t* __restrict__ code, int n,
+                                   int K, int Ke, uint8_t* __restrict__ CE) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // (j, k) of key blockIdx.y's rows
+  const int m = blockIdx.y;
+  if (t >= (int64_t)n * Ke) return;
+  const int j = (int)(t / Ke), k = (int)(t % Ke);
+  const int r = Tid[(int64_t)m * n + j];
+  CE[((int64_t)m * n + j) * Ke + k] = (uint8_t)(0x80u | (k < K ? (uint32_t)(code[(int64_t)r * K + k] >> 1) : 0u));
 }
 
 }  // namespace
@@ -243,6 +260,8 @@ cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
   e = cudaMemsetAsync(ix.CW, 0, sizeof(uint32_t) * (size_t)K * ix.G * ix.nw, s);
   if (e != cudaSuccess) return e;
   k_pack_codes<<<dim3((n + 255) / 256, K), 256, 0, s>>>(ix.Tid, code, n, K, ix.G, ix.nw, ix.CW);
+  k_pack_entry_codes<<<dim3((unsigned)(((int64_t)n * ix.Ke + 255) / 256), K), 256, 0, s>>>(ix.Tid, code, n, K,
+                                                                                          ix.Ke, ix.CE);
   e = cudaFreeAsync(code, s);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

@@ -156,21 +156,11 @@ __device__ __forceinline__ int2 ring_run(const uint32_t* __restrict__ ta, const 
   return make_int2(a, b > a ? b : a);
 }
 
-// Byte-wise unsigned compares on four packed 8-bit codes, in plain 32-bit
-// integer operations.  (x | H) - (y & ~H) subtracts the low 7 bits of every
-// byte without a borrow crossing into the next byte; bit 7 of each result byte
-// is then [x_lo7 >= y_lo7], which with the two top bits decides x >= y.
+// Filter codes are bytes 0x80 | c with c < 128, and range bounds bytes l <= 127
+// and h1 = hi + 1 <= 128, so each byte of w - lo and w - h1 stays in [0, 255]
+// (no borrow into the next byte): bit 7 of the first is [c >= l], of the
+// second [c > hi].  A word passes when every byte has c in [l, hi].
 constexpr uint32_t kHi = 0x80808080u;
-
-__device__ __forceinline__ uint32_t bytes_ge(uint32_t x, uint32_t y) {   // 0x80 where x >= y
-  const uint32_t t = (x | kHi) - (y & ~kHi);
-  return ((x & ~y) | (~(x ^ y) & t)) & kHi;
-}
-
-// every byte with lo <= code <= hi, or marked "always passes" in any4
-__device__ __forceinline__ bool codes_pass(uint32_t w, uint32_t lo4, uint32_t hi4, uint32_t any4) {
-  return ((bytes_ge(w, lo4) & bytes_ge(hi4, w)) | (any4 & kHi)) == kHi;
-}
 
 // k-NN variant: the warp's best keys so far, lane j < k holding the j-th
 // smallest (dist << 32 | index), the other lanes ~0.  Each lane offers one
@@ -194,7 +184,8 @@ __device__ __forceinline__ void knn_merge(unsigned long long& list, unsigned lon
   }
 }
 
-constexpr int kQueue = 256;   // per-warp ring buffer of stage-1 survivors
+constexpr int kQueueA = 256;  // per-warp ring buffers of the filter cascade (powers of two)
+constexpr int kQueueC = 64;
 constexpr int kRowBatch = 4;  // 16-byte words of a distance row loaded per round (4 keys each)
 
 // One CTA per tile of TY x TX query positions; the grid is one frame's tiles.
@@ -224,11 +215,13 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   __shared__ int16_t s_clo[kWarps][kMaxK];        // their bucket codes (-1..255)
   __shared__ int16_t s_chi[kWarps][kMaxK];
   __shared__ uint32_t s_ub[kWarps][kMaxK];        // buckets each ring touches
-  __shared__ uint32_t s_lo4[kWarps][kMaxG];       // per group: packed code ranges
-  __shared__ uint32_t s_hi4[kWarps][kMaxG];
-  __shared__ uint32_t s_any4[kWarps][kMaxG];      // bytes of keys that always pass (seed, padding)
-  __shared__ uint8_t s_ord[kWarps][kMaxG];        // group check order
-  __shared__ int32_t s_queue[kWarps][kQueue];     // stage-1 survivors (seed-run positions)
+  // per group in filter order: (offset of its code row in CW, packed 7-bit
+  // lo, packed hi + 1, unused)
+  __shared__ uint4 s_gd[kWarps][kMaxG];
+  __shared__ __align__(16) uint32_t s_klo[kWarps][kMaxG];   // the same ranges in key order
+  __shared__ __align__(16) uint32_t s_khi[kWarps][kMaxG];
+  __shared__ int32_t s_qa[kWarps][kQueueA];       // filter queues: seed-run positions after stage A,
+  __shared__ int32_t s_qc[kWarps][kQueueC];       // reference ids after stage B
   __shared__ __align__(16) uint32_t s_q[kWarps][NW];   // the warp's query patch
   __shared__ int32_t s_dense[TY * TX];
   __shared__ __align__(16) float s_qf[UNIT ? kWarps : 1][UNIT ? D : 4];   // UNIT: the normalised query
@@ -454,199 +447,233 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     }
     const int jlo = run.x, jhi = run.y;
 
-    // per group of 4 keys: packed code ranges, keys that always pass, and an
-    // estimate of the fraction of references passing (product over its keys of
-    // the fraction of buckets each ring touches)
+    // per group of 4 keys: the 7-bit code ranges of its rings (filter codes
+    // are 0x80 | code7 with code7 = code >> 1, see index_build.cu), packed one
+    // byte per key as lo and hi + 1 (keys that always pass -- the seed,
+    // padding -- take [0, 127]; an empty ring takes lo = hi + 1 = 1, which no
+    // code meets), and an estimate of the fraction of references passing
+    // (product over its keys of the fraction of buckets each ring touches)
     float est = 2.f;
+    uint32_t glo = 0, ghi = 0;
     if (lane < G) {
-      uint32_t lo4 = 0, hi4 = 0, any4 = 0;
       est = 1.f;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int k = 4 * lane + i;
-        uint32_t l = 0, hh = 255, any = 0xffu;
+        uint32_t l = 0, h1 = 128;
         if (k < K && k != ms) {
           const int clo = s_clo[warp][k], chi = s_chi[warp][k];
-          l = (uint32_t)(clo < 0 ? 0 : clo);
-          hh = (uint32_t)(chi < 0 ? 0 : chi);
-          if (chi < 0) l = 1;                 // empty ring: no code fits
-          any = 0;
+          if (chi < 0) {
+            l = h1 = 1;
+          } else {
+            l = (uint32_t)(clo < 0 ? 0 : clo) >> 1;
+            h1 = ((uint32_t)chi >> 1) + 1;
+          }
           est *= (float)s_ub[warp][k] * (1.f / kBuckets);   // fraction of buckets the ring touches
         }
-        lo4 |= l << (8 * i);
-        hi4 |= hh << (8 * i);
-        any4 |= any << (8 * i);
+        glo |= l << (8 * i);
+        ghi |= h1 << (8 * i);
       }
-      s_lo4[warp][lane] = lo4;
-      s_hi4[warp][lane] = hi4;
-      s_any4[warp][lane] = any4;
     }
     {
-      // rank of this lane's group by ascending estimate (ties: lower group)
+      // rank of this lane's group by ascending estimate (ties: lower group);
+      // the scan visits the groups in that order
       int rank = 0;
       for (int g2 = 0; g2 < G; ++g2) {
         const float e2 = __shfl_sync(kFull, est, g2);
         rank += (e2 < est) || (e2 == est && g2 < lane);
       }
-      if (lane < G) s_ord[warp][rank] = (uint8_t)lane;
+      if (lane < G) s_gd[warp][rank] = make_uint4((uint32_t)(lane * a.nw), glo, ghi, 0u);
+      // in key order for the entry rows (padding groups of a row always pass)
+      if (lane < (a.Ke >> 2)) {
+        s_klo[warp][lane] = lane < G ? glo : 0u;
+        s_khi[warp][lane] = lane < G ? ghi : kHi;
+      }
     }
     __syncwarp();
 
-    // a3 + a4.  Stage 1: each lane tests 4 consecutive seed-run entries (one
-    // 16-byte load of the most selective group's codes, next chunk prefetched)
-    // and the survivors against the next two groups; survivors go to a
-    // per-warp ring buffer (warp prefix sum).  Stage 2: each lane takes one
-    // queued entry and tests its distance row exactly against every ring,
-    // lo_m <= A_m <= hi_m as one unsigned compare (A_m - lo_m <= hi_m - lo_m);
-    // members are verified against the query.
+    // a3 + a4, a cascade of filters over the seed ring's run; each stage
+    // compacts its survivors into a per-warp queue (warp prefix sums and
+    // ballots), so that the next, costlier stage runs on full batches of 32:
+    //   A  each lane tests 4 consecutive run entries against the codes of the
+    //      ns1 most selective groups (co-sorted rows of CW: one 16-byte load
+    //      per group, the first three prefetched a chunk ahead);
+    //   B  one queued entry per lane: its reference id (Tid) and the codes of
+    //      every key (its row of CE, one 16-byte load per 16 keys);
+    //   D  one queued reference per lane: the exact test of its key-distance
+    //      row against every ring, lo_m <= A_m <= hi_m as one unsigned compare
+    //      (A_m - lo_m <= hi_m - lo_m), and verification of the members
+    //      against the query.
+    // A code range is a superset of its ring, so only D decides membership.
+    // A deeper stage runs first whenever it holds a full batch, which bounds
+    // the queues (A: < 32 + 128 entries, B: < 64).
     // (k-NN: the same start -- r_p on lane 0 -- is the warp's best-k list)
     unsigned long long best = lane == 0 ? (((unsigned long long)Cd << 32) | (unsigned)rp) : ~0ull;
     uint32_t cnt = 0;
     const uint32_t* cw = a.CW + (int64_t)ms * G * a.nw;
     const int32_t* tid = a.Tid + (int64_t)ms * n;
+    const uint8_t* ce = a.CE + (int64_t)ms * n * a.Ke;
+    const int kc = a.Ke >> 4;                      // 16-byte words per entry row of CE
     const int ns1 = G < a.depth ? G : a.depth;
-    const int g0 = s_ord[warp][0];
-    const int g1 = s_ord[warp][ns1 > 1 ? 1 : 0];
-    const int g2 = s_ord[warp][ns1 > 2 ? 2 : 0];
-    const uint32_t lo0 = s_lo4[warp][g0], hi0 = s_hi4[warp][g0], any0 = s_any4[warp][g0];
-    const uint32_t lo1 = s_lo4[warp][g1], hi1 = s_hi4[warp][g1], any1 = s_any4[warp][g1];
-    const uint32_t lo2 = s_lo4[warp][g2], hi2 = s_hi4[warp][g2], any2 = s_any4[warp][g2];
-    const uint4* cw0 = reinterpret_cast<const uint4*>(cw + (int64_t)g0 * a.nw);
-    const uint32_t* cw1 = cw + (int64_t)g1 * a.nw;
-    const uint32_t* cw2 = cw + (int64_t)g2 * a.nw;
+    const uint4* gd = s_gd[warp];
+    const uint4 d0 = gd[0];
+    const uint4 d1 = gd[ns1 > 1 ? 1 : 0];
+    const uint4 d2 = gd[ns1 > 2 ? 2 : 0];
+    const uint4* cw0 = reinterpret_cast<const uint4*>(cw + d0.x);
+    const uint4* cw1 = reinterpret_cast<const uint4*>(cw + d1.x);
+    const uint4* cw2 = reinterpret_cast<const uint4*>(cw + d2.x);
     const uint4* prow = reinterpret_cast<const uint4*>(a.P);
     const int kq = a.Kp >> 2;                      // 16-byte words per distance row
     const uint4* lw4 = reinterpret_cast<const uint4*>(s_lw[warp]);
-    int32_t* queue = s_queue[warp];
-    int qhead = 0, qn = 0;                         // ring buffer: [qhead, qhead + qn)
-
-    auto drain = [&](int take) {
-      bool alive = lane < take;
-      const int j = alive ? queue[(qhead + lane) & (kQueue - 1)] : 0;
-      int r = 0;
-      if (alive) {
-        r = __ldg(tid + j);
-        const uint4* row = prow + (int64_t)r * kq;
-        // kRowBatch 4-key groups per round of loads; a lane stops at its
-        // first failed round
-#pragma unroll 1
-        for (int h = 0; h < kq && alive; h += kRowBatch) {
-          uint4 v[kRowBatch];
-#pragma unroll
-          for (int c = 0; c < kRowBatch; ++c) v[c] = h + c < kq ? __ldg(row + h + c) : make_uint4(0, 0, 0, 0);
-          unsigned ok = 1u;
-#pragma unroll
-          for (int c = 0; c < kRowBatch; ++c) {
-            if (h + c < kq) {
-              const uint4 l0 = lw4[2 * (h + c)], l1 = lw4[2 * (h + c) + 1];
-              ok &= (unsigned)(v[c].x - l0.x <= l0.y) & (unsigned)(v[c].y - l0.z <= l0.w) &
-                    (unsigned)(v[c].z - l1.x <= l1.y) & (unsigned)(v[c].w - l1.z <= l1.w);
-            }
-          }
-          alive = ok != 0u;
-        }
-      }
-      unsigned long long key = ~0ull;
-      if (alive) {
-        ++cnt;
-        uint32_t d = 0;
-        if (UNIT) {
-          d = __float_as_uint(unit_dist<D>(qf, a.Rf + (int64_t)r * D));
-        } else {
-          const uint4* r4 = reinterpret_cast<const uint4*>(a.R + (int64_t)r * D);
-#pragma unroll
-          for (int v = 0; v < NW / 4; ++v) d = sq4(q + 4 * v, __ldg(r4 + v), d);
-        }
-        key = ((unsigned long long)d << 32) | (unsigned)r;
-        if (!KNN) best = key < best ? key : best;
-      }
-      // k-NN: r_p is on the list already (S u {r_p} is a set)
-      if (KNN) knn_merge(best, alive && r != rp ? key : ~0ull, a.knn, lane);
-    };
+    const uint4* klo4 = reinterpret_cast<const uint4*>(s_klo[warp]);
+    const uint4* khi4 = reinterpret_cast<const uint4*>(s_khi[warp]);
+    int32_t* qa = s_qa[warp];
+    int32_t* qc = s_qc[warp];
+    int ha = 0, na = 0, hc = 0, nc = 0;            // queue heads and lengths
+    const unsigned lt = (1u << lane) - 1u;
 
     const int ja = jlo & ~3;
-    const uint4* c1 = reinterpret_cast<const uint4*>(cw1);
-    const uint4* c2 = reinterpret_cast<const uint4*>(cw2);
     uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, a2 = a0;
     if (ja + 4 * lane < jhi) {
       a0 = __ldg(cw0 + (ja >> 2) + lane);
-      if (ns1 > 1) a1 = __ldg(c1 + (ja >> 2) + lane);
-      if (ns1 > 2) a2 = __ldg(c2 + (ja >> 2) + lane);
+      if (ns1 > 1) a1 = __ldg(cw1 + (ja >> 2) + lane);
+      if (ns1 > 2) a2 = __ldg(cw2 + (ja >> 2) + lane);
     }
-    for (int base = ja;; base += 128) {
-      const bool more = base < jhi;
-      if (more) {
-        // prefetch the next chunk of all three groups, then test this one
-        uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0, b2 = b0;
-        if (base + 128 + 4 * lane < jhi) {
-          const int o = ((base + 128) >> 2) + lane;
-          b0 = __ldg(cw0 + o);
-          if (ns1 > 1) b1 = __ldg(c1 + o);
-          if (ns1 > 2) b2 = __ldg(c2 + o);
-        }
-        const int j0 = base + 4 * lane;
-        const uint32_t v0[4] = {a0.x, a0.y, a0.z, a0.w};
-        const uint32_t v1[4] = {a1.x, a1.y, a1.z, a1.w};
-        const uint32_t v2[4] = {a2.x, a2.y, a2.z, a2.w};
-        unsigned bits = 0;
+    int base = ja;
+    for (;;) {
+      const bool done = base >= jhi;
+      if (nc >= 32 || (done && nc > 0)) {
+        // ---- D: exact row test and verification ----
+        const int take = nc < 32 ? nc : 32;
+        bool alive = lane < take;
+        const int r = alive ? qc[(hc + lane) & (kQueueC - 1)] : 0;
+        hc = (hc + take) & (kQueueC - 1);
+        nc -= take;
+        if (alive) {
+          const uint4* row = prow + (int64_t)r * kq;
+          // kRowBatch 4-key words per round of loads; a lane stops at its
+          // first failed round
+#pragma unroll 1
+          for (int h = 0; h < kq && alive; h += kRowBatch) {
+            uint4 v[kRowBatch];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const bool ok = codes_pass(v0[u], lo0, hi0, any0) &&
-                          (ns1 < 2 || codes_pass(v1[u], lo1, hi1, any1)) &&
-                          (ns1 < 3 || codes_pass(v2[u], lo2, hi2, any2));
-          bits |= (ok ? 1u : 0u) << u;
-        }
-        // only the first and the last chunk hold entries outside [jlo, jhi)
-        // (a warp-uniform test: the middle chunks skip the range check)
-        if (base < jlo || base + 128 > jhi) {
-          unsigned inr = 0;
+            for (int c = 0; c < kRowBatch; ++c) v[c] = h + c < kq ? __ldg(row + h + c) : make_uint4(0, 0, 0, 0);
+            unsigned ok = 1u;
 #pragma unroll
-          for (int u = 0; u < 4; ++u) inr |= (j0 + u >= jlo && j0 + u < jhi ? 1u : 0u) << u;
-          bits &= inr;
-        }
-        // deeper stage 1 (depth 4..5): the next groups by estimated
-        // selectivity, one 16-byte load per lane for its four entries, only
-        // while some entry of the warp is still alive
-        for (int oi = 3; oi < ns1; ++oi) {
-          if (!__any_sync(kFull, bits != 0)) break;
-          if (bits) {
-            const int g = s_ord[warp][oi];
-            const uint4 wv4 = __ldg(reinterpret_cast<const uint4*>(cw + (int64_t)g * a.nw) + (j0 >> 2));
-            const uint32_t lo4 = s_lo4[warp][g], hi4 = s_hi4[warp][g], any4 = s_any4[warp][g];
-            const uint32_t vg[4] = {wv4.x, wv4.y, wv4.z, wv4.w};
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (((bits >> u) & 1u) && !codes_pass(vg[u], lo4, hi4, any4)) bits &= ~(1u << u);
+            for (int c = 0; c < kRowBatch; ++c) {
+              if (h + c < kq) {
+                const uint4 l0 = lw4[2 * (h + c)], l1 = lw4[2 * (h + c) + 1];
+                ok &= (unsigned)(v[c].x - l0.x <= l0.y) & (unsigned)(v[c].y - l0.z <= l0.w) &
+                      (unsigned)(v[c].z - l1.x <= l1.y) & (unsigned)(v[c].w - l1.z <= l1.w);
+              }
+            }
+            alive = ok != 0u;
           }
         }
-        a0 = b0;
-        a1 = b1;
-        a2 = b2;
-        // warp prefix sum of survivor counts -> append to the ring buffer
-        const int c = __popc(bits);
-        int pre = c;
+        unsigned long long key = ~0ull;
+        if (alive) {
+          ++cnt;
+          uint32_t d = 0;
+          if (UNIT) {
+            d = __float_as_uint(unit_dist<D>(qf, a.Rf + (int64_t)r * D));
+          } else {
+            const uint4* r4 = reinterpret_cast<const uint4*>(a.R + (int64_t)r * D);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(kFull, pre, o);
-          if (lane >= o) pre += v;
+            for (int v = 0; v < NW / 4; ++v) d = sq4(q + 4 * v, __ldg(r4 + v), d);
+          }
+          key = ((unsigned long long)d << 32) | (unsigned)r;
+          if (!KNN) best = key < best ? key : best;
         }
-        const int tot = __shfl_sync(kFull, pre, 31);
-        pre -= c;
-        int slot = qhead + qn + pre;
+        // k-NN: r_p is on the list already (S u {r_p} is a set)
+        if (KNN) knn_merge(best, alive && r != rp ? key : ~0ull, a.knn, lane);
+        continue;
+      }
+      if (na >= 32 || (done && na > 0)) {
+        // ---- B: the codes of every key of the entry, and its reference id ----
+        const int take = na < 32 ? na : 32;
+        const bool on = lane < take;
+        const int j = on ? qa[(ha + lane) & (kQueueA - 1)] : 0;
+        ha = (ha + take) & (kQueueA - 1);
+        na -= take;
+        const int r = on ? __ldg(tid + j) : 0;
+        const uint4* er = reinterpret_cast<const uint4*>(ce + (int64_t)j * a.Ke);
+        uint32_t pass = kHi;
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if ((bits >> u) & 1u) queue[(slot++) & (kQueue - 1)] = j0 + u;
-        qn += tot;
+        for (int c = 0; c < kMaxK / 16; ++c) {
+          if (c < kc) {
+            const uint4 w = on ? __ldg(er + c) : make_uint4(kHi, kHi, kHi, kHi);
+            const uint4 l = klo4[c], h = khi4[c];
+            pass &= (w.x - l.x) & ~(w.x - h.x) & (w.y - l.y) & ~(w.y - h.y);
+            pass &= (w.z - l.z) & ~(w.z - h.z) & (w.w - l.w) & ~(w.w - h.w);
+          }
+        }
+        const bool ok = on && (pass & kHi) == kHi;
+        const unsigned m = __ballot_sync(kFull, ok);
+        if (ok) qc[(hc + nc + __popc(m & lt)) & (kQueueC - 1)] = r;
+        nc += __popc(m);
+        continue;
       }
-      // drain full batches; after the last chunk also the remainder
-      while (qn >= 32 || (!more && qn > 0)) {
-        const int take = qn < 32 ? qn : 32;
-        __syncwarp();
-        drain(take);
-        qhead = (qhead + take) & (kQueue - 1);
-        qn -= take;
+      if (done) break;
+      // ---- A: the next chunk of 128 run entries against the first groups ----
+      uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0, b2 = b0;
+      if (base + 128 + 4 * lane < jhi) {
+        const int o = ((base + 128) >> 2) + lane;
+        b0 = __ldg(cw0 + o);
+        if (ns1 > 1) b1 = __ldg(cw1 + o);
+        if (ns1 > 2) b2 = __ldg(cw2 + o);
       }
-      if (!more) break;
+      const int j0 = base + 4 * lane;
+      const uint32_t v0[4] = {a0.x, a0.y, a0.z, a0.w};
+      const uint32_t v1[4] = {a1.x, a1.y, a1.z, a1.w};
+      const uint32_t v2[4] = {a2.x, a2.y, a2.z, a2.w};
+      unsigned bits = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        uint32_t p = (v0[u] - d0.y) & ~(v0[u] - d0.z);
+        if (ns1 > 1) p &= (v1[u] - d1.y) & ~(v1[u] - d1.z);
+        if (ns1 > 2) p &= (v2[u] - d2.y) & ~(v2[u] - d2.z);
+        bits |= ((p & kHi) == kHi ? 1u : 0u) << u;
+      }
+      // only the first and the last chunk hold entries outside [jlo, jhi)
+      // (a warp-uniform test: the middle chunks skip the range check)
+      if (base < jlo || base + 128 > jhi) {
+        unsigned inr = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) inr |= (j0 + u >= jlo && j0 + u < jhi ? 1u : 0u) << u;
+        bits &= inr;
+      }
+      // depth 4..5: the next groups, one 16-byte load per lane for its four
+      // entries, only while some entry of the warp is still alive
+      for (int oi = 3; oi < ns1; ++oi) {
+        if (!__any_sync(kFull, bits != 0)) break;
+        if (bits) {
+          const uint4 g = gd[oi];
+          const uint4 wv4 = __ldg(reinterpret_cast<const uint4*>(cw + g.x) + (j0 >> 2));
+          const uint32_t vg[4] = {wv4.x, wv4.y, wv4.z, wv4.w};
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if ((((vg[u] - g.y) & ~(vg[u] - g.z) & kHi) != kHi)) bits &= ~(1u << u);
+        }
+      }
+      a0 = b0;
+      a1 = b1;
+      a2 = b2;
+      base += 128;
+      // warp prefix sum of survivor counts -> append to queue A
+      const int c = __popc(bits);
+      int pre = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, pre, o);
+        if (lane >= o) pre += v;
+      }
+      const int tot = __shfl_sync(kFull, pre, 31);
+      pre -= c;
+      int slot = ha + na + pre;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if ((bits >> u) & 1u) qa[(slot++) & (kQueueA - 1)] = j0 + u;
+      na += tot;
     }
     if (KNN) {
       if (lane < a.knn) {

@@ -98,6 +98,7 @@ _lib.riann_frame_stats.argtypes = [_P, _P, ctypes.POINTER(riann_frame_stats_t)]
 _lib.riann_profile_enable.argtypes = [_P, ctypes.c_int]
 _lib.riann_profile_read.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_float), _i32]
 _lib.riann_exact_nn_noalloc.argtypes = [_P, _P, _P, _i32, _i32, _P, _P]
+_lib.riann_test_wait_expiry.argtypes = [_P, _P, _P, _i32, _i32, _P, _i64]
 _lib.riann_exact_nn_noalloc_max_queries.argtypes = [_i32]
 _lib.riann_exact_nn_noalloc_max_queries.restype = ctypes.c_int64
 _lib.riann_session_create.argtypes = [_P, _i32, _i32, ctypes.POINTER(_P)]
@@ -494,6 +495,17 @@ def riann_exact_nn(index: RiannIndex, frame: torch.Tensor, out_annf: torch.Tenso
                                H, W, _dev(out_annf, _I32, "out_annf", Q),
                                _dev(out_dist, _U32, "out_dist", Q)),
            "riann_exact_nn")
+
+
+def riann_test_wait_expiry(index: RiannIndex, frame: torch.Tensor, out_annf: torch.Tensor, spin_cycles: int,
+                           stream: Optional[torch.cuda.Stream] = None) -> None:
+    """Brute force with every reference tile withheld, so that its bounded
+    wait runs out after spin_cycles (see riann.h); read the result with riann_status."""
+    H, W = _frame_dims(frame, index.C)
+    Q = (H - 7) * (W - 7)
+    _check(_lib.riann_test_wait_expiry(index.handle, _stream(stream), _dev(frame, (torch.uint8,), "frame"),
+                                       H, W, _dev(out_annf, _I32, "out_annf", Q), int(spin_cycles)),
+           "riann_test_wait_expiry")
 
 
 def riann_frame_stats(index: RiannIndex, stream: Optional[torch.cuda.Stream] = None) -> dict:
