@@ -83,7 +83,7 @@ typedef struct {
    * answered by brute force over all of R (count = n).  -1: never. */
   int32_t ring_limit;
   /* Performance knob only; results never depend on it.  0 = the index's
-   * tuned setting; 1..5 = number of 4-ring code groups the candidate scan
+   * tuned setting; 1..3 = number of 4-ring code groups the candidate scan
    * tests before it compacts survivors (see riann_autotune). */
   int32_t cap;
 } riann_params;
@@ -112,6 +112,28 @@ typedef struct {
 int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t channels,
                                 const uint8_t* d_keypoints, int32_t K,
                                 riann_stream_t stream, riann_index_t* out);
+
+/*
+ * riann_build_reference_index with a choice of scan order (performance only:
+ * every order gives identical results).  For each key point the index also
+ * keeps the references in a "pair order": sorted by (7-bit bucket of the
+ * distance to the key point, 7-bit bucket of the distance to a partner key
+ * point), then as in the key's sorted list; a query whose seed ring is that
+ * key's scans only the buckets where both rings' code ranges meet.
+ *   scan_order  RIANN_SCAN_AUTO: RIANN_SCAN_PAIRS for n >= 32768, else
+ *                 RIANN_SCAN_SINGLE (smaller buckets fragment the runs);
+ *               RIANN_SCAN_PAIRS: partner = the farthest other key point;
+ *               RIANN_SCAN_SINGLE: partner = the key itself (the pair order is
+ *                 its sorted list; the scan visits the seed ring's exact run).
+ * Errors as riann_build_reference_index, plus RIANN_ERR_INVALID_ARG for an
+ * unknown scan_order.
+ */
+#define RIANN_SCAN_AUTO 0
+#define RIANN_SCAN_PAIRS 1
+#define RIANN_SCAN_SINGLE 2
+int riann_build_reference_index_ex(const uint8_t* d_patches, int32_t n, int32_t channels,
+                                   const uint8_t* d_keypoints, int32_t K, int32_t scan_order,
+                                   riann_stream_t stream, riann_index_t* out);
 
 /*
  * Unit-normalised float variant (Sec. 3.4: representatives scaled to length
@@ -421,13 +443,13 @@ int riann_batch_info(riann_batch_t b, riann_batch_info_t* out);
 
 /* ------------------------------------------------------------------------
  * Autotuner: times the ring kernel's variants (query tile 4x32 or 8x16;
- * 1 to 5 code groups tested before compaction) on a sample frame and its
+ * 1 to 3 code groups tested before compaction) on a sample frame and its
  * previous field, keeps the fastest in the index, and returns every timing.
  * The variants compute identical results.
  * ------------------------------------------------------------------------ */
 typedef struct {
   int32_t tile_shape;   /* 0: 4 x 32 queries per CTA, 1: 8 x 16 */
-  int32_t depth;        /* 1..5 */
+  int32_t depth;        /* 1..3 */
   float ms;             /* mean time of one frame (riann_autotune), else -1 */
 } riann_tuning_t;
 

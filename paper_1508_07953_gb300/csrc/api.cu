@@ -66,7 +66,7 @@ cudaError_t dalloc(T** p, size_t count, size_t& total) {
 
 bool params_ok(const riann_params* p) {
   return p && p->alpha_den >= 1 && p->alpha_den <= 8 && p->alpha_num >= 0 &&
-         p->alpha_num <= 8 * p->alpha_den && p->ring_limit >= -1 && p->cap >= 0 && p->cap <= 5;
+         p->alpha_num <= 8 * p->alpha_den && p->ring_limit >= -1 && p->cap >= 0 && p->cap <= kMaxScanDepth;
 }
 
 bool frame_ok(int32_t H, int32_t W) {
@@ -105,6 +105,9 @@ SparseArgs sparse_args(const Index& ix, const riann_params* p, Workspace& ws, un
   sa.Tid = ix.Tid;
   sa.E = ix.E;
   sa.RB = ix.RB;
+  sa.partner = ix.partner;
+  sa.Tid2 = ix.Tid2;
+  sa.OFF = ix.OFF;
   sa.CW = ix.CW;
   sa.CE = ix.CE;
   sa.Ke = ix.Ke;
@@ -186,6 +189,9 @@ void free_index(Index* ix) {
   cudaFree(ix->Tid);
   cudaFree(ix->E);
   cudaFree(ix->RB);
+  cudaFree(ix->partner);
+  cudaFree(ix->Tid2);
+  cudaFree(ix->OFF);
   cudaFree(ix->CW);
   cudaFree(ix->CE);
   cudaFree(ix->Rf);
@@ -389,9 +395,11 @@ cudaError_t enqueue_batch(riann_batch_s* b, const riann_params* p, cudaStream_t 
 namespace {
 
 int build_index(const uint8_t* d_patches, int32_t n, int32_t channels, const uint8_t* d_keypoints, int32_t K,
-                riann_stream_t stream, bool unit, riann_index_t* out) {
+                riann_stream_t stream, bool unit, int scan_order, riann_index_t* out) {
   if (!out) return RIANN_ERR_INVALID_ARG;
   *out = nullptr;
+  if (scan_order != RIANN_SCAN_AUTO && scan_order != RIANN_SCAN_PAIRS && scan_order != RIANN_SCAN_SINGLE)
+    return RIANN_ERR_INVALID_ARG;
   if (!d_patches || !d_keypoints || n < 1 || n > (1 << 24) || K < 1 || K > kMaxK ||
       (channels != 1 && channels != 3))
     return RIANN_ERR_INVALID_ARG;
@@ -405,6 +413,7 @@ int build_index(const uint8_t* d_patches, int32_t n, int32_t channels, const uin
   if (!ix) return RIANN_ERR_OOM;
   ix->device = dev;
   ix->unit = unit;
+  ix->pair_scan = scan_order == RIANN_SCAN_PAIRS || (scan_order == RIANN_SCAN_AUTO && n >= kPairMinN);
   ix->n = n;
   ix->K = K;
   ix->C = channels;
@@ -426,6 +435,9 @@ int build_index(const uint8_t* d_patches, int32_t n, int32_t channels, const uin
   if (e == cudaSuccess) e = dalloc(&ix->Tid, (size_t)n * K, tot);
   if (e == cudaSuccess) e = dalloc(&ix->E, (size_t)K * kBuckets, tot);
   if (e == cudaSuccess) e = dalloc(&ix->RB, (size_t)K * (kBuckets + 1), tot);
+  if (e == cudaSuccess) e = dalloc(&ix->partner, (size_t)K, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->Tid2, (size_t)n * K, tot);
+  if (e == cudaSuccess) e = dalloc(&ix->OFF, (size_t)K * (kPairCodes * kPairCodes + 1), tot);
   if (e == cudaSuccess) e = dalloc(&ix->CW, (size_t)K * ix->G * ix->nw, tot);
   if (e == cudaSuccess) e = dalloc(&ix->CE, (size_t)K * n * ix->Ke, tot);
   if (e == cudaSuccess) e = dalloc(&ix->status, 1, tot);
@@ -488,12 +500,18 @@ const char* riann_strerror(int code) {
 int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t channels,
                                 const uint8_t* d_keypoints, int32_t K, riann_stream_t stream,
                                 riann_index_t* out) {
-  return build_index(d_patches, n, channels, d_keypoints, K, stream, false, out);
+  return build_index(d_patches, n, channels, d_keypoints, K, stream, false, RIANN_SCAN_AUTO, out);
+}
+
+int riann_build_reference_index_ex(const uint8_t* d_patches, int32_t n, int32_t channels,
+                                   const uint8_t* d_keypoints, int32_t K, int32_t scan_order,
+                                   riann_stream_t stream, riann_index_t* out) {
+  return build_index(d_patches, n, channels, d_keypoints, K, stream, false, scan_order, out);
 }
 
 int riann_build_unit_index(const uint8_t* d_patches, int32_t n, int32_t channels, const uint8_t* d_keypoints,
                            int32_t K, riann_stream_t stream, riann_index_t* out) {
-  return build_index(d_patches, n, channels, d_keypoints, K, stream, true, out);
+  return build_index(d_patches, n, channels, d_keypoints, K, stream, true, RIANN_SCAN_AUTO, out);
 }
 
 void riann_index_destroy(riann_index_t idx) {
@@ -1181,7 +1199,7 @@ int riann_batch_info(riann_batch_t b, riann_batch_info_t* out) {
 // autotuner
 // ---------------------------------------------------------------------------
 int riann_set_tuning(riann_index_t idx, const riann_tuning_t* t) {
-  if (!idx || !t || t->tile_shape < 0 || t->tile_shape >= kTileShapes || t->depth < 1 || t->depth > 5)
+  if (!idx || !t || t->tile_shape < 0 || t->tile_shape >= kTileShapes || t->depth < 1 || t->depth > kMaxScanDepth)
     return RIANN_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(idx->mu);
   idx->tile_shape = t->tile_shape;
@@ -1221,7 +1239,7 @@ int riann_autotune(riann_index_t idx, const riann_params* p, riann_stream_t stre
   ix.profile = false;
   const int saved_shape = ix.tile_shape, saved_depth = ix.depth;
   for (int shape = 0; shape < kTileShapes && e == cudaSuccess; ++shape) {
-    for (int depth = 1; depth <= 5 && e == cudaSuccess; ++depth) {
+    for (int depth = 1; depth <= kMaxScanDepth && e == cudaSuccess; ++depth) {
       ix.tile_shape = shape;
       ix.depth = depth;
       const FrameItem it = make_item(d_frame, d_prev_annf, out, nullptr, nullptr, H, W, shape);

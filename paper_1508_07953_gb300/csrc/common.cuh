@@ -19,6 +19,11 @@ constexpr int kMaxDim = 192;
 constexpr int kDenseTileN = 256;   // reference rows per tensor-core tile
 constexpr int kDenseTileM = 128;   // query rows per tensor-core tile
 constexpr int kBuckets = 256;      // quantile buckets per key point (8-bit codes)
+constexpr int kPairCodes = 128;    // filter codes per key point (7-bit: code >> 1)
+// Smallest reference set whose keys scan in pair order with a second key:
+// below it a 7-bit bucket holds too few references for the partner's runs
+// to fill the scan's 128-entry chunks, and each key pairs with itself.
+constexpr int kPairMinN = 32768;
 constexpr int kKnnMax = 8;         // largest k of the k-NN output
 static_assert(kKnnMax == RIANN_KNN_MAX, "k-NN list length");
 
@@ -28,7 +33,9 @@ enum StatSlot { kStatRingQueries = 0, kStatDenseQueries, kStatSumSeed, kStatSumS
 // Kernel slots of the per-kernel event profiler (riann_profile_*).
 enum KernelSlot { kSlotSparse = 0, kSlotDense = 1, kSlotPrep = 2, kSlots = 4 };
 
-// Ring-kernel variants the autotuner chooses between: query tile shape.
+// Ring-kernel variants the autotuner chooses between: query tile shape, and
+// the number of code groups (1..kMaxScanDepth) the scan tests per chunk.
+constexpr int kMaxScanDepth = 3;
 enum TileShape { kTile4x32 = 0, kTile8x16 = 1, kTileShapes = 2 };
 
 // Largest possible squared distance between two patches of `dim` bytes.
@@ -106,10 +113,19 @@ struct Index {
   // inside a ring's code range lies inside the ring.
   uint32_t* E = nullptr;          // [K][kBuckets] bucket edges (UINT32_MAX past the end)
   uint32_t* RB = nullptr;         // [K][kBuckets + 1] first rank of each bucket in TA[m]; RB[m][256] = n
-  uint32_t* CW = nullptr;         // [K][G][nw] in key m's sorted order, filter codes of keys 4g..4g+3 (one
+  // Pair order of key m: the references sorted by the cell (code7_m, code7_p)
+  // of m and its partner p = partner[m] (code7 = code >> 1), then in the order
+  // of key m's sorted list (TA, Tid), so that the references of one seed bucket
+  // whose partner code lies in a range are contiguous.  A key paired with
+  // itself (n < kPairMinN) keeps exactly its sorted list's order.
+  bool pair_scan = false;         // partners are the farthest key points (else every key pairs with itself)
+  int32_t* partner = nullptr;     // [K] scan partner of each key (the farthest key point, or itself)
+  int32_t* Tid2 = nullptr;        // [K][n] reference id at each position of the pair order
+  uint32_t* OFF = nullptr;        // [K][kPairCodes^2 + 1] first position of each cell (cell = cm * 128 + cp)
+  uint32_t* CW = nullptr;         // [K][G][nw] in key m's pair order, filter codes of keys 4g..4g+3 (one
                                   // byte each: 0x80 | (code >> 1)); rows padded to nw = n rounded up to 4
                                   // (16-byte aligned rows)
-  uint8_t* CE = nullptr;          // [K][n][Ke] in key m's sorted order, the filter codes of every key of an
+  uint8_t* CE = nullptr;          // [K][n][Ke] in key m's pair order, the filter codes of every key of an
                                   // entry (the bytes of CW), rows of Ke = K rounded up to 16 bytes (pad 0x80)
   int Ke = 0;
   int G = 0;                      // ceil(K / 4) = Kp / 4
@@ -125,7 +141,7 @@ struct Index {
 
   // ring-kernel tuning (riann_autotune sets them; these are the defaults)
   int tile_shape = kTile4x32;
-  int depth = 3;                  // stage-1 filter depth (groups tested before compaction)
+  int depth = 3;                  // scan depth (code groups tested before compaction, 1..kMaxScanDepth)
 
   // optional per-kernel timing with CUDA events recorded on the launch stream
   bool profile = false;
@@ -153,11 +169,14 @@ struct SparseArgs {
   const int32_t* Tid;
   const uint32_t* E;
   const uint32_t* RB;
+  const int32_t* partner;
+  const int32_t* Tid2;
+  const uint32_t* OFF;
   const uint32_t* CW;
   const uint8_t* CE;
   int n, K, Kp, G, nw, Ke;
   int alpha_num, alpha_den, ring_limit;
-  int depth;                      // stage-1 filter depth (1..5)
+  int depth;                      // scan depth (1..kMaxScanDepth)
   int unit;                       // unit-normalised float variant (Rf, KPf below)
   const float* Rf;
   const float* KPf;

@@ -203,6 +203,79 @@ __global__ void k_pack_entry_codes(const int32_t* __restrict__ Tid, const uint8_
   CE[((int64_t)m * n + j) * Ke + k] = (uint8_t)(0x80u | (k < K ? (uint32_t)(code[(int64_t)r * K + k] >> 1) : 0u));
 }
 
+// Scan partner of each key point (performance only): the key point farthest
+// from it (largest ||k_m - k_p||^2, lowest index on ties), or the key itself
+// (self = 1, and always when K = 1), whose pair order is then its sorted list.
+__global__ void k_partners(const uint8_t* __restrict__ KP, int K, int D, int self, int32_t* __restrict__ partner) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= K) return;
+  if (self) {
+    partner[m] = m;
+    return;
+  }
+  const uint32_t* a = reinterpret_cast<const uint32_t*>(KP + (int64_t)m * D);
+  uint32_t best = 0;
+  int bp = m;
+  for (int p = 0; p < K; ++p) {
+    if (p == m) continue;
+    const uint32_t* b = reinterpret_cast<const uint32_t*>(KP + (int64_t)p * D);
+    uint32_t s = 0;
+    for (int w = 0; w < D / 4; ++w) {
+      const uint32_t d = __vabsdiffu4(a[w], b[w]);
+      s = __dp4a(d, d, s);
+    }
+    if (s > best || (s == best && bp == m)) {
+      best = s;
+      bp = p;
+    }
+  }
+  partner[m] = bp;
+}
+
+// keys[m][t] = (cell << 32) | t for the reference r = Tid[m][t] at rank t of
+// key m's sorted list, cell = code7_m(r) * 128 + code7_p(r) with p the partner
+// of m and code7 = code >> 1; all-ones padding up to NP.  Sorted, a cell's
+// references keep the sorted list's order (distance to k_m, then index).
+__global__ void k_make_pair_keys(const uint8_t* __restrict__ code, const int32_t* __restrict__ Tid,
+                                 const int32_t* __restrict__ partner, int n, int K, int NP,
+                                 unsigned long long* __restrict__ keys) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (t >= NP) return;
+  unsigned long long v = ~0ull;
+  if (t < n) {
+    const int r = Tid[(int64_t)m * n + t];
+    const uint32_t cm = code[(int64_t)r * K + m] >> 1, cp = code[(int64_t)r * K + partner[m]] >> 1;
+    v = ((unsigned long long)(cm * kPairCodes + cp) << 32) | (unsigned)t;
+  }
+  keys[(int64_t)m * NP + t] = v;
+}
+
+__global__ void k_pair_split(const unsigned long long* __restrict__ keys, const int32_t* __restrict__ Tid, int n,
+                             int NP, int32_t* __restrict__ Tid2) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  if (j >= n) return;
+  const int t = (int)(keys[(int64_t)m * NP + j] & 0xffffffffu);
+  Tid2[(int64_t)m * n + j] = Tid[(int64_t)m * n + t];
+}
+
+// OFF[m][v] = first position j of key m's pair order whose cell is >= v, for
+// v = 0 .. kPairCodes^2 (the last entry is n).
+__global__ void k_pair_offsets(const unsigned long long* __restrict__ keys, int n, int NP, uint32_t* __restrict__ OFF) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int m = blockIdx.y;
+  constexpr int kCells = kPairCodes * kPairCodes;
+  if (v > kCells) return;
+  const unsigned long long* t = keys + (int64_t)m * NP;
+  int lo = 0, len = n;
+  while (len > 0) {
+    const int half = len >> 1;
+    if ((uint32_t)(t[lo + half] >> 32) < (uint32_t)v) { lo += half + 1; len -= half + 1; } else { len = half; }
+  }
+  OFF[(int64_t)m * (kCells + 1) + v] = (uint32_t)lo;
+}
+
 }  // namespace
 
 // Ascending sort of nseg segments of NP keys each (NP a power of two >= 2048),
@@ -257,10 +330,22 @@ cudaError_t launch_index_build(Index& ix, cudaStream_t s) {
     const int64_t tot = (int64_t)n * K;
     k_codes<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(ix.P, ix.E, n, K, ix.Kp, code);
   }
+  // the pair order of every key (Sec. 3.3's sorted lists refined by a second
+  // key's bucket code): its reference ids, cell offsets and filter codes
+  k_partners<<<(K + 63) / 64, 64, 0, s>>>(ix.KP, K, D, ix.pair_scan ? 0 : 1, ix.partner);
+  e = cudaMallocAsync((void**)&keys, sizeof(unsigned long long) * (size_t)NP * K, s);
+  if (e != cudaSuccess) return e;
+  k_make_pair_keys<<<dim3((NP + 255) / 256, K), 256, 0, s>>>(code, ix.Tid, ix.partner, n, K, NP, keys);
+  e = sort_segments(keys, NP, K, s);
+  if (e != cudaSuccess) return e;
+  k_pair_split<<<dim3((n + 255) / 256, K), 256, 0, s>>>(keys, ix.Tid, n, NP, ix.Tid2);
+  k_pair_offsets<<<dim3((kPairCodes * kPairCodes + 1 + 255) / 256, K), 256, 0, s>>>(keys, n, NP, ix.OFF);
+  e = cudaFreeAsync(keys, s);
+  if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(ix.CW, 0, sizeof(uint32_t) * (size_t)K * ix.G * ix.nw, s);
   if (e != cudaSuccess) return e;
-  k_pack_codes<<<dim3((n + 255) / 256, K), 256, 0, s>>>(ix.Tid, code, n, K, ix.G, ix.nw, ix.CW);
-  k_pack_entry_codes<<<dim3((unsigned)(((int64_t)n * ix.Ke + 255) / 256), K), 256, 0, s>>>(ix.Tid, code, n, K,
+  k_pack_codes<<<dim3((n + 255) / 256, K), 256, 0, s>>>(ix.Tid2, code, n, K, ix.G, ix.nw, ix.CW);
+  k_pack_entry_codes<<<dim3((unsigned)(((int64_t)n * ix.Ke + 255) / 256), K), 256, 0, s>>>(ix.Tid2, code, n, K,
                                                                                           ix.Ke, ix.CE);
   e = cudaFreeAsync(code, s);
   if (e != cudaSuccess) return e;

@@ -186,7 +186,7 @@ __device__ __forceinline__ void knn_merge(unsigned long long& list, unsigned lon
 
 constexpr int kQueueA = 256;  // per-warp ring buffers of the filter cascade (powers of two)
 constexpr int kQueueC = 64;
-constexpr int kRowBatch = 4;  // 16-byte words of a distance row loaded per round (4 keys each)
+constexpr int kMaxRuns = kPairCodes;   // runs of one query: one per 7-bit seed bucket
 
 // One CTA per tile of TY x TX query positions; the grid is one frame's tiles.
 // Single-frame launch (BATCH = false): the frame's descriptor is a kernel
@@ -220,8 +220,16 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   __shared__ uint4 s_gd[kWarps][kMaxG];
   __shared__ __align__(16) uint32_t s_klo[kWarps][kMaxG];   // the same ranges in key order
   __shared__ __align__(16) uint32_t s_khi[kWarps][kMaxG];
-  __shared__ int32_t s_qa[kWarps][kQueueA];       // filter queues: seed-run positions after stage A,
-  __shared__ int32_t s_qc[kWarps][kQueueC];       // reference ids after stage B
+  __shared__ __align__(16) uint32_t s_kil[kWarps][kMaxG];   // interiors: packed lo + 1 and hi
+  __shared__ __align__(16) uint32_t s_kih[kWarps][kMaxG];
+  __shared__ int32_t s_partner[kMaxK];            // scan partner of each key
+  __shared__ uint32_t s_rs[kWarps][kMaxRuns];     // the query's runs in the seed's pair order: first position,
+  __shared__ uint32_t s_rl[kWarps][kMaxRuns];     // and length
+  __shared__ int32_t s_qa[kWarps][kQueueA];       // filter queues: run positions after stage A,
+  __shared__ int32_t s_qc[kWarps][kQueueC];       // reference ids after stage B,
+  __shared__ uint16_t s_qm[kWarps][kQueueC];      // and the words of their boundary codes
+  __shared__ uint16_t s_pr[kWarps][32 * kMaxG];   // stage D: (entry, word) pairs of a batch
+  __shared__ uint32_t s_fail[kWarps];             // stage D: entries with a failed word
   __shared__ __align__(16) uint32_t s_q[kWarps][NW];   // the warp's query patch
   __shared__ int32_t s_dense[TY * TX];
   __shared__ __align__(16) float s_qf[UNIT ? kWarps : 1][UNIT ? D : 4];   // UNIT: the normalised query
@@ -234,8 +242,10 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     const uint32_t* kp = reinterpret_cast<const uint32_t*>(a.KP);
     for (int i = threadIdx.x; i < K * NW; i += blockDim.x) s_kp[(i / NW) * KPW + (i % NW)] = kp[i];
     for (int i = threadIdx.x; i < K * 64; i += blockDim.x) s_coarse[i >> 6][i & 63] = __ldg(a.E + (i >> 6) * kBuckets + 4 * (i & 63));
+    for (int i = threadIdx.x; i < K; i += blockDim.x) s_partner[i] = __ldg(a.partner + i);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;          // lanes below this one
   const uint32_t p2 = (uint32_t)(a.alpha_num * a.alpha_num);
   const uint32_t q2 = (uint32_t)(a.alpha_den * a.alpha_den);
   const float alpha = (float)a.alpha_num / (float)a.alpha_den;
@@ -338,7 +348,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     // bucket codes, and bucket-granular bounds lb <= |Ring_m| <= ub.
     const float sC = (float)Cd;
     unsigned long long seedkey = ~0ull;
-#pragma unroll
+#pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       const int m = lane + 32 * h;
       if (m < K) {
@@ -386,93 +396,170 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     int ms = (int)(seedkey & 0xffffffffu);
     __syncwarp();
 
-    // exact run of the seed ring in its sorted list (the whole warp searches)
-    int2 run = ring_run(a.TA + (int64_t)ms * n, a.RB + ms * (kBuckets + 1), s_clo[warp][ms],
-                        s_chi[warp][ms], s_lw[warp][2 * ms], s_lw[warp][2 * ms] + s_lw[warp][2 * ms + 1], lane);
-
     // routing: brute force iff every ring holds more than ring_limit
-    // references.  Settled by the seed ring's exact size when it is within
-    // the limit; otherwise by bucket-granular bounds on every ring (first ranks
-    // of the buckets, RB) and exact sizes of the rings whose bounds straddle
-    // it -- the ring that settles it becomes the seed.
-    if (a.ring_limit >= 0 && (uint32_t)(run.y - run.x) > (uint32_t)a.ring_limit) {
-      unsigned long long ubkey = ~0ull;            // smallest upper bound over the other rings
-      unsigned straddle[2];                        // rings whose bounds straddle the limit, per half
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int m = lane + 32 * h;
-        bool mine = false;
-        if (m < K && m != ms) {
-          const int clo = s_clo[warp][m], chi = s_chi[warp][m];
-          const uint32_t* rb = a.RB + m * (kBuckets + 1);
-          const uint32_t ub = __ldg(rb + chi + 1) - (clo < 0 ? 0u : __ldg(rb + clo));
-          const uint32_t lb = chi > clo + 1 ? __ldg(rb + chi) - __ldg(rb + clo + 1) : 0u;
-          const unsigned long long k2 = ((unsigned long long)ub << 32) | (unsigned)m;
-          ubkey = k2 < ubkey ? k2 : ubkey;
-          mine = ub > (uint32_t)a.ring_limit && lb <= (uint32_t)a.ring_limit;
+    // references.  Settled at once when the seed's bucket-granular upper bound
+    // (first ranks of the buckets, RB) is within the limit; else by the seed
+    // ring's exact size (its run in TA, counted by the whole warp), then by
+    // the bounds of every ring and exact sizes of the rings whose bounds
+    // straddle the limit -- the ring that settles it becomes the seed.
+    if (a.ring_limit >= 0) {
+      const int sclo = s_clo[warp][ms], schi = s_chi[warp][ms];
+      const uint32_t* rbs = a.RB + ms * (kBuckets + 1);
+      const uint32_t ubs = __ldg(rbs + schi + 1) - (sclo < 0 ? 0u : __ldg(rbs + sclo));
+      bool found = ubs <= (uint32_t)a.ring_limit;
+      // rings counted exactly, in order: the seed, then (unless some ring is
+      // certainly within the limit) every ring whose bounds straddle it
+      int cand = found ? -1 : ms;
+      bool first = true;
+      unsigned todo0 = 0u, todo1 = 0u;
+      while (cand >= 0) {
+        const int2 rr = ring_run(a.TA + (int64_t)cand * n, a.RB + cand * (kBuckets + 1), s_clo[warp][cand],
+                                 s_chi[warp][cand], s_lw[warp][2 * cand],
+                                 s_lw[warp][2 * cand] + s_lw[warp][2 * cand + 1], lane);
+        if ((uint32_t)(rr.y - rr.x) <= (uint32_t)a.ring_limit) {
+          found = true;
+          ms = cand;
+          break;
         }
-        straddle[h] = __ballot_sync(kFull, mine);
-      }
+        if (first) {
+          first = false;
+          unsigned long long ubkey = ~0ull;          // smallest upper bound over the other rings
+#pragma unroll 1
+          for (int h = 0; h < 2; ++h) {
+            const int m = lane + 32 * h;
+            bool mine = false;
+            if (m < K && m != ms) {
+              const int clo = s_clo[warp][m], chi = s_chi[warp][m];
+              const uint32_t* rb = a.RB + m * (kBuckets + 1);
+              const uint32_t ub = __ldg(rb + chi + 1) - (clo < 0 ? 0u : __ldg(rb + clo));
+              const uint32_t lb = chi > clo + 1 ? __ldg(rb + chi) - __ldg(rb + clo + 1) : 0u;
+              const unsigned long long k2 = ((unsigned long long)ub << 32) | (unsigned)m;
+              ubkey = k2 < ubkey ? k2 : ubkey;
+              mine = ub > (uint32_t)a.ring_limit && lb <= (uint32_t)a.ring_limit;
+            }
+            const unsigned bal = __ballot_sync(kFull, mine);
+            if (h == 0) todo0 = bal; else todo1 = bal;
+          }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long v = __shfl_xor_sync(kFull, ubkey, o);
-        ubkey = v < ubkey ? v : ubkey;
-      }
-      bool found = false;
-      if ((uint32_t)(ubkey >> 32) <= (uint32_t)a.ring_limit) {   // a ring certainly within the limit
-        ms = (int)(ubkey & 0xffffffffu);
-        run = ring_run(a.TA + (int64_t)ms * n, a.RB + ms * (kBuckets + 1), s_clo[warp][ms], s_chi[warp][ms],
-                       s_lw[warp][2 * ms], s_lw[warp][2 * ms] + s_lw[warp][2 * ms + 1], lane);
-        found = true;
-      }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        unsigned todo = straddle[h];
-        while (todo && !found) {
-          const int m = __ffs(todo) - 1 + 32 * h;
-          todo &= todo - 1;
-          const int2 r2 = ring_run(a.TA + (int64_t)m * n, a.RB + m * (kBuckets + 1), s_clo[warp][m],
-                                   s_chi[warp][m], s_lw[warp][2 * m], s_lw[warp][2 * m] + s_lw[warp][2 * m + 1], lane);
-          if ((uint32_t)(r2.y - r2.x) <= (uint32_t)a.ring_limit) {
+          for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long v = __shfl_xor_sync(kFull, ubkey, o);
+            ubkey = v < ubkey ? v : ubkey;
+          }
+          if ((uint32_t)(ubkey >> 32) <= (uint32_t)a.ring_limit) {   // a ring certainly within the limit
+            ms = (int)(ubkey & 0xffffffffu);
             found = true;
-            ms = m;
-            run = r2;
+            break;
           }
         }
+        cand = todo0 ? __ffs(todo0) - 1 : (todo1 ? __ffs(todo1) - 1 + 32 : -1);
+        if (todo0) todo0 &= todo0 - 1; else todo1 &= todo1 - 1;
       }
       if (!found) {
         if (lane == 0) s_dense[atomicAdd(&s_ndense, 1)] = (int32_t)(it.query_begin + qi);
         continue;
       }
     }
-    const int jlo = run.x, jhi = run.y;
 
+    // a3: the runs the scan visits.  In the pair order of the seed ms (its
+    // references sorted by the cells (code7_ms, code7_pm), pm its partner key,
+    // each cell in the order of the seed's sorted list), every seed bucket b
+    // of the seed ring's 7-bit code range holds one contiguous run of the
+    // references whose partner code lies in the partner ring's range: run b =
+    // [OFF(b, cl), OFF(b, ch + 1)); adjacent runs are merged.  The runs cover
+    // every member of both rings (and more: the code ranges are supersets).
+    // A seed paired with itself keeps its sorted list's order, and the scan
+    // visits the seed ring's exact run in it.  An empty ring leaves no run:
+    // S is empty.
+    const int pm = s_partner[ms];
+    int nruns = 0;
+    uint32_t scanned = 0;
+    {
+      const int sclo = s_clo[warp][ms], schi = s_chi[warp][ms];
+      const int pclo = s_clo[warp][pm], pchi = s_chi[warp][pm];
+      if (pm == ms) {
+        const int2 run = ring_run(a.TA + (int64_t)ms * n, a.RB + ms * (kBuckets + 1), sclo, schi,
+                                  s_lw[warp][2 * ms], s_lw[warp][2 * ms] + s_lw[warp][2 * ms + 1], lane);
+        if (run.y > run.x) {
+          nruns = 1;
+          scanned = (uint32_t)(run.y - run.x);
+          if (lane == 0) {
+            s_rs[warp][0] = (uint32_t)run.x;
+            s_rl[warp][0] = scanned;
+          }
+        }
+      } else if (schi >= 0 && pchi >= 0) {
+        const int bl = (sclo < 0 ? 0 : sclo) >> 1, bh = schi >> 1;
+        const int cl = (pclo < 0 ? 0 : pclo) >> 1, ch = pchi >> 1;
+        const int nb = bh - bl + 1;
+        const uint32_t* off = a.OFF + (int64_t)ms * (kPairCodes * kPairCodes + 1);
+        for (int b0 = 0; b0 < nb; b0 += 32) {
+          // one bucket per lane; a run that starts where the lower lane's
+          // ends continues it, and a head's run ends with the last lane
+          // below the next head
+          const bool v = b0 + lane < nb;
+          uint32_t st = 0, en = 0;
+          if (v) {
+            const uint32_t* ob = off + (bl + b0 + lane) * kPairCodes;
+            st = __ldg(ob + cl);
+            en = __ldg(ob + ch + 1);
+          }
+          const uint32_t pen = __shfl_up_sync(kFull, en, 1);
+          const bool head = v && (lane == 0 || st != pen);
+          const unsigned hm = __ballot_sync(kFull, head), vm = __ballot_sync(kFull, v);
+          const unsigned above = hm & ~((2u << lane) - 1u);
+          const int last = above ? __ffs(above) - 2 : 31 - __clz(vm);
+          const uint32_t send = __shfl_sync(kFull, en, last);
+          if (head) {
+            const int k = nruns + __popc(hm & lt);
+            s_rs[warp][k] = st;
+            s_rl[warp][k] = send - st;
+          }
+          nruns += __popc(hm);
+          scanned += v ? en - st : 0u;
+        }
+        scanned = __reduce_add_sync(kFull, scanned);
+      }
+    }
     // per group of 4 keys: the 7-bit code ranges of its rings (filter codes
     // are 0x80 | code7 with code7 = code >> 1, see index_build.cu), packed one
-    // byte per key as lo and hi + 1 (keys that always pass -- the seed,
-    // padding -- take [0, 127]; an empty ring takes lo = hi + 1 = 1, which no
-    // code meets), and an estimate of the fraction of references passing
+    // byte per key as lo and hi + 1 (keys that always pass -- the seed and its
+    // partner, whose ranges the runs already meet, and padding -- take [0, 127];
+    // an empty ring takes lo = hi + 1 = 1, which no code meets), and an
+    // estimate of the fraction of references passing
     // (product over its keys of the fraction of buckets each ring touches)
     float est = 2.f;
-    uint32_t glo = 0, ghi = 0;
+    uint32_t glo = 0, ghi = 0;                     // the scan's ranges (seed and partner always pass)
+    uint32_t elo = 0, ehi = 0, ilo = 0, ihi = 0;   // every ring's range, and its interior (see below)
     if (lane < G) {
       est = 1.f;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const int k = 4 * lane + i;
-        uint32_t l = 0, h1 = 128;
-        if (k < K && k != ms) {
+        uint32_t l = 0, h1 = 128, l1 = 0, h0 = 128;
+        if (k < K) {
           const int clo = s_clo[warp][k], chi = s_chi[warp][k];
           if (chi < 0) {
             l = h1 = 1;
           } else {
             l = (uint32_t)(clo < 0 ? 0 : clo) >> 1;
             h1 = ((uint32_t)chi >> 1) + 1;
+            l1 = l + 1;
+            h0 = h1 - 1;
           }
-          est *= (float)s_ub[warp][k] * (1.f / kBuckets);   // fraction of buckets the ring touches
         }
-        glo |= l << (8 * i);
-        ghi |= h1 << (8 * i);
+        // a code strictly inside its ring's code range (l < c < hi) lies in
+        // a bucket entirely inside the ring: only the others need the exact test
+        elo |= l << (8 * i);
+        ehi |= h1 << (8 * i);
+        ilo |= l1 << (8 * i);
+        ihi |= h0 << (8 * i);
+        if (k < K && k != ms && k != pm) {
+          est *= (float)s_ub[warp][k] * (1.f / kBuckets);   // fraction of buckets the ring touches
+          glo |= l << (8 * i);
+          ghi |= h1 << (8 * i);
+        } else {
+          ghi |= 128u << (8 * i);
+        }
       }
     }
     {
@@ -484,92 +571,120 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         rank += (e2 < est) || (e2 == est && g2 < lane);
       }
       if (lane < G) s_gd[warp][rank] = make_uint4((uint32_t)(lane * a.nw), glo, ghi, 0u);
-      // in key order for the entry rows (padding groups of a row always pass)
+      // in key order for the entry rows (padding groups of a row always pass
+      // and are interior)
       if (lane < (a.Ke >> 2)) {
-        s_klo[warp][lane] = lane < G ? glo : 0u;
-        s_khi[warp][lane] = lane < G ? ghi : kHi;
+        s_klo[warp][lane] = lane < G ? elo : 0u;
+        s_khi[warp][lane] = lane < G ? ehi : kHi;
+        s_kil[warp][lane] = lane < G ? ilo : 0u;
+        s_kih[warp][lane] = lane < G ? ihi : kHi;
       }
     }
     __syncwarp();
 
-    // a3 + a4, a cascade of filters over the seed ring's run; each stage
-    // compacts its survivors into a per-warp queue (warp prefix sums and
-    // ballots), so that the next, costlier stage runs on full batches of 32:
-    //   A  each lane tests 4 consecutive run entries against the codes of the
-    //      ns1 most selective groups (co-sorted rows of CW: one 16-byte load
-    //      per group, the first three prefetched a chunk ahead);
-    //   B  one queued entry per lane: its reference id (Tid) and the codes of
-    //      every key (its row of CE, one 16-byte load per 16 keys);
-    //   D  one queued reference per lane: the exact test of its key-distance
-    //      row against every ring, lo_m <= A_m <= hi_m as one unsigned compare
-    //      (A_m - lo_m <= hi_m - lo_m), and verification of the members
-    //      against the query.
+    // a3 + a4, a cascade of filters over the runs; each stage compacts its
+    // survivors into a per-warp queue (warp ballots), so that the next,
+    // costlier stage runs on full batches of 32:
+    //   A  128 run positions per step, 4 consecutive ones per lane, against
+    //      the codes of the ns1 most selective groups (rows of CW: one 16-byte
+    //      load per group, the first three prefetched a chunk ahead);
+    //   B  one queued position per lane: its reference id (Tid2) and the
+    //      codes of every key (its row of CE, one 16-byte load per 16 keys);
+    //   D  one queued reference per lane: the exact test, lo_m <= A_m <= hi_m
+    //      as one unsigned compare (A_m - lo_m <= hi_m - lo_m), of the keys
+    //      whose codes B found on a boundary of their range (a 4-key word of
+    //      the distance row each, spread over the warp's lanes), and
+    //      verification of the members against the query.
     // A code range is a superset of its ring, so only D decides membership.
     // A deeper stage runs first whenever it holds a full batch, which bounds
-    // the queues (A: < 32 + 128 entries, B: < 64).
+    // the queues (A: < 32 + 128 entries, C: < 64).
     // (k-NN: the same start -- r_p on lane 0 -- is the warp's best-k list)
     unsigned long long best = lane == 0 ? (((unsigned long long)Cd << 32) | (unsigned)rp) : ~0ull;
     uint32_t cnt = 0;
     const uint32_t* cw = a.CW + (int64_t)ms * G * a.nw;
-    const int32_t* tid = a.Tid + (int64_t)ms * n;
+    const int32_t* tid = a.Tid2 + (int64_t)ms * n;
     const uint8_t* ce = a.CE + (int64_t)ms * n * a.Ke;
     const int kc = a.Ke >> 4;                      // 16-byte words per entry row of CE
     const int ns1 = G < a.depth ? G : a.depth;
     const uint4* gd = s_gd[warp];
+    const uint4* prow = reinterpret_cast<const uint4*>(a.P);
+    const int kq = a.Kp >> 2;                      // 16-byte words per distance row
+    const uint4* lw4 = reinterpret_cast<const uint4*>(s_lw[warp]);
+    const uint4* klo4 = reinterpret_cast<const uint4*>(s_klo[warp]);
+    const uint4* khi4 = reinterpret_cast<const uint4*>(s_khi[warp]);
+    const uint4* kil4 = reinterpret_cast<const uint4*>(s_kil[warp]);
+    const uint4* kih4 = reinterpret_cast<const uint4*>(s_kih[warp]);
+    const uint32_t* rs = s_rs[warp];
+    const uint32_t* rl = s_rl[warp];
+    int32_t* qa = s_qa[warp];
+    int32_t* qc = s_qc[warp];
+    uint16_t* qm = s_qm[warp];
+    int ha = 0, na = 0, hc = 0, nc = 0;            // queue heads and lengths
+
+    // scan position (warp-uniform): run ri, 4-aligned chunk start base in
+    // it; the current chunk's codes a0..a2 (4 positions per lane: base +
+    // 4 lane .. + 3), the next chunk prefetched during the current one's test
+    int ri = 0;
+    while (ri < nruns && rl[ri] == 0u) ++ri;
+    int base = ri < nruns ? (int)(rs[ri] & ~3u) : 0;
     const uint4 d0 = gd[0];
     const uint4 d1 = gd[ns1 > 1 ? 1 : 0];
     const uint4 d2 = gd[ns1 > 2 ? 2 : 0];
     const uint4* cw0 = reinterpret_cast<const uint4*>(cw + d0.x);
     const uint4* cw1 = reinterpret_cast<const uint4*>(cw + d1.x);
     const uint4* cw2 = reinterpret_cast<const uint4*>(cw + d2.x);
-    const uint4* prow = reinterpret_cast<const uint4*>(a.P);
-    const int kq = a.Kp >> 2;                      // 16-byte words per distance row
-    const uint4* lw4 = reinterpret_cast<const uint4*>(s_lw[warp]);
-    const uint4* klo4 = reinterpret_cast<const uint4*>(s_klo[warp]);
-    const uint4* khi4 = reinterpret_cast<const uint4*>(s_khi[warp]);
-    int32_t* qa = s_qa[warp];
-    int32_t* qc = s_qc[warp];
-    int ha = 0, na = 0, hc = 0, nc = 0;            // queue heads and lengths
-    const unsigned lt = (1u << lane) - 1u;
-
-    const int ja = jlo & ~3;
     uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, a2 = a0;
-    if (ja + 4 * lane < jhi) {
-      a0 = __ldg(cw0 + (ja >> 2) + lane);
-      if (ns1 > 1) a1 = __ldg(cw1 + (ja >> 2) + lane);
-      if (ns1 > 2) a2 = __ldg(cw2 + (ja >> 2) + lane);
+    if (ri < nruns && (uint32_t)(base + 4 * lane) < rs[ri] + rl[ri]) {
+      a0 = __ldg(cw0 + (base >> 2) + lane);
+      if (ns1 > 1) a1 = __ldg(cw1 + (base >> 2) + lane);
+      if (ns1 > 2) a2 = __ldg(cw2 + (base >> 2) + lane);
     }
-    int base = ja;
     for (;;) {
-      const bool done = base >= jhi;
+      const bool done = ri >= nruns;
       if (nc >= 32 || (done && nc > 0)) {
-        // ---- D: exact row test and verification ----
+        // ---- D: exact test of the boundary words, and verification ----
+        // Entry e (lane e) needs the exact key distances only of the words
+        // in its mask.  The warp spreads its (entry, word) pairs over the
+        // lanes -- a lane's pairs after the sum of the lower lanes' counts,
+        // from ballots of the counts' five bits -- loads each pair's 16-byte
+        // word of the distance row and records a failed word in s_fail.
         const int take = nc < 32 ? nc : 32;
         bool alive = lane < take;
-        const int r = alive ? qc[(hc + lane) & (kQueueC - 1)] : 0;
+        const int slot = (hc + lane) & (kQueueC - 1);
+        const int r = alive ? qc[slot] : 0;
+        uint32_t mk = alive ? (uint32_t)qm[slot] : 0u;
         hc = (hc + take) & (kQueueC - 1);
         nc -= take;
-        if (alive) {
-          const uint4* row = prow + (int64_t)r * kq;
-          // kRowBatch 4-key words per round of loads; a lane stops at its
-          // first failed round
-#pragma unroll 1
-          for (int h = 0; h < kq && alive; h += kRowBatch) {
-            uint4 v[kRowBatch];
+        const uint32_t pc = (uint32_t)__popc(mk);
+        int ppos = 0, ptot = 0;
 #pragma unroll
-            for (int c = 0; c < kRowBatch; ++c) v[c] = h + c < kq ? __ldg(row + h + c) : make_uint4(0, 0, 0, 0);
-            unsigned ok = 1u;
-#pragma unroll
-            for (int c = 0; c < kRowBatch; ++c) {
-              if (h + c < kq) {
-                const uint4 l0 = lw4[2 * (h + c)], l1 = lw4[2 * (h + c) + 1];
-                ok &= (unsigned)(v[c].x - l0.x <= l0.y) & (unsigned)(v[c].y - l0.z <= l0.w) &
-                      (unsigned)(v[c].z - l1.x <= l1.y) & (unsigned)(v[c].w - l1.z <= l1.w);
-              }
-            }
-            alive = ok != 0u;
+        for (int bt = 0; bt < 5; ++bt) {
+          const unsigned bb = __ballot_sync(kFull, (pc >> bt) & 1u);
+          ppos += __popc(bb & lt) << bt;
+          ptot += __popc(bb) << bt;
+        }
+        uint16_t* pr = s_pr[warp];
+        while (mk) {
+          pr[ppos++] = (uint16_t)((lane << 4) | (__ffs(mk) - 1));
+          mk &= mk - 1;
+        }
+        if (lane == 0) s_fail[warp] = 0u;
+        __syncwarp();
+        for (int p0 = 0; p0 < ptot; p0 += 32) {
+          const int k1 = p0 + lane;
+          const uint32_t e1 = k1 < ptot ? pr[k1] : 0u;
+          const int r1 = __shfl_sync(kFull, r, (int)(e1 >> 4));
+          if (k1 < ptot) {
+            const uint4 v1 = __ldg(prow + (int64_t)r1 * kq + (e1 & 15u));
+            const uint4 l0 = lw4[2 * (e1 & 15u)], l1 = lw4[2 * (e1 & 15u) + 1];
+            const bool okw = (v1.x - l0.x <= l0.y) && (v1.y - l0.z <= l0.w) && (v1.z - l1.x <= l1.y) &&
+                             (v1.w - l1.z <= l1.w);
+            if (!okw) atomicOr(&s_fail[warp], 1u << (e1 >> 4));
           }
         }
+        __syncwarp();
+        alive = alive && ((s_fail[warp] >> lane) & 1u) == 0u;
+        __syncwarp();
         unsigned long long key = ~0ull;
         if (alive) {
           ++cnt;
@@ -597,27 +712,42 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         na -= take;
         const int r = on ? __ldg(tid + j) : 0;
         const uint4* er = reinterpret_cast<const uint4*>(ce + (int64_t)j * a.Ke);
-        uint32_t pass = kHi;
+        uint32_t pass = kHi, bmask = 0;            // bmask: words of the entry with a boundary code
 #pragma unroll
         for (int c = 0; c < kMaxK / 16; ++c) {
           if (c < kc) {
             const uint4 w = on ? __ldg(er + c) : make_uint4(kHi, kHi, kHi, kHi);
-            const uint4 l = klo4[c], h = khi4[c];
+            const uint4 l = klo4[c], h = khi4[c], il = kil4[c], ih = kih4[c];
             pass &= (w.x - l.x) & ~(w.x - h.x) & (w.y - l.y) & ~(w.y - h.y);
             pass &= (w.z - l.z) & ~(w.z - h.z) & (w.w - l.w) & ~(w.w - h.w);
+            bmask |= ((((w.x - il.x) & ~(w.x - ih.x) & kHi) != kHi) ? 1u : 0u) << (4 * c);
+            bmask |= ((((w.y - il.y) & ~(w.y - ih.y) & kHi) != kHi) ? 2u : 0u) << (4 * c);
+            bmask |= ((((w.z - il.z) & ~(w.z - ih.z) & kHi) != kHi) ? 4u : 0u) << (4 * c);
+            bmask |= ((((w.w - il.w) & ~(w.w - ih.w) & kHi) != kHi) ? 8u : 0u) << (4 * c);
           }
         }
         const bool ok = on && (pass & kHi) == kHi;
         const unsigned m = __ballot_sync(kFull, ok);
-        if (ok) qc[(hc + nc + __popc(m & lt)) & (kQueueC - 1)] = r;
+        if (ok) {
+          const int slot = (hc + nc + __popc(m & lt)) & (kQueueC - 1);
+          qc[slot] = r;
+          qm[slot] = (uint16_t)bmask;
+        }
         nc += __popc(m);
         continue;
       }
       if (done) break;
-      // ---- A: the next chunk of 128 run entries against the first groups ----
+      // ---- A: the chunk of 128 positions at base of run ri ----
+      const int st = (int)rs[ri], en = st + (int)rl[ri];
+      int ri2 = ri, base2 = base + 128;
+      if (base2 >= en) {                           // the next non-empty run
+        ++ri2;
+        while (ri2 < nruns && rl[ri2] == 0u) ++ri2;
+        base2 = ri2 < nruns ? (int)(rs[ri2] & ~3u) : 0;
+      }
       uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0, b2 = b0;
-      if (base + 128 + 4 * lane < jhi) {
-        const int o = ((base + 128) >> 2) + lane;
+      if (ri2 < nruns && (uint32_t)(base2 + 4 * lane) < rs[ri2] + rl[ri2]) {
+        const int o = (base2 >> 2) + lane;
         b0 = __ldg(cw0 + o);
         if (ns1 > 1) b1 = __ldg(cw1 + o);
         if (ns1 > 2) b2 = __ldg(cw2 + o);
@@ -634,41 +764,27 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         if (ns1 > 2) p &= (v2[u] - d2.y) & ~(v2[u] - d2.z);
         bits |= ((p & kHi) == kHi ? 1u : 0u) << u;
       }
-      // only the first and the last chunk hold entries outside [jlo, jhi)
-      // (a warp-uniform test: the middle chunks skip the range check)
-      if (base < jlo || base + 128 > jhi) {
+      // only a run's first and last chunk hold positions outside it (a
+      // warp-uniform test: the middle chunks skip the range check)
+      if (base < st || base + 128 > en) {
         unsigned inr = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) inr |= (j0 + u >= jlo && j0 + u < jhi ? 1u : 0u) << u;
+        for (int u = 0; u < 4; ++u) inr |= (j0 + u >= st && j0 + u < en ? 1u : 0u) << u;
         bits &= inr;
-      }
-      // depth 4..5: the next groups, one 16-byte load per lane for its four
-      // entries, only while some entry of the warp is still alive
-      for (int oi = 3; oi < ns1; ++oi) {
-        if (!__any_sync(kFull, bits != 0)) break;
-        if (bits) {
-          const uint4 g = gd[oi];
-          const uint4 wv4 = __ldg(reinterpret_cast<const uint4*>(cw + g.x) + (j0 >> 2));
-          const uint32_t vg[4] = {wv4.x, wv4.y, wv4.z, wv4.w};
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if ((((vg[u] - g.y) & ~(vg[u] - g.z) & kHi) != kHi)) bits &= ~(1u << u);
-        }
       }
       a0 = b0;
       a1 = b1;
       a2 = b2;
-      base += 128;
-      // warp prefix sum of survivor counts -> append to queue A
-      const int c = __popc(bits);
-      int pre = c;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(kFull, pre, o);
-        if (lane >= o) pre += v;
-      }
-      const int tot = __shfl_sync(kFull, pre, 31);
-      pre -= c;
+      ri = ri2;
+      base = base2;
+      // append the survivors to queue A: a lane's offset is the sum of the
+      // survivor counts (0..4) of the lanes below it, from ballots of the
+      // counts' three bits
+      const unsigned c = (unsigned)__popc(bits);
+      const unsigned c0 = __ballot_sync(kFull, c & 1u), c1 = __ballot_sync(kFull, c & 2u),
+                     c2 = __ballot_sync(kFull, c & 4u);
+      const int pre = __popc(c0 & lt) + 2 * __popc(c1 & lt) + 4 * __popc(c2 & lt);
+      const int tot = __popc(c0) + 2 * __popc(c1) + 4 * __popc(c2);
       int slot = ha + na + pre;
 #pragma unroll
       for (int u = 0; u < 4; ++u)
@@ -696,7 +812,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       if (it.out_count) it.out_count[qi] = cnt;
       if (a.stats) {
         atomicAdd(&s_stat[0], 1ull);
-        atomicAdd(&s_stat[1], (unsigned long long)(jhi - jlo));
+        atomicAdd(&s_stat[1], (unsigned long long)scanned);
         atomicAdd(&s_stat[2], (unsigned long long)cnt);
       }
     }

@@ -34,6 +34,9 @@ RIANN_ERR_TOO_LARGE = 8
 RIANN_DEV_BAD_PREV = 0x1
 RIANN_DEV_BOUNDS = 0x2
 RIANN_DEV_TIMEOUT = 0x4
+RIANN_SCAN_AUTO = 0
+RIANN_SCAN_PAIRS = 1
+RIANN_SCAN_SINGLE = 2
 
 
 class riann_params(ctypes.Structure):
@@ -85,6 +88,7 @@ _lib.riann_strerror.argtypes = [ctypes.c_int]
 _lib.riann_strerror.restype = ctypes.c_char_p
 _lib.riann_build_reference_index.argtypes = [_P, _i32, _i32, _P, _i32, _P, ctypes.POINTER(_P)]
 _lib.riann_build_unit_index.argtypes = [_P, _i32, _i32, _P, _i32, _P, ctypes.POINTER(_P)]
+_lib.riann_build_reference_index_ex.argtypes = [_P, _i32, _i32, _P, _i32, _i32, _P, ctypes.POINTER(_P)]
 _lib.riann_index_destroy.argtypes = [_P]
 _lib.riann_index_destroy.restype = None
 _lib.riann_index_info.argtypes = [_P, ctypes.POINTER(riann_index_info_t)]
@@ -226,9 +230,11 @@ class RiannIndex:
 
 
 def riann_build_reference_index(patches: torch.Tensor, keypoints: torch.Tensor,
-                                stream: Optional[torch.cuda.Stream] = None, unit: bool = False) -> RiannIndex:
+                                stream: Optional[torch.cuda.Stream] = None, unit: bool = False,
+                                scan_order: Optional[int] = None) -> RiannIndex:
     """patches uint8 [n][8][8][C] and keypoints uint8 [K][8][8][C] on the GPU.
-    unit=True builds the unit-normalised float index (riann_build_unit_index)."""
+    unit=True builds the unit-normalised float index (riann_build_unit_index);
+    scan_order (RIANN_SCAN_*) calls riann_build_reference_index_ex."""
     if patches.dim() != 4 or patches.shape[1:3] != (8, 8):
         raise ValueError("patches must be [n][8][8][C]")
     n, C = patches.shape[0], patches.shape[3]
@@ -236,6 +242,14 @@ def riann_build_reference_index(patches: torch.Tensor, keypoints: torch.Tensor,
         raise ValueError("keypoints must be [K][8][8][C] with the patches' C")
     K = keypoints.shape[0]
     h = ctypes.c_void_p(0)
+    if scan_order is not None:
+        if unit:
+            raise ValueError("scan_order applies to the integer index")
+        _check(_lib.riann_build_reference_index_ex(_dev(patches, (torch.uint8,), "patches"), n, C,
+                                                   _dev(keypoints, (torch.uint8,), "keypoints"), K, int(scan_order),
+                                                   _stream(stream), ctypes.byref(h)),
+               "riann_build_reference_index_ex")
+        return RiannIndex(h.value, n, K, C)
     fn = _lib.riann_build_unit_index if unit else _lib.riann_build_reference_index
     _check(fn(_dev(patches, (torch.uint8,), "patches"), n, C, _dev(keypoints, (torch.uint8,), "keypoints"), K,
               _stream(stream), ctypes.byref(h)),

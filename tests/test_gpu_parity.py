@@ -42,8 +42,8 @@ def make_params(rt, n, alpha=(1, 4), ring_limit="default", cap=0):
     return p
 
 
-def gpu_chain(rt, R, KP, frames, params):
-    idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
+def gpu_chain(rt, R, KP, frames, params, scan_order=None):
+    idx = rt.riann_build_reference_index(_dev(R), _dev(KP), scan_order=scan_order)
     outs, prev = [], None
     for f in frames:
         a, d, c = rt.annf(idx, _dev(f), prev, params)
@@ -133,12 +133,15 @@ def tiny():
     return R, KP, frames
 
 
+@pytest.mark.parametrize("scan", ["auto", "pairs"])
 @pytest.mark.parametrize("alpha,limit", [((1, 4), "default"), ((1, 4), -1), ((1, 4), 0),
                                          ((1, 1), -1), ((0, 1), -1), ((3, 8), 64)])
-def test_tiny_chain_all_queries(rt, tiny, alpha, limit):
+def test_tiny_chain_all_queries(rt, tiny, alpha, limit, scan):
+    # "pairs": the scan of a second key's buckets, which the index uses for
+    # n >= 32768 only, forced on the tiny index
     R, KP, frames = tiny
     params = make_params(rt, len(R), alpha, limit)
-    g = gpu_chain(rt, R, KP, frames, params)
+    g = gpu_chain(rt, R, KP, frames, params, None if scan == "auto" else rt.RIANN_SCAN_PAIRS)
     o = oracle_chain(R, KP, frames, params)
     for t in range(len(frames)):
         assert_same(g[t], o[t], what=f"frame {t}")
@@ -147,7 +150,7 @@ def test_tiny_chain_all_queries(rt, tiny, alpha, limit):
 def test_cap_does_not_change_output(rt, tiny):
     R, KP, frames = tiny
     base = gpu_chain(rt, R, KP, frames[:3], make_params(rt, len(R)))
-    for cap in (1, 2, 3, 4, 5):
+    for cap in (1, 2, 3):
         other = gpu_chain(rt, R, KP, frames[:3], make_params(rt, len(R), cap=cap))
         for t in range(3):
             for k in range(3):
@@ -167,10 +170,11 @@ def test_cap_does_not_change_output(rt, tiny):
     (6001, 64, 1, 24, 90),    # n not a multiple of 4 with K = 64: long seed runs, many drains
 ])
 @pytest.mark.parametrize("alpha,limit", [((1, 4), -1), ((1, 2), 40), ((8, 1), -1)])
-def test_random_cases(rt, n, K, C, H, W, alpha, limit):
+@pytest.mark.parametrize("scan", [1, 2])
+def test_random_cases(rt, n, K, C, H, W, alpha, limit, scan):
     R, KP, frame, prev = synth.random_case(300 + n + K, n, K, C, H, W)
     params = make_params(rt, n, alpha, limit)
-    idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
+    idx = rt.riann_build_reference_index(_dev(R), _dev(KP), scan_order=scan)
     a, d, c = rt.annf(idx, _dev(frame), _dev(prev), params)
     assert rt.riann_status(idx) == 0
     oix = oracle.Index(R, KP)
@@ -200,7 +204,7 @@ def test_invalid_arguments_rejected(rt):
     idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
     out = torch.empty((5, 5), dtype=torch.int32, device="cuda")
     for bad in (dict(alpha_den=0), dict(alpha_den=9), dict(alpha_num=-1), dict(alpha_num=65, alpha_den=8),
-                dict(ring_limit=-2), dict(cap=-1)):
+                dict(ring_limit=-2), dict(cap=-1), dict(cap=4)):
         p = make_params(rt, 64)
         for k, v in bad.items():
             setattr(p, k, v)
@@ -213,18 +217,21 @@ def test_invalid_arguments_rejected(rt):
     idx.close()
     with pytest.raises(rt.RiannError):
         rt.riann_build_reference_index(_dev(R), _dev(np.zeros((65, 8, 8, 1), np.uint8)))
+    with pytest.raises(rt.RiannError) as e:
+        rt.riann_build_reference_index(_dev(R), _dev(KP), scan_order=3)
+    assert e.value.code == rt.RIANN_ERR_INVALID_ARG
 
 
 # ---------------------------------------------------------------------------
 # full-size workloads, sampled queries
 # ---------------------------------------------------------------------------
-def _sampled_chain(rt, w, t0, t1, nsamp, seed):
+def _sampled_chain(rt, w, t0, t1, nsamp, seed, scan_order=None):
     R = synth.workload_reference(w)
     KP = synth.workload_keypoints(w, R)
     video = synth.Video(w.video)
     frames = [video.frame(t) for t in range(t0, t1)]
     params = make_params(rt, len(R))
-    g = gpu_chain(rt, R, KP, frames, params)
+    g = gpu_chain(rt, R, KP, frames, params, scan_order)
     H, W = frames[0].shape[:2]
     Q = (H - 7) * (W - 7)
     rng = np.random.default_rng(seed)
@@ -237,6 +244,16 @@ def _sampled_chain(rt, w, t0, t1, nsamp, seed):
 
 def test_720p_rgb_full_frames_sampled(rt):
     _sampled_chain(rt, synth.WORKLOADS["720p_rgb"], 0, 3, 600, 21)
+
+
+def test_720p_rgb_pair_scan_sampled(rt):
+    # the pair scan (used for n >= 32768) forced on the 16384-patch RGB index
+    _sampled_chain(rt, synth.WORKLOADS["720p_rgb"], 0, 3, 600, 23, rt.RIANN_SCAN_PAIRS)
+
+
+def test_1080p_single_key_scan_sampled(rt):
+    # the single-key scan (used for n < 32768) forced on the 65536-patch index
+    _sampled_chain(rt, synth.WORKLOADS["1080p"], 20, 23, 400, 24, rt.RIANN_SCAN_SINGLE)
 
 
 def test_1080p_across_scene_cut_sampled(rt):
