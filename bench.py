@@ -87,10 +87,10 @@ def job_throughput(world: int, steps: int, queries_per_frame: int, job_ms: float
     return world * steps * queries_per_frame / (job_ms / 1000.0)
 
 
-def video_for_rank(rank: int) -> synth.Video:
-    """Rank r's stream: the workload's video with its seed moved by 1000 r
-    (rank 0 keeps the workload's own), so ranks share no frames."""
-    spec = WORKLOAD.video
+def video_for_rank(rank: int, spec=None) -> synth.Video:
+    """Rank r's stream: the workload's video (or `spec`) with its seed moved by
+    1000 r (rank 0 keeps the workload's own), so ranks share no frames."""
+    spec = spec or WORKLOAD.video
     if rank:
         spec = synth.VideoSpec(**{**spec.__dict__, "seed": spec.seed + 1000 * rank})
     return synth.Video(spec)
@@ -157,46 +157,78 @@ class ClockSampler:
 # algorithmic bytes of the ring-intersection kernel (per frame)
 # ---------------------------------------------------------------------------
 def ring_kernel_bytes(stats: dict, H: int, W: int, C: int, n: int, K: int) -> int:
-    """Bytes the ring-intersection step must touch for one frame.
+    """Algorithmic bytes of one frame's ring step, the terms of the scope
+    table's byte count (the filter term, an upper bound there, is left out):
 
-    frame read once + previous field + outputs (annf, dist, count) + per ring
-    query: the previous match's row (D), two binary searches of ceil(log2(n+1))
-    probes per ring (4 B each), one id and one distance per seed-ring entry
-    (8 B), and each candidate's row (D) for verification.
-    """
+    IO: the frame read once, the previous field and the three outputs
+    (C H W + 16 Q); verification: one D-byte row per member of S u {r_p} of
+    every ring query (D (|S| + 1)); ring search: two binary searches of
+    ceil(log2(n + 1)) 4-byte probes per ring for every query (Q 2K lg 4)."""
     D = 64 * C
     Q = (H - 7) * (W - 7)
     lg = int(np.ceil(np.log2(n + 1)))
     rq = stats["ring_queries"]
-    return int(C * H * W + 4 * Q + 12 * Q + rq * D + rq * 2 * K * lg * 4
-               + 8 * stats["sum_seed"] + D * stats["sum_candidates"])
+    return int(C * H * W + 16 * Q + D * (stats["sum_candidates"] + rq) + Q * 2 * K * lg * 4)
 
 
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# full-size ring launch, 1080p frame 21, from a one-pass ncu capture of the
-# ring-kernel sources with these SHA-256 digests; reported only while the
-# sources are unchanged.
-RING_TRAFFIC = {"bytes": 1.22e9 + 28.84e6, "frame": 21, "tile_shape": 0, "depth": 3,
-                "sha256": {"paper_1508_07953_gb300/csrc/sparse_query.cu":
-                           "5a4c926078d5cca273a533cdeb00fd45812358cebfa224269b6c59f03426eb88",
+def ring_verification_bytes(stats: dict, C: int) -> int:
+    """The verification part alone: one row per member of S u {r_p}."""
+    return int(64 * C * (stats["sum_candidates"] + stats["ring_queries"]))
+
+
+def ring_traffic_model(stats: dict, H: int, W: int, C: int, K: int, depth: int) -> int:
+    """Bytes the ring kernel as built gathers per frame (its own traffic model,
+    not the algorithmic count): IO; per ring query the previous match's row;
+    per scanned entry `depth` 4-byte code words; per entry past the scan its
+    reference id and its row of every key's codes; per entry past every code
+    range its reference row (the boundary words of its key-distance row are
+    not counted)."""
+    D = 64 * C
+    Q = (H - 7) * (W - 7)
+    Ke = (K + 15) // 16 * 16
+    return int(C * H * W + 16 * Q + D * stats["ring_queries"] + 4 * depth * stats["sum_seed"]
+               + (4 + Ke) * stats.get("sum_filtered", 0) + D * stats.get("sum_exact", 0))
+
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) and L2 traffic
+# (lts__t_bytes.sum) of one full-size ring launch, 1080p frame 21, from a
+# one-pass ncu capture of the sources with these SHA-256 digests; reported
+# only while the sources and the launch variant are the captured ones.
+RING_CAPTURE = {"dram_bytes": 4.01e9 + 30.04e6, "l2_bytes": 71.28e9, "frame": 21, "tile_shape": 0, "depth": 3,
+                "sha256": {
+                           "paper_1508_07953_gb300/csrc/sparse_query.cu":
+                           "05e27ab7aac58262d333b537b43299a5eff1a862df233764de83fa2c04f83492",
                            "paper_1508_07953_gb300/csrc/common.cuh":
-                           "8563a50c4b8285cfde95148a72ff6155ce87ca8cd2885344d04add2c6cd4c70b",
+                           "81b24fa55dd0359aae8f63fcb5d276b4c92bc7aaeba22ccdfd875167da06816f",
                            "paper_1508_07953_gb300/csrc/unit.cuh":
-                           "cf4a6e3000f7920ec4389b9067169a54804ebcd071d08759b165b2c77358a18e"}}
+                           "cf4a6e3000f7920ec4389b9067169a54804ebcd071d08759b165b2c77358a18e",
+                           "paper_1508_07953_gb300/csrc/index_build.cu":
+                           "db146e0c501d9d17a53ba49ae9b5ee3c5e27798f7870ff410fcca961320aad33"}}
+
+
+def _capture_current(tuning=None) -> bool:
+    import hashlib
+    if not RING_CAPTURE["sha256"]:
+        return False
+    if tuning and (tuning.get("tile_shape") != RING_CAPTURE["tile_shape"]
+                   or tuning.get("depth") != RING_CAPTURE["depth"]):
+        return False
+    for rel, digest in RING_CAPTURE["sha256"].items():
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != digest:
+                return False
+    return True
 
 
 def ring_traffic(tuning=None):
     """The captured DRAM bytes, or None once the kernel source or the launch
     variant (tile shape, filter depth) differs from the captured one."""
-    import hashlib
-    if tuning and (tuning.get("tile_shape") != RING_TRAFFIC["tile_shape"]
-                   or tuning.get("depth") != RING_TRAFFIC["depth"]):
-        return None
-    for rel, digest in RING_TRAFFIC["sha256"].items():
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != digest:
-                return None
-    return RING_TRAFFIC["bytes"]
+    return RING_CAPTURE["dram_bytes"] if _capture_current(tuning) else None
+
+
+def ring_l2_bytes(tuning=None):
+    """The captured L2 bytes under the same conditions as ring_traffic."""
+    return RING_CAPTURE["l2_bytes"] if _capture_current(tuning) else None
 
 
 def measured_peaks():
@@ -388,14 +420,20 @@ def run_reference(args, rank, world):
     q, el, nf = oracle_chain_rate(oracle, oix, frames_np[args.warmup:], params, n_samp, 8, 1e9)
     val = q / el
     Q = 1073 * 1913
+    # the timed work is the sample: ms_per_step is the oracle's time per step
+    # of it; a whole frame at the sampled rate would take Q / val seconds
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * Q / val,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(1, nf),
+            "ms_per_step_note": f"oracle time per step on its sample of {n_samp} query positions",
+            "ms_per_full_frame_extrapolated": 1000.0 * Q / val,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic",
             "config": {"workload": "1080p gray video, n=65536 refs, K=64 key points, alpha=1/4, ring_limit=n/8",
-                       "frames": f"{t0}..{t0 + args.steps - 1}", "l2": "n/a (CPU)"},
+                       "frames": f"{t0}..{t0 + args.steps - 1} (scene cut every 40)",
+                       "queries_per_frame": Q, "fps": val / Q, "crop": None,
+                       "l2": "n/a: CPU oracle on a sample of query positions"},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                             "sample": f"{n_samp} sampled query positions chained over {nf} frames"},
+                             "sample": f"{n_samp} sampled query positions chained over {nf} frames, {el:.1f} s"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -560,9 +598,11 @@ def run_anchor(riann, idx, frames, H, W, stream, flush, steps: int, warm: int = 
            "frames": nf, "ms_per_frame": frame_ms, "queries_per_s": Q / (frame_ms / 1000.0),
            "mean_first_ring": tot["sum_first_ring"] / (nf * Q), "mean_rings": sum(rings) / nf,
            "mean_final_candidates": tot["sum_final"] / (nf * Q), "ring_tests_per_query": tot["ring_tests"] / (nf * Q),
-           "roofline": {"bound": "hbm", "kernel": "k_anchor (Alg. 1 random anchors)",
+           "roofline": {"bound": "l2", "kernel": "k_anchor (Alg. 1 random anchors)",
                         "achieved": alg / nf / (frame_ms / 1000.0) / 1e9, "peak": hbm, "unit": "GB/s",
-                        "frac": alg / nf / (frame_ms / 1000.0) / 1e9 / hbm, "algorithmic_bytes_per_frame": alg / nf},
+                        "frac": alg / nf / (frame_ms / 1000.0) / 1e9 / hbm, "algorithmic_bytes_per_frame": alg / nf,
+                        "note": "a traffic model over rows the 4 MB reference set serves from L1/L2, against "
+                                "the HBM copy rate for scale; the kernel's DRAM traffic is a small fraction of it"},
            "cpu_baseline": None,
            "cpu_baseline_note": "the oracle needs the same 34 GB matrix in host memory and minutes to sort it; "
                                 "parity is tested at n <= 2049"}
@@ -752,9 +792,10 @@ def run_unit(riann, R, KP, frames, frames_np, H, W, stream, flush, steps, cpu):
         st = riann.riann_frame_stats(idx, stream)
         if ms[0] >= 0:
             ring_ms.append(ms[0])
+            # the same terms with 4-byte float rows (verification of S u {r_p})
             lg = int(np.ceil(np.log2(n + 1)))
             rq = st["ring_queries"]
-            byts.append(H * W + 16 * Q + rq * 256 + rq * 2 * K * lg * 4 + 8 * st["sum_seed"] + 256 * st["sum_candidates"])
+            byts.append(H * W + 16 * Q + 256 * (st["sum_candidates"] + rq) + Q * 2 * K * lg * 4)
         if ms[1] >= 0:
             dense_ms.append(ms[1])
             pairs.append(st["dense_queries"] * n)
@@ -853,6 +894,8 @@ def run_ours(args, rank, world, local):
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     ring_ms, dense_ms, dense_flops, byts, stats_all = [], [], [], [], []
+    ver_byts, model_byts = [], []
+    cur_depth = riann.riann_get_tuning(idx)["depth"]
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
@@ -870,6 +913,8 @@ def run_ours(args, rank, world, local):
             if ms[0] >= 0:
                 ring_ms.append(ms[0])
                 byts.append(ring_kernel_bytes(st, H, W, 1, WORKLOAD.n, WORKLOAD.K))
+                ver_byts.append(ring_verification_bytes(st, 1))
+                model_byts.append(ring_traffic_model(st, H, W, 1, WORKLOAD.K, cur_depth))
             if ms[1] >= 0:
                 dense_ms.append(ms[1])
                 dense_flops.append(2.0 * st["dense_queries"] * WORKLOAD.n * 64)
@@ -978,6 +1023,38 @@ def run_ours(args, rank, world, local):
     ring_avg_ms = float(np.mean(ring_ms)) if ring_ms else None
     achieved = float(np.mean(byts)) / (ring_avg_ms / 1000.0) / 1e9 if ring_ms else None
     tot = {k: sum(s[k] for s in stats_all) for k in stats_all[0]}
+    traffic = ring_traffic(tuning["chosen"] if tuning else None) if not args.crop else None
+    l2_bytes = ring_l2_bytes(tuning["chosen"] if tuning else None) if not args.crop else None
+    l2_block = None
+    if l2_bytes and ring_avg_ms:
+        l2_block = {"bytes_per_launch": l2_bytes, "achieved_gbs": l2_bytes / (ring_avg_ms / 1000.0) / 1e9,
+                    "note": "lts__t_bytes.sum of the same capture: the traffic the kernel draws from L2"}
+    verification = None
+    if ver_byts and ring_avg_ms:
+        va = float(np.mean(ver_byts)) / (ring_avg_ms / 1000.0) / 1e9
+        verification = {"bound": "hbm", "kernel": "k_sparse, verification of S u {r_p} alone",
+                        "achieved": va, "peak": hbm, "unit": "GB/s", "frac": va / hbm,
+                        "bytes_per_launch": float(np.mean(ver_byts)),
+                        "note": "the candidate-verification rows over the whole ring kernel's time"}
+    # a1 (key-point distances, fused into the ring kernel): 2 K D integer
+    # operations per query with a previous match, against the measured rate of
+    # the instruction pair that computes them
+    roof_a1 = None
+    if ring_avg_ms:
+        try:
+            ipeak = riann.riann_measure_int_peak(stream) / 1e12
+        except Exception:
+            ipeak = None
+        q_prev = (tot["ring_queries"] + tot["dense_queries"]) / args.steps
+        ops = 2.0 * q_prev * WORKLOAD.K * 64
+        if ipeak:
+            roof_a1 = {"bound": "alu", "kernel": "a1 inside k_sparse (|q - k_m|^2 for every key point)",
+                       "achieved": ops / (ring_avg_ms / 1000.0) / 1e12, "peak": ipeak, "unit": "T int-ops/s",
+                       "frac": ops / (ring_avg_ms / 1000.0) / 1e12 / ipeak, "ops_per_launch": ops,
+                       "min_ms": ops / (ipeak * 1e12) * 1000.0,
+                       "peak_source": "riann_measure_int_peak (absolute-difference + dot-product pairs on every SM)",
+                       "note": "a1's operations over the whole ring kernel's time: the step's floor if a1 ran alone "
+                               "is min_ms"}
     # brute-force kernel against the tensor roofline: algorithmic flops 2 Qd n D
     # over its event time, summed over the timed frames (it runs for 1-15 ms at
     # a time inside the step, at the clocks recorded below: burst peak)
@@ -997,10 +1074,21 @@ def run_ours(args, rank, world, local):
         "roofline": {"bound": "hbm", "kernel": "k_sparse (ring intersection, a1-a4)",
                      "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": (achieved / hbm) if achieved else None,
-                     "traffic": ring_traffic(tuning["chosen"] if tuning else None) if not args.crop else None,
-                     "traffic_note": "DRAM bytes of one full-size launch (frame 21), one-pass ncu capture of the current kernel source",
+                     "traffic": traffic,
+                     "traffic_note": "dram__bytes_read.sum + dram__bytes_write.sum of one full-size launch (frame 21), "
+                                     "one-pass ncu capture of the current kernel source",
+                     "l2": l2_block,
                      "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback",
-                     "avg_launch_ms": ring_avg_ms, "algorithmic_bytes_per_launch": float(np.mean(byts)) if byts else None},
+                     "avg_launch_ms": ring_avg_ms, "algorithmic_bytes_per_launch": float(np.mean(byts)) if byts else None,
+                     "numerator": "IO (frame, previous field, 3 outputs) + verification (D bytes per member of "
+                                  "S u {r_p}) + ring search (2 K ceil(log2(n+1)) 4-byte probes per query); "
+                                  "the scope table's filter term, an upper bound, is not counted",
+                     "traffic_model_bytes_per_launch": float(np.mean(model_byts)) if model_byts else None,
+                     "traffic_model_note": "bytes the kernel as built gathers (codes of the scanned entries, entry "
+                                           "rows and ids past the scan, reference rows past every code range): "
+                                           "mostly L2 hits, see l2"},
+        "roofline_verification": verification,
+        "roofline_a1": roof_a1,
         "roofline_dense": {"bound": "tensor", "kernel": "k_dense_tc (brute force, a5; bf16 operands, fp32 accumulation)",
                            "achieved": dense_tf, "peak": bf16, "unit": "TFLOP/s",
                            "frac": (dense_tf / bf16) if dense_tf else None,

@@ -69,7 +69,8 @@ enum {
 
 /* Bits of the device status word. */
 #define RIANN_DEV_BAD_PREV 0x1u   /* a previous-field entry was outside [0, n)  */
-#define RIANN_DEV_BOUNDS 0x2u     /* ring-bound refinement did not converge      */
+#define RIANN_DEV_BOUNDS 0x2u     /* checked build: a table index was out of range
+                                     (the access was skipped)                    */
 #define RIANN_DEV_TIMEOUT 0x4u    /* a bounded spin-wait in a kernel gave up      */
 
 typedef struct {
@@ -277,8 +278,13 @@ int riann_exact_nn(riann_index_t idx, riann_stream_t stream,
 typedef struct {
   uint64_t ring_queries;     /* queries answered by ring intersection           */
   uint64_t dense_queries;    /* queries answered by brute force (incl. frame 0)  */
-  uint64_t sum_seed;         /* sum over ring queries of min_m |Ring_m|         */
+  uint64_t sum_seed;         /* sum over ring queries of the entries the scan visits
+                                (the seed ring's runs, see riann_build_reference_index_ex) */
   uint64_t sum_candidates;   /* sum over ring queries of |S|                    */
+  uint64_t sum_filtered;     /* sum over ring queries of the entries that pass the scan's
+                                code test (each gathers its row of every key's codes) */
+  uint64_t sum_exact;        /* sum over ring queries of the entries that pass every
+                                code range (each needs the exact test and its row)  */
 } riann_frame_stats_t;
 
 /*
@@ -324,6 +330,32 @@ int64_t riann_exact_nn_noalloc_max_queries(int32_t channels);
  */
 int riann_test_wait_expiry(riann_index_t idx, riann_stream_t stream, const uint8_t* d_frame, int32_t H, int32_t W,
                            int32_t* d_out_annf, int64_t spin_cycles);
+
+/*
+ * Measurement utility (the paper has no counterpart): the sustained rate of
+ * the integer instruction pair the key-point distances use -- per 4 bytes a
+ * per-byte absolute difference and a 4-way dot product of it with itself --
+ * over every SM of the current device, in integer operations per second
+ * (8 per pair: 4 multiplies and 4 adds).  Synchronises `stream`; allocates a
+ * small buffer from the stream-ordered pool.  Errors: RIANN_ERR_INVALID_ARG
+ * for a null pointer, RIANN_ERR_OOM, RIANN_ERR_CUDA.
+ */
+int riann_measure_int_peak(riann_stream_t stream, double* ops_per_s);
+
+/*
+ * Check of the checked build (the paper has no counterpart).  Overwrites the
+ * pair-order cell offsets of key point `key` from its second cell on with
+ * n + extra, so that the first run of every query seeded by that key reaches
+ * `extra` entries past the end of the key's rows.  The checked library
+ * (libriann_checked.so) detects the bad run before any access, sets
+ * RIANN_DEV_BOUNDS and skips it; the normal library reads those entries from
+ * the next key's rows (they exist because key < K - 1) and gives wrong
+ * results.  The index is unusable afterwards: destroy it.  Synchronous.
+ * Errors: RIANN_ERR_INVALID_ARG unless 0 <= key < K - 1 and 1 <= extra <= 64;
+ * RIANN_ERR_UNSUPPORTED unless the index scans in pair order
+ * (RIANN_SCAN_PAIRS, or n >= 32768).
+ */
+int riann_test_corrupt_offsets(riann_index_t idx, int32_t key, int32_t extra);
 
 /* Synchronises `stream` and reads the counters. */
 int riann_frame_stats(riann_index_t idx, riann_stream_t stream, riann_frame_stats_t* out);

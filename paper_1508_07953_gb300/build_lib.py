@@ -1,7 +1,10 @@
 """Compile the CUDA library (libriann.so) in-tree for sm_103a.
 
 Each translation unit is compiled by its own nvcc process (in parallel), then
-linked into ``paper_1508_07953_gb300/_lib/libriann.so``.  No GPU is needed.
+linked into ``paper_1508_07953_gb300/_lib/libriann.so``.  The translation units
+whose kernels gather through table indices are compiled a second time with
+-DRIANN_CHECKED (every gathered index tested before the access) and linked with
+the others into ``_lib/libriann_checked.so``.  No GPU is needed.
 """
 from __future__ import annotations
 
@@ -17,8 +20,10 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "libriann.so")
+LIB_CHECKED = os.path.join(LIB_DIR, "libriann_checked.so")
+CHECKED_SOURCES = ["sparse_query.cu", "dense_tc.cu", "anchor.cu"]
 SOURCES = ["api.cu", "index_build.cu", "sparse_query.cu", "dense_tc.cu", "server.cu", "reconstruct.cu", "stack.cu", "cluster.cu", "unit.cu",
-           "anchor.cu"]
+           "anchor.cu", "peaks.cu"]
 HEADERS = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [os.path.join(ROOT, "include", "riann.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
@@ -49,6 +54,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         o = os.path.join(OBJ, src.replace(".cu", ".o"))
         if force or _stale(o, [s] + HEADERS):
             jobs.append([cc, *FLAGS, *extra_flags, "-c", s, "-o", o])
+    for src in CHECKED_SOURCES:
+        s = os.path.join(CSRC, src)
+        o = os.path.join(OBJ, src.replace(".cu", ".checked.o"))
+        if force or _stale(o, [s] + HEADERS):
+            jobs.append([cc, *FLAGS, *extra_flags, "-DRIANN_CHECKED", "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -64,6 +74,11 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
         tmp = LIB + f".{os.getpid()}.tmp"
         run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-ldl"])
         os.replace(tmp, LIB)
+    cobjs = [os.path.join(OBJ, s.replace(".cu", ".checked.o" if s in CHECKED_SOURCES else ".o")) for s in SOURCES]
+    if force or jobs or _stale(LIB_CHECKED, cobjs):
+        tmp = LIB_CHECKED + f".{os.getpid()}.tmp"
+        run([cc, *ARCH, "-shared", "-o", tmp, *cobjs, "-ldl"])
+        os.replace(tmp, LIB_CHECKED)
     return LIB
 
 

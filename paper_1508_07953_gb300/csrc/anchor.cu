@@ -165,7 +165,8 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
       uint32_t xr;
       philox4x32_10((uint32_t)qi, t, a.frame_id, 0u, a.key0, a.key1, &xr);
       const int idx = (int)(((unsigned long long)xr * (unsigned)ns) >> 32);
-      const int ra = src ? src[idx] : (int)(uint32_t)__ldg(row + lo + idx);
+      int ra = src ? src[idx] : (int)(uint32_t)__ldg(row + lo + idx);
+      if (!RIANN_IN_RANGE((unsigned)ra < (unsigned)a.n, a.status)) ra = ri;
       const uint4* ra4 = reinterpret_cast<const uint4*>(a.R + (int64_t)ra * D);
       for (int w = lane; w < NW / 4; w += 32) reinterpret_cast<uint4*>(s_a[warp])[w] = __ldg(ra4 + w);
       __syncwarp();
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
         if (use_bits) {
           for (int k = alo + lane; k < ahi; k += 32) {
             const uint32_t id = (uint32_t)__ldg(arow + k);
-            atomicOr(bits + (id >> 5), 1u << (id & 31));
+            if (RIANN_IN_RANGE(id < (uint32_t)a.n, a.status)) atomicOr(bits + (id >> 5), 1u << (id & 31));
           }
           __syncwarp();
         }
@@ -199,7 +200,9 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
         int rj = 0;
         if (k < ns) {
           rj = src ? src[k] : (int)(uint32_t)__ldg(row + lo + k);
-          if (use_bits) {
+          if (!RIANN_IN_RANGE((unsigned)rj < (unsigned)a.n, a.status)) {
+            rj = ri;
+          } else if (use_bits) {
             keep = (bits[rj >> 5] >> (rj & 31)) & 1u;
           } else {
             const uint32_t A = row_sqdist<NW>(a4, reinterpret_cast<const uint4*>(a.R + (int64_t)rj * D));
@@ -212,7 +215,10 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
       }
       __syncwarp();
       if (use_bits) {   // back to all-zero
-        for (int k = alo + lane; k < ahi; k += 32) bits[(uint32_t)__ldg(arow + k) >> 5] = 0u;
+        for (int k = alo + lane; k < ahi; k += 32) {
+          const uint32_t id = (uint32_t)__ldg(arow + k);
+          if (id < (uint32_t)a.n) bits[id >> 5] = 0u;
+        }
         __syncwarp();
       }
       src = dst;
@@ -223,7 +229,8 @@ __global__ void __launch_bounds__(kAnchorWarps * 32, kAnchorCtasPerSm) k_anchor(
     for (int base = 0; base < ns; base += 32) {
       const int k = base + lane;
       if (k < ns) {
-        const int rj = src ? src[k] : (int)(uint32_t)__ldg(row + lo + k);
+        int rj = src ? src[k] : (int)(uint32_t)__ldg(row + lo + k);
+        if (!RIANN_IN_RANGE((unsigned)rj < (unsigned)a.n, a.status)) rj = ri;
         const uint32_t d = row_sqdist<NW>(q4, reinterpret_cast<const uint4*>(a.R + (int64_t)rj * D));
         const unsigned long long kk = ((unsigned long long)d << 32) | (unsigned)rj;
         best = kk < best ? kk : best;

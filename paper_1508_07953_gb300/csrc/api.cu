@@ -802,6 +802,19 @@ int riann_test_wait_expiry(riann_index_t idx, riann_stream_t stream, const uint8
   return from_cuda(launch_dense_tc(da, ix, ix.ws, reinterpret_cast<cudaStream_t>(stream)));
 }
 
+int riann_test_corrupt_offsets(riann_index_t idx, int32_t key, int32_t extra) {
+  if (!idx || key < 0 || key >= idx->K - 1 || extra < 1 || extra > 64) return RIANN_ERR_INVALID_ARG;
+  if (!idx->pair_scan) return RIANN_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(idx->mu);
+  constexpr int kCells = kPairCodes * kPairCodes;
+  std::vector<uint32_t> v((size_t)kCells, (uint32_t)(idx->n + extra));
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(idx->OFF + (size_t)key * (kCells + 1) + 1, v.data(), sizeof(uint32_t) * kCells,
+                   cudaMemcpyHostToDevice);
+  return from_cuda(e);
+}
+
 int riann_frame_stats(riann_index_t idx, riann_stream_t stream, riann_frame_stats_t* out) {
   if (!idx || !out) return RIANN_ERR_INVALID_ARG;
   unsigned long long v[kStats];
@@ -813,6 +826,8 @@ int riann_frame_stats(riann_index_t idx, riann_stream_t stream, riann_frame_stat
   out->dense_queries = v[kStatDenseQueries];
   out->sum_seed = v[kStatSumSeed];
   out->sum_candidates = v[kStatSumS];
+  out->sum_filtered = v[kStatSumFiltered];
+  out->sum_exact = v[kStatSumExact];
   return RIANN_OK;
 }
 
@@ -1181,6 +1196,8 @@ int riann_batch_stats(riann_batch_t b, riann_stream_t stream, riann_frame_stats_
   out->dense_queries = v[kStatDenseQueries];
   out->sum_seed = v[kStatSumSeed];
   out->sum_candidates = v[kStatSumS];
+  out->sum_filtered = v[kStatSumFiltered];
+  out->sum_exact = v[kStatSumExact];
   return RIANN_OK;
 }
 

@@ -28,7 +28,8 @@ constexpr int kKnnMax = 8;         // largest k of the k-NN output
 static_assert(kKnnMax == RIANN_KNN_MAX, "k-NN list length");
 
 // Work counters of the last frame or batch (riann_frame_stats).
-enum StatSlot { kStatRingQueries = 0, kStatDenseQueries, kStatSumSeed, kStatSumS, kStats = 8 };
+enum StatSlot { kStatRingQueries = 0, kStatDenseQueries, kStatSumSeed, kStatSumS, kStatSumFiltered, kStatSumExact,
+                kStats = 8 };
 
 // Kernel slots of the per-kernel event profiler (riann_profile_*).
 enum KernelSlot { kSlotSparse = 0, kSlotDense = 1, kSlotPrep = 2, kSlots = 4 };
@@ -37,6 +38,22 @@ enum KernelSlot { kSlotSparse = 0, kSlotDense = 1, kSlotPrep = 2, kSlots = 4 };
 // the number of code groups (1..kMaxScanDepth) the scan tests per chunk.
 constexpr int kMaxScanDepth = 3;
 enum TileShape { kTile4x32 = 0, kTile8x16 = 1, kTileShapes = 2 };
+
+// Checked build (compiled with -DRIANN_CHECKED into libriann_checked.so):
+// every index a kernel gathers from a table is tested against the table's
+// extent before the access; a failed test sets RIANN_DEV_BOUNDS in the
+// status word and the access is skipped.  In the normal build the test is
+// compiled out (the tables are built by the library, so the indices are in
+// range by construction).
+#if defined(RIANN_CHECKED)
+__device__ __forceinline__ bool checked_ok(bool ok, uint32_t* status) {
+  if (!ok) atomicOr(status, RIANN_DEV_BOUNDS);
+  return ok;
+}
+#define RIANN_IN_RANGE(cond, status) ::riann::checked_ok((cond), (status))
+#else
+#define RIANN_IN_RANGE(cond, status) true
+#endif
 
 // Largest possible squared distance between two patches of `dim` bytes.
 __host__ __device__ constexpr uint32_t max_sqdist(int dim) { return (uint32_t)dim * 255u * 255u; }

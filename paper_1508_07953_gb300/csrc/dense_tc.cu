@@ -558,6 +558,7 @@ struct PrepArgs {
   __nv_bfloat16* Aq;
   uint32_t* qnorm;
   unsigned long long* best;
+  uint32_t* status;               // checked build: RIANN_DEV_BOUNDS for a query id outside its frame
 };
 
 // The item holding global query id gid (items sorted by query_begin).
@@ -579,7 +580,8 @@ __global__ void k_dense_prep(PrepArgs a) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t gid = a.list ? (int64_t)a.list[i] : i;
     const FrameItem& it = a.items ? item_of(a.items, a.hdr, gid) : a.one;
-    const int64_t qi = gid - it.query_begin;
+    int64_t qi = gid - it.query_begin;
+    if (!RIANN_IN_RANGE(qi >= 0 && qi < (int64_t)it.Hq * it.Wq, a.status)) qi = 0;
     const int y = (int)(qi / it.Wq), x = (int)(qi % it.Wq);
     uint2* dst = reinterpret_cast<uint2*>(a.Aq + i * (64 * C));
     uint32_t nrm = 0;
@@ -611,6 +613,7 @@ struct FinishArgs {
   const unsigned long long* best;
   int n;
   unsigned long long* stats;
+  uint32_t* status;               // checked build: RIANN_DEV_BOUNDS for a query id outside its frame
 };
 
 __global__ void k_dense_finish(FinishArgs a) {
@@ -620,6 +623,7 @@ __global__ void k_dense_finish(FinishArgs a) {
     const int64_t gid = a.list ? (int64_t)a.list[i] : i;
     const FrameItem& it = a.items ? item_of(a.items, a.hdr, gid) : a.one;
     const int64_t qi = gid - it.query_begin;
+    if (!RIANN_IN_RANGE(qi >= 0 && qi < (int64_t)it.Hq * it.Wq, a.status)) continue;
     const unsigned long long k = a.best[i];
     it.out_annf[qi] = (int32_t)(k & 0xffffffffu);
     if (it.out_dist) it.out_dist[qi] = (uint32_t)(k >> 32);
@@ -759,6 +763,7 @@ cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, Workspace& ws, cudaSt
   p.Aq = ws.Aq;
   p.qnorm = ws.qnorm;
   p.best = ws.best;
+  p.status = ix.status;
   int64_t blocks = (d.Q + 255) / 256;
   const int64_t cap = (int64_t)sm_count() * 16;
   if (blocks > cap) blocks = cap;
@@ -817,6 +822,7 @@ cudaError_t launch_dense_tc(const DenseArgs& d, Index& ix, Workspace& ws, cudaSt
   f.best = ws.best;
   f.n = ix.n;
   f.stats = d.stats;
+  f.status = ix.status;
   k_dense_finish<<<(unsigned)blocks, 256, 0, s>>>(f);
   return cudaGetLastError();
 }
@@ -926,6 +932,7 @@ cudaError_t launch_exact_nn_noalloc(const DenseArgs& d, Index& ix, cudaStream_t 
   p.Aq = Aq;
   p.qnorm = qnorm;
   p.best = best;
+  p.status = ix.status;
   int64_t blocks = (d.Q + 255) / 256;
   const int64_t cap = (int64_t)sm_count() * 16;
   if (blocks > cap) blocks = cap;
@@ -960,6 +967,7 @@ cudaError_t launch_exact_nn_noalloc(const DenseArgs& d, Index& ix, cudaStream_t 
   f.best = best;
   f.n = ix.n;
   f.stats = nullptr;
+  f.status = ix.status;
   k_dense_finish<<<(unsigned)blocks, 256, 0, s>>>(f);
   return cudaGetLastError();
 }

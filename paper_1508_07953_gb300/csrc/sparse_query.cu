@@ -148,9 +148,17 @@ __device__ __forceinline__ int warp_count_below(const uint32_t* __restrict__ t, 
 // Rank range [first >= lo, first > hi) of the exact ring [lo, hi] in TA[m]:
 // the first end lies in bucket clo's rank range, the second in bucket chi's.
 __device__ __forceinline__ int2 ring_run(const uint32_t* __restrict__ ta, const uint32_t* __restrict__ rb,
-                                         int clo, int chi, uint32_t lo, uint32_t hi, int lane) {
+                                         int clo, int chi, uint32_t lo, uint32_t hi, int lane,
+                                         uint32_t* status) {
   const int a0 = clo < 0 ? 0 : (int)__ldg(rb + clo), a1 = (int)__ldg(rb + clo + 1);
   const int b0 = chi < 0 ? 0 : (int)__ldg(rb + chi), b1 = (int)__ldg(rb + chi + 1);
+#if defined(RIANN_CHECKED)
+  // the sorted list holds rb[kBuckets] entries: its counted ranges end there
+  if (!(a0 <= a1 && b0 <= b1 && a1 <= (int)__ldg(rb + kBuckets) && b1 <= (int)__ldg(rb + kBuckets))) {
+    if (lane == 0) atomicOr(status, RIANN_DEV_BOUNDS);
+    return make_int2(0, 0);
+  }
+#endif
   const int a = a0 + warp_count_below(ta, a0, a1, lo, false, lane);
   const int b = b0 + warp_count_below(ta, b0, b1, hi, true, lane);
   return make_int2(a, b > a ? b : a);
@@ -235,7 +243,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   __shared__ __align__(16) float s_qf[UNIT ? kWarps : 1][UNIT ? D : 4];   // UNIT: the normalised query
   __shared__ int s_next, s_ndense, s_dense_base;
   __shared__ FrameItem s_item;                    // batched launch: this launch's frame
-  __shared__ unsigned long long s_stat[3];        // ring-answered queries, scanned entries, sum of |S|
+  __shared__ unsigned long long s_stat[5];        // ring-answered queries, scanned entries, |S|, B and D entries
 
   const int K = a.K, n = a.n, G = a.G;
   {
@@ -273,7 +281,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       const int64_t xb = (int64_t)tx0 * C + c;
       s_tile[i] = (c < TROW && y < it.H && xb < rowb) ? it.frame[(int64_t)y * rowb + xb] : (uint8_t)0;
     }
-    if (threadIdx.x == 0) { s_next = 0; s_ndense = 0; s_stat[0] = s_stat[1] = s_stat[2] = 0; }
+    if (threadIdx.x == 0) { s_next = 0; s_ndense = 0; s_stat[0] = s_stat[1] = s_stat[2] = s_stat[3] = s_stat[4] = 0; }
   }
   __syncthreads();
 
@@ -415,7 +423,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       while (cand >= 0) {
         const int2 rr = ring_run(a.TA + (int64_t)cand * n, a.RB + cand * (kBuckets + 1), s_clo[warp][cand],
                                  s_chi[warp][cand], s_lw[warp][2 * cand],
-                                 s_lw[warp][2 * cand] + s_lw[warp][2 * cand + 1], lane);
+                                 s_lw[warp][2 * cand] + s_lw[warp][2 * cand + 1], lane, a.status);
         if ((uint32_t)(rr.y - rr.x) <= (uint32_t)a.ring_limit) {
           found = true;
           ms = cand;
@@ -478,7 +486,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       const int pclo = s_clo[warp][pm], pchi = s_chi[warp][pm];
       if (pm == ms) {
         const int2 run = ring_run(a.TA + (int64_t)ms * n, a.RB + ms * (kBuckets + 1), sclo, schi,
-                                  s_lw[warp][2 * ms], s_lw[warp][2 * ms] + s_lw[warp][2 * ms + 1], lane);
+                                  s_lw[warp][2 * ms], s_lw[warp][2 * ms] + s_lw[warp][2 * ms + 1], lane, a.status);
         if (run.y > run.x) {
           nruns = 1;
           scanned = (uint32_t)(run.y - run.x);
@@ -502,6 +510,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
             const uint32_t* ob = off + (bl + b0 + lane) * kPairCodes;
             st = __ldg(ob + cl);
             en = __ldg(ob + ch + 1);
+            if (!RIANN_IN_RANGE(st <= en && en <= (uint32_t)n, a.status)) st = en = 0u;
           }
           const uint32_t pen = __shfl_up_sync(kFull, en, 1);
           const bool head = v && (lane == 0 || st != pen);
@@ -620,6 +629,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     int32_t* qc = s_qc[warp];
     uint16_t* qm = s_qm[warp];
     int ha = 0, na = 0, hc = 0, nc = 0;            // queue heads and lengths
+    uint32_t nfilt = 0, nexact = 0;                // entries through B and through D (statistics)
 
     // scan position (warp-uniform): run ri, 4-aligned chunk start base in
     // it; the current chunk's codes a0..a2 (4 positions per lane: base +
@@ -654,6 +664,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         const int r = alive ? qc[slot] : 0;
         uint32_t mk = alive ? (uint32_t)qm[slot] : 0u;
         hc = (hc + take) & (kQueueC - 1);
+        nexact += take;
         nc -= take;
         const uint32_t pc = (uint32_t)__popc(mk);
         int ppos = 0, ptot = 0;
@@ -674,7 +685,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
           const int k1 = p0 + lane;
           const uint32_t e1 = k1 < ptot ? pr[k1] : 0u;
           const int r1 = __shfl_sync(kFull, r, (int)(e1 >> 4));
-          if (k1 < ptot) {
+          if (k1 < ptot && RIANN_IN_RANGE((int)(e1 & 15u) < kq, a.status)) {
             const uint4 v1 = __ldg(prow + (int64_t)r1 * kq + (e1 & 15u));
             const uint4 l0 = lw4[2 * (e1 & 15u)], l1 = lw4[2 * (e1 & 15u) + 1];
             const bool okw = (v1.x - l0.x <= l0.y) && (v1.y - l0.z <= l0.w) && (v1.z - l1.x <= l1.y) &&
@@ -709,8 +720,10 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         const bool on = lane < take;
         const int j = on ? qa[(ha + lane) & (kQueueA - 1)] : 0;
         ha = (ha + take) & (kQueueA - 1);
+        nfilt += take;
         na -= take;
         const int r = on ? __ldg(tid + j) : 0;
+        const bool rok = !on || RIANN_IN_RANGE((unsigned)r < (unsigned)n, a.status);
         const uint4* er = reinterpret_cast<const uint4*>(ce + (int64_t)j * a.Ke);
         uint32_t pass = kHi, bmask = 0;            // bmask: words of the entry with a boundary code
 #pragma unroll
@@ -726,7 +739,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
             bmask |= ((((w.w - il.w) & ~(w.w - ih.w) & kHi) != kHi) ? 8u : 0u) << (4 * c);
           }
         }
-        const bool ok = on && (pass & kHi) == kHi;
+        const bool ok = on && rok && (pass & kHi) == kHi;
         const unsigned m = __ballot_sync(kFull, ok);
         if (ok) {
           const int slot = (hc + nc + __popc(m & lt)) & (kQueueC - 1);
@@ -814,6 +827,8 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         atomicAdd(&s_stat[0], 1ull);
         atomicAdd(&s_stat[1], (unsigned long long)scanned);
         atomicAdd(&s_stat[2], (unsigned long long)cnt);
+        atomicAdd(&s_stat[3], (unsigned long long)nfilt);
+        atomicAdd(&s_stat[4], (unsigned long long)nexact);
       }
     }
     __syncwarp();
@@ -827,6 +842,8 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     atomicAdd(&a.stats[kStatDenseQueries], (unsigned long long)s_ndense);
     atomicAdd(&a.stats[kStatSumSeed], s_stat[1]);
     atomicAdd(&a.stats[kStatSumS], s_stat[2]);
+    atomicAdd(&a.stats[kStatSumFiltered], s_stat[3]);
+    atomicAdd(&a.stats[kStatSumExact], s_stat[4]);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < s_ndense; i += blockDim.x) a.dense_list[s_dense_base + i] = s_dense[i];

@@ -15,7 +15,10 @@ from typing import Optional
 
 import torch
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", "libriann.so")
+# RIANN_LIBRARY=checked selects the checked build (every gathered table index
+# tested before the access, RIANN_DEV_BOUNDS on a failure)
+_LIB_NAME = "libriann_checked.so" if os.environ.get("RIANN_LIBRARY") == "checked" else "libriann.so"
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_lib", _LIB_NAME)
 if not os.path.exists(_LIB_PATH):
     raise ImportError(
         f"RIANN CUDA library not found at {_LIB_PATH}; build it with "
@@ -55,7 +58,8 @@ class riann_index_info_t(ctypes.Structure):
 
 class riann_frame_stats_t(ctypes.Structure):
     _fields_ = [("ring_queries", ctypes.c_uint64), ("dense_queries", ctypes.c_uint64),
-                ("sum_seed", ctypes.c_uint64), ("sum_candidates", ctypes.c_uint64)]
+                ("sum_seed", ctypes.c_uint64), ("sum_candidates", ctypes.c_uint64),
+                ("sum_filtered", ctypes.c_uint64), ("sum_exact", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -103,6 +107,8 @@ _lib.riann_profile_enable.argtypes = [_P, ctypes.c_int]
 _lib.riann_profile_read.argtypes = [_P, _P, ctypes.POINTER(ctypes.c_float), _i32]
 _lib.riann_exact_nn_noalloc.argtypes = [_P, _P, _P, _i32, _i32, _P, _P]
 _lib.riann_test_wait_expiry.argtypes = [_P, _P, _P, _i32, _i32, _P, _i64]
+_lib.riann_measure_int_peak.argtypes = [_P, ctypes.POINTER(ctypes.c_double)]
+_lib.riann_test_corrupt_offsets.argtypes = [_P, _i32, _i32]
 _lib.riann_exact_nn_noalloc_max_queries.argtypes = [_i32]
 _lib.riann_exact_nn_noalloc_max_queries.restype = ctypes.c_int64
 _lib.riann_session_create.argtypes = [_P, _i32, _i32, ctypes.POINTER(_P)]
@@ -520,6 +526,24 @@ def riann_test_wait_expiry(index: RiannIndex, frame: torch.Tensor, out_annf: tor
     _check(_lib.riann_test_wait_expiry(index.handle, _stream(stream), _dev(frame, (torch.uint8,), "frame"),
                                        H, W, _dev(out_annf, _I32, "out_annf", Q), int(spin_cycles)),
            "riann_test_wait_expiry")
+
+
+def riann_test_corrupt_offsets(index: RiannIndex, key: int, extra: int) -> None:
+    """Checked-build check: push key `key`'s scan runs `extra` entries past its
+    rows (see riann.h).  The index is unusable afterwards."""
+    _check(_lib.riann_test_corrupt_offsets(index.handle, int(key), int(extra)), "riann_test_corrupt_offsets")
+
+
+def library_name() -> str:
+    return _LIB_NAME
+
+
+def riann_measure_int_peak(stream: Optional[torch.cuda.Stream] = None) -> float:
+    """Integer operations per second of the absolute-difference / dot-product
+    pair the key-point distances use (see riann.h)."""
+    v = ctypes.c_double(0.0)
+    _check(_lib.riann_measure_int_peak(_stream(stream), ctypes.byref(v)), "riann_measure_int_peak")
+    return float(v.value)
 
 
 def riann_frame_stats(index: RiannIndex, stream: Optional[torch.cuda.Stream] = None) -> dict:
