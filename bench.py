@@ -547,6 +547,24 @@ def run_served(riann, dev, gray_idx, seconds: float):
     out["batched"] = one(False, load_limit)
     out["plain"] = one(True, load_limit)
     out["batched_memory_admission_only"] = one(False, 0.0)
+
+    # 1080p gray streams alone: (a) at 30 fps with the GPU-time admission
+    # (how many such streams the GPU carries, at what latency), (b) one stream
+    # sending 60 fps, admitted by memory alone: the server answers the newest
+    # frame of each tick, so its completed frames per second are the 1080p
+    # frame rate the served path sustains
+    def alone(fps, limit, starts, duration):
+        spec = serve.ServeSpec(duration=duration, fps=fps, mix=((1080, 1920, 1),))
+        trace = [serve.Arrival(t, (1080, 1920, 1), duration - t, 0) for t in starts]
+        srv = riann.RiannServer(gray_idx, rgb_idx, budget_bytes=4 << 30, max_tick_queries=48 << 20,
+                                max_streams=64, params=params, plain=False, load_limit=limit)
+        try:
+            return serve.run(srv, pools, spec, trace)
+        finally:
+            srv.close()
+
+    out["1080p_gray_30fps_three_offered"] = alone(30.0, load_limit, (0.0, 0.5, 1.0), 6.0)
+    out["1080p_gray_one_stream_60fps_offered"] = alone(60.0, 0.0, (0.0,), 6.0)
     rgb_idx.close()
     return out
 

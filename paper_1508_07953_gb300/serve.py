@@ -124,6 +124,8 @@ def run(server, pools: Dict[Tuple[int, int, int], list], spec: ServeSpec, trace:
         "frames_replaced_in_queue": info["dropped"],
         "latency_ms_p50": 1e3 * percentile(lat, 50), "latency_ms_p99": 1e3 * percentile(lat, 99),
         "latency_ms_p50_by_format": {k: 1e3 * percentile(v, 50) for k, v in sorted(per_fmt_lat.items())},
+        "latency_ms_p99_by_format": {k: 1e3 * percentile(v, 99) for k, v in sorted(per_fmt_lat.items())},
+        "frames_by_format": {k: len(v) for k, v in sorted(per_fmt_lat.items())},
         "queries_per_s": info["queries_done"] / max(wall, 1e-9), "wall_s": wall,
         "ns_per_query_measured": info["ns_per_query"],
         "ticks": info["ticks"], "stream_seconds": stream_seconds,
