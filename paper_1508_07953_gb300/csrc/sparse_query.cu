@@ -25,13 +25,17 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Exact ring membership |sqrt(A) - sqrt(B)| <= (p/q) sqrt(C) for A, B <= 192*255^2:
 // q^2 (A + B) - p^2 C <= 2 q^2 sqrt(A B)  <=>  L <= 0  or  L^2 <= 4 q^4 A B.
-// All terms fit 64-bit integers: L < 64 * 2^25, 4 q^4 A B < 2^14 * 2^48.
+// A positive L is below q^2 (A + B) <= 64 * 2 * 192 * 255^2 < 2^31, so L^2 and
+// A B are 32 x 32 -> 64-bit products, and 4 q^4 A B < 2^14 * 2^48 fits 64 bits.
 __device__ __forceinline__ bool in_ring(uint32_t A, uint32_t B, uint32_t C, uint32_t p2,
                                         uint32_t q2) {
   const int64_t L = (int64_t)q2 * ((int64_t)A + (int64_t)B) - (int64_t)p2 * (int64_t)C;
   if (L <= 0) return true;
-  const uint64_t l = (uint64_t)L;
-  return l * l <= (4ull * q2 * q2) * (uint64_t)A * (uint64_t)B;
+  const uint32_t l = (uint32_t)L;
+  const unsigned long long ll = (unsigned long long)l * l;
+  const unsigned long long ab = (unsigned long long)A * B;
+  const unsigned long long k = 4u * q2 * q2;
+  return ll <= ab * k;
 }
 
 // Smallest member A in [0, B] (B itself is always a member: |sqrt B - sqrt B| = 0).
@@ -355,7 +359,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     // a2: per ring m (lane m and m+32): B_m, exact bounds [lo, hi] on A, their
     // bucket codes, and bucket-granular bounds lb <= |Ring_m| <= ub.
     const float sC = (float)Cd;
-    unsigned long long seedkey = ~0ull;
+    uint32_t seedkey = 0xffffffffu;                // (bucket width << 6) | m, width <= 256
 #pragma unroll 1
     for (int h = 0; h < 2; ++h) {
       const int m = lane + 32 * h;
@@ -389,19 +393,14 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         s_clo[warp][m] = (int16_t)clo;
         s_chi[warp][m] = (int16_t)chi;
         s_ub[warp][m] = width;
-        const unsigned long long key = ((unsigned long long)width << 32) | (unsigned)m;
+        const uint32_t key = (width << 6) | (uint32_t)m;
         seedkey = key < seedkey ? key : seedkey;
       } else if (m < a.Kp) {   // padding key of a distance row: always passes
         s_lw[warp][2 * m] = 0u;
         s_lw[warp][2 * m + 1] = 0xffffffffu;
       }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const unsigned long long v = __shfl_xor_sync(kFull, seedkey, o);
-      seedkey = v < seedkey ? v : seedkey;
-    }
-    int ms = (int)(seedkey & 0xffffffffu);
+    int ms = (int)(__reduce_min_sync(kFull, seedkey) & 63u);
     __syncwarp();
 
     // routing: brute force iff every ring holds more than ring_limit
@@ -431,7 +430,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         }
         if (first) {
           first = false;
-          unsigned long long ubkey = ~0ull;          // smallest upper bound over the other rings
+          uint32_t ubkey = 0xffffffffu;              // (smallest upper bound over the other rings << 6) | ring
 #pragma unroll 1
           for (int h = 0; h < 2; ++h) {
             const int m = lane + 32 * h;
@@ -441,20 +440,16 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
               const uint32_t* rb = a.RB + m * (kBuckets + 1);
               const uint32_t ub = __ldg(rb + chi + 1) - (clo < 0 ? 0u : __ldg(rb + clo));
               const uint32_t lb = chi > clo + 1 ? __ldg(rb + chi) - __ldg(rb + clo + 1) : 0u;
-              const unsigned long long k2 = ((unsigned long long)ub << 32) | (unsigned)m;
+              const uint32_t k2 = (ub << 6) | (uint32_t)m;   // ub <= n <= 2^24
               ubkey = k2 < ubkey ? k2 : ubkey;
               mine = ub > (uint32_t)a.ring_limit && lb <= (uint32_t)a.ring_limit;
             }
             const unsigned bal = __ballot_sync(kFull, mine);
             if (h == 0) todo0 = bal; else todo1 = bal;
           }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long v = __shfl_xor_sync(kFull, ubkey, o);
-            ubkey = v < ubkey ? v : ubkey;
-          }
-          if ((uint32_t)(ubkey >> 32) <= (uint32_t)a.ring_limit) {   // a ring certainly within the limit
-            ms = (int)(ubkey & 0xffffffffu);
+          ubkey = __reduce_min_sync(kFull, ubkey);
+          if (ubkey != 0xffffffffu && (ubkey >> 6) <= (uint32_t)a.ring_limit) {   // a ring certainly within the limit
+            ms = (int)(ubkey & 63u);
             found = true;
             break;
           }
@@ -572,14 +567,18 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       }
     }
     {
-      // rank of this lane's group by ascending estimate (ties: lower group);
-      // the scan visits the groups in that order
-      int rank = 0;
-      for (int g2 = 0; g2 < G; ++g2) {
-        const float e2 = __shfl_sync(kFull, est, g2);
-        rank += (e2 < est) || (e2 == est && g2 < lane);
+      // the scan's groups: the ns1 smallest estimates (ties: lower group),
+      // each found by a warp minimum over (estimate bits, group) -- the
+      // estimates are non-negative floats, whose bits order like them
+      const int nsel = G < a.depth ? G : a.depth;
+      uint32_t ekey = (__float_as_uint(est) & ~31u) | (uint32_t)lane;
+      for (int i = 0; i < nsel; ++i) {
+        const uint32_t mn = __reduce_min_sync(kFull, ekey);
+        if ((uint32_t)lane == (mn & 31u)) {
+          s_gd[warp][i] = make_uint4((uint32_t)(lane * a.nw), glo, ghi, 0u);
+          ekey = 0xffffffffu;
+        }
       }
-      if (lane < G) s_gd[warp][rank] = make_uint4((uint32_t)(lane * a.nw), glo, ghi, 0u);
       // in key order for the entry rows (padding groups of a row always pass
       // and are interior)
       if (lane < (a.Ke >> 2)) {
@@ -811,13 +810,11 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       }
       best = __shfl_sync(kFull, best, 0);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      if (!KNN) {
-        const unsigned long long v = __shfl_xor_sync(kFull, best, o);
-        best = v < best ? v : best;
-      }
-      cnt += __shfl_xor_sync(kFull, cnt, o);
+    cnt = __reduce_add_sync(kFull, cnt);
+    if (!KNN) {   // the (dist, index) minimum: the least distance, then the least index holding it
+      const uint32_t dmin = __reduce_min_sync(kFull, (uint32_t)(best >> 32));
+      const uint32_t imin = __reduce_min_sync(kFull, (uint32_t)(best >> 32) == dmin ? (uint32_t)best : 0xffffffffu);
+      best = ((unsigned long long)dmin << 32) | imin;
     }
     if (lane == 0) {
       it.out_annf[qi] = (int32_t)(best & 0xffffffffu);
