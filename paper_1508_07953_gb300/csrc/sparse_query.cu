@@ -14,6 +14,8 @@
 // references that pass the filter are then tested exactly against every ring
 // from their row of key-point distances in P (16 MB for n = 65536, K = 64:
 // it stays in L2).
+#include <algorithm>
+
 #include "unit.cuh"
 
 namespace riann {
@@ -22,6 +24,8 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kCtasPerSm = 3;   // register budget 80 per thread
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kCarveDevices = 64;          // devices whose carveout preference has been set
+constexpr int kSmemPerCtaReserved = 1024;  // shared memory the hardware reserves per resident CTA
 
 // Exact ring membership |sqrt(A) - sqrt(B)| <= (p/q) sqrt(C) for A, B <= 192*255^2:
 // q^2 (A + B) - p^2 C <= 2 q^2 sqrt(A B)  <=>  L <= 0  or  L^2 <= 4 q^4 A B.
@@ -38,68 +42,37 @@ __device__ __forceinline__ bool in_ring(uint32_t A, uint32_t B, uint32_t C, uint
   return ll <= ab * k;
 }
 
-// Smallest member A in [0, B] (B itself is always a member: |sqrt B - sqrt B| = 0).
-// Membership is false..false true..true on [0, B].  The float estimate is
-// usually exact or off by one, so probe it and its neighbour first; otherwise
-// gallop from it and bisect, so an estimate error only costs iterations.
-__device__ uint32_t ring_low(uint32_t B, uint32_t C, uint32_t p2, uint32_t q2, float est) {
-  uint32_t a = est <= 0.f ? 0u : (est >= (float)B ? B : (uint32_t)ceilf(est));
-  if (a == 0u && in_ring(0u, B, C, p2, q2)) return 0u;
-  uint32_t good, bad;   // in_ring(good), !in_ring(bad), bad < good
-  if (in_ring(a, B, C, p2, q2)) {
-    if (a == 0u || !in_ring(a - 1, B, C, p2, q2)) return a;
-    good = a - 1;
-    for (uint32_t step = 2;; step <<= 1) {
-      const uint32_t c = good > step ? good - step : 0u;
-      if (!in_ring(c, B, C, p2, q2)) { bad = c; break; }
-      if (c == 0u) return 0u;
-      good = c;
-    }
-  } else {
-    if (in_ring(a + 1, B, C, p2, q2)) return a + 1;
-    bad = a + 1;
-    for (uint32_t step = 2;; step <<= 1) {
-      const uint32_t c = (B - bad > step) ? bad + step : B;
-      if (in_ring(c, B, C, p2, q2)) { good = c; break; }
-      bad = c;
-    }
-  }
-  while (good - bad > 1) {
-    const uint32_t mid = bad + (good - bad) / 2;
-    if (in_ring(mid, B, C, p2, q2)) good = mid; else bad = mid;
-  }
-  return good;
-}
-
-// Largest member A in [B, Amax]; membership is true..true false..false there.
-__device__ uint32_t ring_high(uint32_t B, uint32_t C, uint32_t p2, uint32_t q2, float est,
+// Farthest member of the ring from B on one side: the smallest member in
+// [0, B] (up = false) or the largest in [B, Amax] (up = true).  The ring is an
+// interval holding B, so in the offset t = |A - B| membership is true up to
+// some t* and false beyond.  The float estimate (usually exact or off by one)
+// is probed first and then its neighbour; otherwise the search gallops on
+// with doubling steps -- away from B from a member, towards B from a
+// non-member -- until it brackets t*, then bisects.  An estimate error only
+// costs iterations; one membership test per iteration.
+__device__ uint32_t ring_edge(uint32_t B, uint32_t C, uint32_t p2, uint32_t q2, float est, bool up,
                               uint32_t Amax) {
-  uint32_t a = est <= (float)B ? B : (est >= (float)Amax ? Amax : (uint32_t)est);
-  uint32_t good, bad;   // in_ring(good), !in_ring(bad), good < bad
-  if (in_ring(a, B, C, p2, q2)) {
-    if (a == Amax || !in_ring(a + 1, B, C, p2, q2)) return a;
-    good = a + 1;
-    for (uint32_t step = 2;; step <<= 1) {
-      const uint32_t c = (Amax - good > step) ? good + step : Amax;
-      if (!in_ring(c, B, C, p2, q2)) { bad = c; break; }
-      if (c == Amax) return Amax;
-      good = c;
+  uint32_t t;                                      // offset of the estimate
+  if (up) t = (est <= (float)B ? B : (est >= (float)Amax ? Amax : (uint32_t)est)) - B;
+  else t = B - (est <= 0.f ? 0u : (est >= (float)B ? B : (uint32_t)ceilf(est)));
+  uint32_t good = 0, bad = (up ? Amax - B : B) + 1;   // a member at offset good, none at bad
+  uint32_t step = 1;
+  int mode = 2;                                    // 2: the estimate, +1 / -1: galloping, 0: bisecting
+#pragma unroll 1
+  for (;;) {
+    if (mode == 1) {
+      if (step >= bad - good) mode = 0; else t = good + step;
+    } else if (mode == -1) {
+      if (step >= bad - good) mode = 0; else t = bad - step;
     }
-  } else {
-    // a > B here (B is a member)
-    if (in_ring(a - 1, B, C, p2, q2)) return a - 1;
-    bad = a - 1;
-    for (uint32_t step = 2;; step <<= 1) {
-      const uint32_t c = (bad - B > step) ? bad - step : B;
-      if (in_ring(c, B, C, p2, q2)) { good = c; break; }
-      bad = c;
-    }
+    if (mode == 0) t = good + (bad - good) / 2;
+    const bool in = in_ring(up ? B + t : B - t, B, C, p2, q2);
+    if (in) good = t; else bad = t;
+    if (bad - good <= 1) return up ? B + good : B - good;
+    if (mode == 2) mode = in ? 1 : -1;
+    else if (mode == (in ? -1 : 1)) mode = 0;      // bracketed
+    else step <<= 1;
   }
-  while (bad - good > 1) {
-    const uint32_t mid = good + (bad - good) / 2;
-    if (in_ring(mid, B, C, p2, q2)) good = mid; else bad = mid;
-  }
-  return good;
 }
 
 // Sum of squared byte differences of two 16-byte vectors, added to acc.
@@ -120,12 +93,14 @@ __device__ __forceinline__ int bucket_code(const uint32_t* __restrict__ coarse, 
                                            uint32_t x) {
   int c = 0;   // coarse edges <= x
 #pragma unroll
-  for (int half = 32; half > 0; half >>= 1)
+  for (int half = 16; half > 0; half >>= 1)
     if (coarse[c + half - 1] <= x) c += half;
-  if (c == 63 && coarse[63] <= x) c = 64;
+  if (c == 31 && coarse[31] <= x) c = 32;
   if (c == 0) return -1;
-  const uint4 u = __ldg(reinterpret_cast<const uint4*>(e + 4 * (c - 1)));
-  return 4 * (c - 1) + (u.x <= x) + (u.y <= x) + (u.z <= x) + (u.w <= x) - 1;
+  const uint4* s = reinterpret_cast<const uint4*>(e + 8 * (c - 1));
+  const uint4 u = __ldg(s), v = __ldg(s + 1);
+  return 8 * (c - 1) + (u.x <= x) + (u.y <= x) + (u.z <= x) + (u.w <= x) + (v.x <= x) + (v.y <= x) +
+         (v.z <= x) + (v.w <= x) - 1;
 }
 
 // Number of entries of the sorted range t[lo, hi) below v (le: at most v),
@@ -133,6 +108,7 @@ __device__ __forceinline__ int bucket_code(const uint32_t* __restrict__ coarse, 
 __device__ __forceinline__ int warp_count_below(const uint32_t* __restrict__ t, int lo, int hi, uint32_t v,
                                                 bool le, int lane) {
   int c = 0;
+#pragma unroll 1
   for (int base = lo; base < hi; base += 256) {
     uint32_t x[8];
 #pragma unroll
@@ -221,7 +197,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   constexpr int kMaxG = kMaxK / 4;
   __shared__ __align__(16) uint8_t s_tile[(TY + 7) * TROWP];
   __shared__ uint32_t s_kp[kMaxK * KPW];
-  __shared__ uint32_t s_coarse[kMaxK][65];        // every 4th bucket edge per key (padded: no bank conflicts)
+  __shared__ uint32_t s_coarse[kMaxK][33];        // every 8th bucket edge per key (padded: no bank conflicts)
   // exact ring bounds [lo, hi] on A as (lo, hi - lo) per key; padding keys (0, ~0)
   __shared__ __align__(16) uint32_t s_lw[kWarps][2 * kMaxK];
   __shared__ int16_t s_clo[kWarps][kMaxK];        // their bucket codes (-1..255)
@@ -229,7 +205,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   __shared__ uint32_t s_ub[kWarps][kMaxK];        // buckets each ring touches
   // per group in filter order: (offset of its code row in CW, packed 7-bit
   // lo, packed hi + 1, unused)
-  __shared__ uint4 s_gd[kWarps][kMaxG];
+  __shared__ uint4 s_gd[kWarps][kMaxScanDepth];
   __shared__ __align__(16) uint32_t s_klo[kWarps][kMaxG];   // the same ranges in key order
   __shared__ __align__(16) uint32_t s_khi[kWarps][kMaxG];
   __shared__ __align__(16) uint32_t s_kil[kWarps][kMaxG];   // interiors: packed lo + 1 and hi
@@ -253,7 +229,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   {
     const uint32_t* kp = reinterpret_cast<const uint32_t*>(a.KP);
     for (int i = threadIdx.x; i < K * NW; i += blockDim.x) s_kp[(i / NW) * KPW + (i % NW)] = kp[i];
-    for (int i = threadIdx.x; i < K * 64; i += blockDim.x) s_coarse[i >> 6][i & 63] = __ldg(a.E + (i >> 6) * kBuckets + 4 * (i & 63));
+    for (int i = threadIdx.x; i < K * 32; i += blockDim.x) s_coarse[i >> 5][i & 31] = __ldg(a.E + (i >> 5) * kBuckets + 8 * (i & 31));
     for (int i = threadIdx.x; i < K; i += blockDim.x) s_partner[i] = __ldg(a.partner + i);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -279,6 +255,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   const int tx0 = (tile % it.tiles_x) * TX;
   {
     const int64_t rowb = (int64_t)it.W * C;
+#pragma unroll 1
     for (int i = threadIdx.x; i < (TY + 7) * TROWP; i += blockDim.x) {
       const int r = i / TROWP, c = i % TROWP;
       const int y = ty0 + r;
@@ -379,8 +356,8 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
           }
           const float cross = 2.f * alpha * sqrtf((float)B * sC);
           const float base = (float)B + alpha * alpha * sC;
-          lo = ring_low(B, Cd, p2, q2, base - cross);
-          hi = ring_high(B, Cd, p2, q2, base + cross, Amax);
+          lo = ring_edge(B, Cd, p2, q2, base - cross, false, Amax);
+          hi = ring_edge(B, Cd, p2, q2, base + cross, true, Amax);
         }
         const uint32_t* e = a.E + m * kBuckets;
         const int clo = bucket_code(s_coarse[m], e, lo);
@@ -495,6 +472,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         const int cl = (pclo < 0 ? 0 : pclo) >> 1, ch = pchi >> 1;
         const int nb = bh - bl + 1;
         const uint32_t* off = a.OFF + (int64_t)ms * (kPairCodes * kPairCodes + 1);
+#pragma unroll 1
         for (int b0 = 0; b0 < nb; b0 += 32) {
           // one bucket per lane; a run that starts where the lower lane's
           // ends continues it, and a head's run ends with the last lane
@@ -570,7 +548,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       // the scan's groups: the ns1 smallest estimates (ties: lower group),
       // each found by a warp minimum over (estimate bits, group) -- the
       // estimates are non-negative floats, whose bits order like them
-      const int nsel = G < a.depth ? G : a.depth;
+      const int nsel = min(min(G, a.depth), kMaxScanDepth);
       uint32_t ekey = (__float_as_uint(est) & ~31u) | (uint32_t)lane;
       for (int i = 0; i < nsel; ++i) {
         const uint32_t mn = __reduce_min_sync(kFull, ekey);
@@ -595,7 +573,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     // costlier stage runs on full batches of 32:
     //   A  128 run positions per step, 4 consecutive ones per lane, against
     //      the codes of the ns1 most selective groups (rows of CW: one 16-byte
-    //      load per group, the first three prefetched a chunk ahead);
+    //      load per group);
     //   B  one queued position per lane: its reference id (Tid2) and the
     //      codes of every key (its row of CE, one 16-byte load per 16 keys);
     //   D  one queued reference per lane: the exact test, lo_m <= A_m <= hi_m
@@ -613,7 +591,7 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     const int32_t* tid = a.Tid2 + (int64_t)ms * n;
     const uint8_t* ce = a.CE + (int64_t)ms * n * a.Ke;
     const int kc = a.Ke >> 4;                      // 16-byte words per entry row of CE
-    const int ns1 = G < a.depth ? G : a.depth;
+    const int ns1 = min(min(G, a.depth), kMaxScanDepth);
     const uint4* gd = s_gd[warp];
     const uint4* prow = reinterpret_cast<const uint4*>(a.P);
     const int kq = a.Kp >> 2;                      // 16-byte words per distance row
@@ -630,9 +608,10 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     int ha = 0, na = 0, hc = 0, nc = 0;            // queue heads and lengths
     uint32_t nfilt = 0, nexact = 0;                // entries through B and through D (statistics)
 
-    // scan position (warp-uniform): run ri, 4-aligned chunk start base in
-    // it; the current chunk's codes a0..a2 (4 positions per lane: base +
-    // 4 lane .. + 3), the next chunk prefetched during the current one's test
+    // scan position (warp-uniform): run ri, 4-aligned chunk start base in it.
+    // A chunk's codes are loaded when its step runs: holding the next chunk
+    // in registers through the other stages measured slower (it costs the
+    // compiler 12 registers everywhere in the loop)
     int ri = 0;
     while (ri < nruns && rl[ri] == 0u) ++ri;
     int base = ri < nruns ? (int)(rs[ri] & ~3u) : 0;
@@ -642,12 +621,6 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     const uint4* cw0 = reinterpret_cast<const uint4*>(cw + d0.x);
     const uint4* cw1 = reinterpret_cast<const uint4*>(cw + d1.x);
     const uint4* cw2 = reinterpret_cast<const uint4*>(cw + d2.x);
-    uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, a2 = a0;
-    if (ri < nruns && (uint32_t)(base + 4 * lane) < rs[ri] + rl[ri]) {
-      a0 = __ldg(cw0 + (base >> 2) + lane);
-      if (ns1 > 1) a1 = __ldg(cw1 + (base >> 2) + lane);
-      if (ns1 > 2) a2 = __ldg(cw2 + (base >> 2) + lane);
-    }
     for (;;) {
       const bool done = ri >= nruns;
       if (nc >= 32 || (done && nc > 0)) {
@@ -757,12 +730,12 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         while (ri2 < nruns && rl[ri2] == 0u) ++ri2;
         base2 = ri2 < nruns ? (int)(rs[ri2] & ~3u) : 0;
       }
-      uint4 b0 = make_uint4(0, 0, 0, 0), b1 = b0, b2 = b0;
-      if (ri2 < nruns && (uint32_t)(base2 + 4 * lane) < rs[ri2] + rl[ri2]) {
-        const int o = (base2 >> 2) + lane;
-        b0 = __ldg(cw0 + o);
-        if (ns1 > 1) b1 = __ldg(cw1 + o);
-        if (ns1 > 2) b2 = __ldg(cw2 + o);
+      uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, a2 = a0;
+      if ((uint32_t)(base + 4 * lane) < (uint32_t)en) {
+        const int o = (base >> 2) + lane;
+        a0 = __ldg(cw0 + o);
+        if (ns1 > 1) a1 = __ldg(cw1 + o);
+        if (ns1 > 2) a2 = __ldg(cw2 + o);
       }
       const int j0 = base + 4 * lane;
       const uint32_t v0[4] = {a0.x, a0.y, a0.z, a0.w};
@@ -784,9 +757,6 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         for (int u = 0; u < 4; ++u) inr |= (j0 + u >= st && j0 + u < en ? 1u : 0u) << u;
         bits &= inr;
       }
-      a0 = b0;
-      a1 = b1;
-      a2 = b2;
       ri = ri2;
       base = base2;
       // append the survivors to queue A: a lane's offset is the sum of the
@@ -849,6 +819,36 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
 
 template <int C, int SHAPE>
 cudaError_t launch_ring(const SparseArgs& a, bool batch, int grid, cudaStream_t s) {
+  static std::mutex mu;
+  static bool carved[kCarveDevices] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kCarveDevices) return cudaErrorInvalidDevice;
+  {
+    // the smallest shared-memory carveout that holds kCtasPerSm CTAs leaves
+    // the rest of the SM's 256 KB to L1 (the scan's gathers): once per device
+    std::lock_guard<std::mutex> lock(mu);
+    if (!carved[dev]) {
+      const void* fs[4] = {(const void*)k_sparse<C, SHAPE, true, false, false>,
+                           (const void*)k_sparse<C, SHAPE, false, false, true>,
+                           (const void*)k_sparse<C, SHAPE, false, true, false>,
+                           (const void*)k_sparse<C, SHAPE, false, false, false>};
+      int smem_max = 0;
+      e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+      if (e != cudaSuccess) return e;
+      for (const void* f : fs) {
+        cudaFuncAttributes fa;
+        e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return e;
+        const int64_t need = (int64_t)kCtasPerSm * ((int64_t)fa.sharedSizeBytes + kSmemPerCtaReserved);
+        const int pct = (int)std::min<int64_t>(100, (100 * need + smem_max - 1) / smem_max);
+        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+        if (e != cudaSuccess) return e;
+      }
+      carved[dev] = true;
+    }
+  }
   if (batch) k_sparse<C, SHAPE, true, false, false><<<grid, kWarps * 32, 0, s>>>(a);
   else if (a.unit) k_sparse<C, SHAPE, false, false, true><<<grid, kWarps * 32, 0, s>>>(a);
   else if (a.knn > 0) k_sparse<C, SHAPE, false, true, false><<<grid, kWarps * 32, 0, s>>>(a);
