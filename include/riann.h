@@ -84,7 +84,7 @@ typedef struct {
    * answered by brute force over all of R (count = n).  -1: never. */
   int32_t ring_limit;
   /* Performance knob only; results never depend on it.  0 = the index's
-   * tuned setting; 1..3 = number of 4-ring code groups the candidate scan
+   * tuned setting; 1..4 = number of 4-ring code groups the candidate scan
    * tests before it compacts survivors (see riann_autotune). */
   int32_t cap;
 } riann_params;
@@ -475,13 +475,13 @@ int riann_batch_info(riann_batch_t b, riann_batch_info_t* out);
 
 /* ------------------------------------------------------------------------
  * Autotuner: times the ring kernel's variants (query tile 4x32 or 8x16;
- * 1 to 3 code groups tested before compaction) on a sample frame and its
+ * 1 to 4 code groups tested before compaction) on a sample frame and its
  * previous field, keeps the fastest in the index, and returns every timing.
  * The variants compute identical results.
  * ------------------------------------------------------------------------ */
 typedef struct {
   int32_t tile_shape;   /* 0: 4 x 32 queries per CTA, 1: 8 x 16 */
-  int32_t depth;        /* 1..3 */
+  int32_t depth;        /* 1..4 */
   float ms;             /* mean time of one frame (riann_autotune), else -1 */
 } riann_tuning_t;
 

@@ -421,6 +421,8 @@ int build_index(const uint8_t* d_patches, int32_t n, int32_t channels, const uin
   ix->n_pad = (n + kDenseTileN - 1) / kDenseTileN * kDenseTileN;
   ix->Kp = (K + 3) / 4 * 4;
   ix->G = (K + 3) / 4;
+  // a fourth group in the scan pays once there are 16 or more (measured)
+  ix->depth = ix->G >= 16 ? 4 : 3;
   ix->nw = (n + 3) / 4 * 4;
   ix->Ke = (K + 15) / 16 * 16;
   const int D = ix->D;

@@ -36,7 +36,7 @@ enum KernelSlot { kSlotSparse = 0, kSlotDense = 1, kSlotPrep = 2, kSlots = 4 };
 
 // Ring-kernel variants the autotuner chooses between: query tile shape, and
 // the number of code groups (1..kMaxScanDepth) the scan tests per chunk.
-constexpr int kMaxScanDepth = 3;
+constexpr int kMaxScanDepth = 4;
 enum TileShape { kTile4x32 = 0, kTile8x16 = 1, kTileShapes = 2 };
 
 // Checked build (compiled with -DRIANN_CHECKED into libriann_checked.so):
@@ -95,13 +95,25 @@ struct Workspace {
 
 // Reference-tile split of the brute-force launch: with fewer than two query
 // tiles per CTA, each query tile's reference tiles are shared among nsplit
-// work items.
-__host__ __device__ inline int dense_nsplit(int64_t n_qt, int grid, int n_rt) {
+// work items.  With balance (the argmin form), more query tiles are split too
+// when that evens out the last wave: the split s of 1..4 with the fewest
+// whole-tile passes per CTA, ceil(n_qt s / grid) / s, is taken if it saves
+// more than 2 %.  (The k-NN form keeps one list per item and does not.)
+__host__ __device__ inline int dense_nsplit(int64_t n_qt, int grid, int n_rt, bool balance = false) {
   int nsplit = 1;
   if (n_qt > 0 && n_qt < 2 * (int64_t)grid) {
     nsplit = (int)((2 * (int64_t)grid + n_qt - 1) / n_qt);
-    if (nsplit > n_rt) nsplit = n_rt;
+  } else if (balance && n_qt > 0) {
+    double best = (double)((n_qt + grid - 1) / grid);
+    for (int sp = 2; sp <= 4; ++sp) {
+      const double w = (double)((n_qt * sp + grid - 1) / grid) / sp;
+      if (w < 0.98 * best) {
+        best = w;
+        nsplit = sp;
+      }
+    }
   }
+  if (nsplit > n_rt) nsplit = n_rt;
   return nsplit;
 }
 
@@ -158,7 +170,8 @@ struct Index {
 
   // ring-kernel tuning (riann_autotune sets them; these are the defaults)
   int tile_shape = kTile4x32;
-  int depth = 3;                  // scan depth (code groups tested before compaction, 1..kMaxScanDepth)
+  int depth = 3;                  // scan depth (code groups tested before compaction, 1..kMaxScanDepth);
+                                  // set at build: 4 for 16 or more groups, else 3
 
   // optional per-kernel timing with CUDA events recorded on the launch stream
   bool profile = false;

@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
   const int64_t Qd = a.count ? (int64_t)*a.count : a.Qfix;
   const int64_t n_qt = (Qd + kM - 1) / kM;
   const int n_rt = a.n_pad / G::BN;
-  const int nsplit = dense_nsplit(n_qt, (int)gridDim.x, n_rt);
+  const int nsplit = dense_nsplit(n_qt, (int)gridDim.x, n_rt, !KNN);
   const int per = (n_rt + nsplit - 1) / nsplit;
   const int64_t n_items = n_qt * nsplit;
   if ((int64_t)blockIdx.x >= n_items) return;   // uniform for the whole CTA

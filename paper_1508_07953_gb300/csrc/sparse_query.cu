@@ -615,12 +615,6 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     int ri = 0;
     while (ri < nruns && rl[ri] == 0u) ++ri;
     int base = ri < nruns ? (int)(rs[ri] & ~3u) : 0;
-    const uint4 d0 = gd[0];
-    const uint4 d1 = gd[ns1 > 1 ? 1 : 0];
-    const uint4 d2 = gd[ns1 > 2 ? 2 : 0];
-    const uint4* cw0 = reinterpret_cast<const uint4*>(cw + d0.x);
-    const uint4* cw1 = reinterpret_cast<const uint4*>(cw + d1.x);
-    const uint4* cw2 = reinterpret_cast<const uint4*>(cw + d2.x);
     for (;;) {
       const bool done = ri >= nruns;
       if (nc >= 32 || (done && nc > 0)) {
@@ -730,25 +724,28 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         while (ri2 < nruns && rl[ri2] == 0u) ++ri2;
         base2 = ri2 < nruns ? (int)(rs[ri2] & ~3u) : 0;
       }
-      uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, a2 = a0;
-      if ((uint32_t)(base + 4 * lane) < (uint32_t)en) {
-        const int o = (base >> 2) + lane;
-        a0 = __ldg(cw0 + o);
-        if (ns1 > 1) a1 = __ldg(cw1 + o);
-        if (ns1 > 2) a2 = __ldg(cw2 + o);
+      uint4 av[kMaxScanDepth];
+      const bool lin = (uint32_t)(base + 4 * lane) < (uint32_t)en;
+#pragma unroll
+      for (int g = 0; g < kMaxScanDepth; ++g) {
+        av[g] = make_uint4(0, 0, 0, 0);
+        if (g < ns1 && lin) av[g] = __ldg(reinterpret_cast<const uint4*>(cw + gd[g].x) + (base >> 2) + lane);
       }
       const int j0 = base + 4 * lane;
-      const uint32_t v0[4] = {a0.x, a0.y, a0.z, a0.w};
-      const uint32_t v1[4] = {a1.x, a1.y, a1.z, a1.w};
-      const uint32_t v2[4] = {a2.x, a2.y, a2.z, a2.w};
+      uint32_t p[4] = {kHi, kHi, kHi, kHi};
+#pragma unroll
+      for (int g = 0; g < kMaxScanDepth; ++g) {
+        if (g < ns1) {
+          const uint32_t lo = gd[g].y, h1 = gd[g].z;
+          p[0] &= (av[g].x - lo) & ~(av[g].x - h1);
+          p[1] &= (av[g].y - lo) & ~(av[g].y - h1);
+          p[2] &= (av[g].z - lo) & ~(av[g].z - h1);
+          p[3] &= (av[g].w - lo) & ~(av[g].w - h1);
+        }
+      }
       unsigned bits = 0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        uint32_t p = (v0[u] - d0.y) & ~(v0[u] - d0.z);
-        if (ns1 > 1) p &= (v1[u] - d1.y) & ~(v1[u] - d1.z);
-        if (ns1 > 2) p &= (v2[u] - d2.y) & ~(v2[u] - d2.z);
-        bits |= ((p & kHi) == kHi ? 1u : 0u) << u;
-      }
+      for (int u = 0; u < 4; ++u) bits |= ((p[u] & kHi) == kHi ? 1u : 0u) << u;
       // only a run's first and last chunk hold positions outside it (a
       // warp-uniform test: the middle chunks skip the range check)
       if (base < st || base + 128 > en) {

@@ -150,7 +150,7 @@ def test_tiny_chain_all_queries(rt, tiny, alpha, limit, scan):
 def test_cap_does_not_change_output(rt, tiny):
     R, KP, frames = tiny
     base = gpu_chain(rt, R, KP, frames[:3], make_params(rt, len(R)))
-    for cap in (1, 2, 3):
+    for cap in (1, 2, 3, 4):
         other = gpu_chain(rt, R, KP, frames[:3], make_params(rt, len(R), cap=cap))
         for t in range(3):
             for k in range(3):
@@ -204,7 +204,7 @@ def test_invalid_arguments_rejected(rt):
     idx = rt.riann_build_reference_index(_dev(R), _dev(KP))
     out = torch.empty((5, 5), dtype=torch.int32, device="cuda")
     for bad in (dict(alpha_den=0), dict(alpha_den=9), dict(alpha_num=-1), dict(alpha_num=65, alpha_den=8),
-                dict(ring_limit=-2), dict(cap=-1), dict(cap=4)):
+                dict(ring_limit=-2), dict(cap=-1), dict(cap=5)):
         p = make_params(rt, 64)
         for k, v in bad.items():
             setattr(p, k, v)

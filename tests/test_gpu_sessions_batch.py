@@ -193,14 +193,14 @@ def test_tuning_variants_identical_and_autotune(rt, tiny):
     a0, _, _ = rt.annf(idx, _dev(frames[0]), None, params)
     outs = []
     for shape in (0, 1):
-        for depth in (1, 2, 3):
+        for depth in (1, 2, 3, 4):
             rt.riann_set_tuning(idx, shape, depth)
             outs.append([x.cpu().numpy() for x in rt.annf(idx, _dev(frames[1]), a0, params)])
     for o in outs[1:]:
         for k in range(3):
             assert np.array_equal(o[k], outs[0][k])
     res = rt.riann_autotune(idx, params, _dev(frames[1]), a0, iters=2)
-    assert len(res) == 6 and all(r["ms"] > 0 for r in res)
+    assert len(res) == 8 and all(r["ms"] > 0 for r in res)
     best = min(res, key=lambda r: r["ms"])
     t = rt.riann_get_tuning(idx)
     assert (t["tile_shape"], t["depth"]) == (best["tile_shape"], best["depth"])
