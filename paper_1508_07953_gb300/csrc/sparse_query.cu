@@ -571,7 +571,8 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
     // a3 + a4, a cascade of filters over the runs; each stage compacts its
     // survivors into a per-warp queue (warp ballots), so that the next,
     // costlier stage runs on full batches of 32:
-    //   A  128 run positions per step, 4 consecutive ones per lane, against
+    //   A  32 words of 4 run positions per step (one per lane; a step that
+    //      reaches the end of a run continues in the next one), against
     //      the codes of the ns1 most selective groups (rows of CW: one 16-byte
     //      load per group);
     //   B  one queued position per lane: its reference id (Tid2) and the
@@ -716,22 +717,43 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
         continue;
       }
       if (done) break;
-      // ---- A: the chunk of 128 positions at base of run ri ----
+      // ---- A: 32 words (4 positions each) from word base of run ri; when run
+      // ri ends inside them, the rest come from the next non-empty run ----
       const int st = (int)rs[ri], en = st + (int)rl[ri];
+      const int left = ((en - 1) >> 2) - (base >> 2) + 1;   // words of run ri from base on (>= 1)
       int ri2 = ri, base2 = base + 128;
-      if (base2 >= en) {                           // the next non-empty run
+      int j0 = base + 4 * lane, lst = st, len = en;        // this lane's word and its run
+      bool lin = lane < left;
+      const bool edge = base < st || left <= 32;           // a run boundary inside the chunk
+      if (left <= 32) {
         ++ri2;
         while (ri2 < nruns && rl[ri2] == 0u) ++ri2;
-        base2 = ri2 < nruns ? (int)(rs[ri2] & ~3u) : 0;
+        base2 = 0;
+        if (ri2 < nruns) {
+          const int st2 = (int)rs[ri2], en2 = st2 + (int)rl[ri2];
+          const int w2 = ((en2 - 1) >> 2) - (st2 >> 2) + 1;      // words of run ri2
+          const int take2 = 32 - left;
+          if (lane >= left) {
+            j0 = (st2 & ~3) + 4 * (lane - left);
+            lst = st2;
+            len = en2;
+            lin = lane - left < w2;
+          }
+          if (w2 > take2) {
+            base2 = (st2 & ~3) + 4 * take2;                       // run ri2 continues
+          } else {
+            ++ri2;
+            while (ri2 < nruns && rl[ri2] == 0u) ++ri2;
+            base2 = ri2 < nruns ? (int)(rs[ri2] & ~3u) : 0;
+          }
+        }
       }
       uint4 av[kMaxScanDepth];
-      const bool lin = (uint32_t)(base + 4 * lane) < (uint32_t)en;
 #pragma unroll
       for (int g = 0; g < kMaxScanDepth; ++g) {
         av[g] = make_uint4(0, 0, 0, 0);
-        if (g < ns1 && lin) av[g] = __ldg(reinterpret_cast<const uint4*>(cw + gd[g].x) + (base >> 2) + lane);
+        if (g < ns1 && lin) av[g] = __ldg(reinterpret_cast<const uint4*>(cw + gd[g].x) + (j0 >> 2));
       }
-      const int j0 = base + 4 * lane;
       uint32_t p[4] = {kHi, kHi, kHi, kHi};
 #pragma unroll
       for (int g = 0; g < kMaxScanDepth; ++g) {
@@ -746,12 +768,12 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
       unsigned bits = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) bits |= ((p[u] & kHi) == kHi ? 1u : 0u) << u;
-      // only a run's first and last chunk hold positions outside it (a
-      // warp-uniform test: the middle chunks skip the range check)
-      if (base < st || base + 128 > en) {
+      // only chunks with a run boundary hold positions outside their runs (a
+      // warp-uniform test: the chunks inside a run skip the range check)
+      if (edge) {
         unsigned inr = 0;
 #pragma unroll
-        for (int u = 0; u < 4; ++u) inr |= (j0 + u >= st && j0 + u < en ? 1u : 0u) << u;
+        for (int u = 0; u < 4; ++u) inr |= (lin && j0 + u >= lst && j0 + u < len ? 1u : 0u) << u;
         bits &= inr;
       }
       ri = ri2;
