@@ -62,11 +62,22 @@ __host__ __device__ constexpr int norm_bytes() { return Cfg<C>::FOLD ? Cfg<C>::B
 template <int C>
 __host__ __device__ constexpr int ones_bytes() { return Cfg<C>::FOLD ? kM * 32 : 0; }
 
-template <int C>
+// k-NN: each epilogue thread stages a 32-column chunk of its row in shared
+// memory (36-float stride: conflict-free 16-byte stores) when the chunk holds
+// list candidates, so that a candidate's score is one load to fetch
+constexpr int kKnnStageStride = 36;
+template <bool KNN>
+__host__ __device__ constexpr int knn_stage_bytes() { return KNN ? kEpiWarps * 32 * kKnnStageStride * 4 : 0; }
+
+// pipeline stages: the RGB k-NN form gives one up to its staging area
+template <int C, bool KNN>
+__host__ __device__ constexpr int stages() { return (C == 3 && KNN) ? Cfg<C>::STAGES - 1 : Cfg<C>::STAGES; }
+
+template <int C, bool KNN>
 __host__ __device__ constexpr int smem_bytes() {
   using G = Cfg<C>;
-  return 1024 /* alignment slack */ + G::ATOMS * kM * 128 + G::STAGES * G::ATOMS * G::BN * 128 +
-         G::STAGES * norm_bytes<C>() + ones_bytes<C>() + 256;
+  return 1024 /* alignment slack */ + G::ATOMS * kM * 128 + stages<C, KNN>() * G::ATOMS * G::BN * 128 +
+         stages<C, KNN>() * norm_bytes<C>() + ones_bytes<C>() + 256 + knn_stage_bytes<KNN>();
 }
 
 struct TcArgs {
@@ -265,16 +276,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = smem;                                        // [ATOMS][128][128 B]
   uint8_t* sB = sA + G::ATOMS * kM * 128;                    // [STAGES][ATOMS][BN][128 B]
-  uint8_t* sN = sB + G::STAGES * G::ATOMS * G::BN * 128;     // gray: [STAGES][BN x 32 B] norm terms
-  uint8_t* sOnes = sN + G::STAGES * norm_bytes<C>();         // gray: [128 x 32 B] ones in columns 0..2
+  constexpr int NST = stages<C, KNN>();
+  uint8_t* sN = sB + NST * G::ATOMS * G::BN * 128;           // gray: [STAGES][BN x 32 B] norm terms
+  uint8_t* sOnes = sN + NST * norm_bytes<C>();               // gray: [128 x 32 B] ones in columns 0..2
   uint64_t* bars = reinterpret_cast<uint64_t*>(sOnes + ones_bytes<C>());
   uint64_t* full = bars;
-  uint64_t* empty = full + G::STAGES;
-  uint64_t* tfull = empty + G::STAGES;
+  uint64_t* empty = full + NST;
+  uint64_t* tfull = empty + NST;
   uint64_t* tempty = tfull + 2;
   uint64_t* afull = tempty + 2;
   uint64_t* aempty = afull + 1;
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(aempty + 1);
+  float* sK = reinterpret_cast<float*>(reinterpret_cast<uint8_t*>(bars) + 256);   // k-NN staging rows
   volatile int* s_abort = reinterpret_cast<volatile int*>(s_tmem + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -297,7 +310,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor cores
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < G::STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -351,16 +364,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
             tma_load_2d(sB + (stage * G::ATOMS + at) * G::BN * 128, &a.tmB, &full[stage], 64 * at, rt * G::BN);
           if (G::FOLD)
             bulk_load(sN + stage * norm_bytes<C>(), a.rn + (int64_t)rt * G::BN * 16, norm_bytes<C>(), &full[stage]);
-          if (++stage == G::STAGES) {
+          if (++stage == NST) {
             stage = 0;
             phase ^= 1;
           }
         }
       }
       // tail: every stage released and the last query tile consumed before exit
-      for (int s = 0; s < G::STAGES && ok; ++s) {
+      for (int s = 0; s < NST && ok; ++s) {
         ok = mbar_wait(&empty[stage], phase ^ 1, s_abort, lim);
-        if (++stage == G::STAGES) {
+        if (++stage == NST) {
           stage = 0;
           phase ^= 1;
         }
@@ -392,7 +405,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
           if (G::FOLD) tc_mma(d, plain_desc(sOnes), plain_desc(sN + stage * norm_bytes<C>()), IDESC, 1u);
           tc_commit(&empty[stage]);
           tc_commit(&tfull[acc]);
-          if (++stage == G::STAGES) {
+          if (++stage == NST) {
             stage = 0;
             phase ^= 1;
           }
@@ -495,15 +508,17 @@ __global__ void __launch_bounds__(kThreads, 1) k_dense_tc(const __grid_constant_
               // lane's work follows its own count (the warp waits for the
               // largest), not all 32 columns
               const float thr = ls[(KNN ? kKnnMax : 1) - 1];
+              float* srow = sK + ((warp - 4) * 32 + lane) * kKnnStageStride;   // this thread's own row
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                reinterpret_cast<float4*>(srow)[j] = make_float4(x[4 * j], x[4 * j + 1], x[4 * j + 2], x[4 * j + 3]);
               uint32_t mask = 0;
 #pragma unroll
               for (int j = 0; j < 32; ++j) mask |= (x[j] < thr ? 1u : 0u) << j;
               while (mask) {
                 const int jj = __ffs(mask) - 1;
                 mask &= mask - 1;
-                float v = x[0];
-#pragma unroll
-                for (int j = 1; j < 32; ++j) v = jj == j ? x[j] : v;
+                const float v = srow[jj];
                 if (v < ls[(KNN ? kKnnMax : 1) - 1]) knn_insert(ls, li, v, col0 + jj);
               }
             }
@@ -700,12 +715,12 @@ cudaError_t launch_tc(const TcArgs& t, cudaStream_t s) {
   {
     std::lock_guard<std::mutex> lock(mu);
     if (!attr[dev]) {
-      e = cudaFuncSetAttribute(k_dense_tc<C, KNN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<C>());
+      e = cudaFuncSetAttribute(k_dense_tc<C, KNN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes<C, KNN>());
       if (e != cudaSuccess) return e;
       attr[dev] = true;
     }
   }
-  k_dense_tc<C, KNN><<<sm_count(), kThreads, smem_bytes<C>(), s>>>(t);
+  k_dense_tc<C, KNN><<<sm_count(), kThreads, smem_bytes<C, KNN>(), s>>>(t);
   return cudaGetLastError();
 }
 
