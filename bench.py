@@ -197,7 +197,7 @@ def ring_traffic_model(stats: dict, H: int, W: int, C: int, K: int, depth: int) 
 RING_CAPTURE = {"dram_bytes": 4.24e9 + 29.97e6, "l2_bytes": 71.60e9, "frame": 21, "tile_shape": 0, "depth": 4,
                 "sha256": {
                            "paper_1508_07953_gb300/csrc/sparse_query.cu":
-                           "26fe490c570d08fed60f4390ff78a9ec53a76a0df81186d1bbd76ff772060720",
+                           "f4424fe579fb4d5122d81c6f14e79e0f791819f6027098e661ba272de5f7b017",
                            "paper_1508_07953_gb300/csrc/common.cuh":
                            "1c2e02581770b8eab77c8be0ceca4283d6359b607c9f32ccec242b7a3ef66556",
                            "paper_1508_07953_gb300/csrc/unit.cuh":

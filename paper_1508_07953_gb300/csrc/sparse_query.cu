@@ -87,8 +87,8 @@ __device__ __forceinline__ uint32_t sq4(const uint32_t* q, uint4 u, uint32_t acc
 }
 
 // code(x) = (number of bucket edges <= x) - 1, in [-1, 255].  Two levels:
-// every 4th edge in shared memory (64 per key), then the 4 edges of one
-// 16-byte segment from global memory.
+// every 8th edge in shared memory (32 per key), then the 8 edges of one
+// 32-byte segment from global memory.
 __device__ __forceinline__ int bucket_code(const uint32_t* __restrict__ coarse, const uint32_t* __restrict__ e,
                                            uint32_t x) {
   int c = 0;   // coarse edges <= x
