@@ -454,6 +454,7 @@ int build_index(const uint8_t* d_patches, int32_t n, int32_t channels, const uin
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(ix->KP, d_keypoints, (size_t)K * D, cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess) e = launch_index_build(*ix, s);
+  if (e == cudaSuccess) e = ring_prepare(channels);
   if (e != cudaSuccess) {
     cudaGetLastError();
     cudaStreamSynchronize(s);

@@ -254,6 +254,8 @@ cudaError_t launch_exact_nn_noalloc(const DenseArgs& a, Index& ix, cudaStream_t 
 // parameters or (batched form) in a device array
 int ring_tile_rows(int shape);
 int ring_tile_cols(int shape);
+// per-device launch set-up of the ring kernels for C channels (outside any capture)
+cudaError_t ring_prepare(int C);
 cudaError_t launch_sparse(const SparseArgs& a, int C, int shape, cudaStream_t s);
 cudaError_t launch_sparse_item(const SparseArgs& a, int C, int shape, int tiles, cudaStream_t s);
 

@@ -836,38 +836,44 @@ __global__ void __launch_bounds__(kWarps * 32, kCtasPerSm) k_sparse(const __grid
   }
 }
 
+// The smallest shared-memory carveout that holds kCtasPerSm CTAs leaves the
+// rest of the SM's 256 KB to L1 (the scan's gathers).  Set once per device
+// for the four kernels of a (C, SHAPE), under a lock; index building calls it
+// (never inside a stream capture), the launches only check the flag.
 template <int C, int SHAPE>
-cudaError_t launch_ring(const SparseArgs& a, bool batch, int grid, cudaStream_t s) {
+cudaError_t carve_ring() {
   static std::mutex mu;
   static bool carved[kCarveDevices] = {};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kCarveDevices) return cudaErrorInvalidDevice;
-  {
-    // the smallest shared-memory carveout that holds kCtasPerSm CTAs leaves
-    // the rest of the SM's 256 KB to L1 (the scan's gathers): once per device
-    std::lock_guard<std::mutex> lock(mu);
-    if (!carved[dev]) {
-      const void* fs[4] = {(const void*)k_sparse<C, SHAPE, true, false, false>,
-                           (const void*)k_sparse<C, SHAPE, false, false, true>,
-                           (const void*)k_sparse<C, SHAPE, false, true, false>,
-                           (const void*)k_sparse<C, SHAPE, false, false, false>};
-      int smem_max = 0;
-      e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-      if (e != cudaSuccess) return e;
-      for (const void* f : fs) {
-        cudaFuncAttributes fa;
-        e = cudaFuncGetAttributes(&fa, f);
-        if (e != cudaSuccess) return e;
-        const int64_t need = (int64_t)kCtasPerSm * ((int64_t)fa.sharedSizeBytes + kSmemPerCtaReserved);
-        const int pct = (int)std::min<int64_t>(100, (100 * need + smem_max - 1) / smem_max);
-        e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
-        if (e != cudaSuccess) return e;
-      }
-      carved[dev] = true;
-    }
+  std::lock_guard<std::mutex> lock(mu);
+  if (carved[dev]) return cudaSuccess;
+  const void* fs[4] = {(const void*)k_sparse<C, SHAPE, true, false, false>,
+                       (const void*)k_sparse<C, SHAPE, false, false, true>,
+                       (const void*)k_sparse<C, SHAPE, false, true, false>,
+                       (const void*)k_sparse<C, SHAPE, false, false, false>};
+  int smem_max = 0;
+  e = cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e != cudaSuccess) return e;
+  for (const void* f : fs) {
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, f);
+    if (e != cudaSuccess) return e;
+    const int64_t need = (int64_t)kCtasPerSm * ((int64_t)fa.sharedSizeBytes + kSmemPerCtaReserved);
+    const int pct = (int)std::min<int64_t>(100, (100 * need + smem_max - 1) / smem_max);
+    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    if (e != cudaSuccess) return e;
   }
+  carved[dev] = true;
+  return cudaSuccess;
+}
+
+template <int C, int SHAPE>
+cudaError_t launch_ring(const SparseArgs& a, bool batch, int grid, cudaStream_t s) {
+  cudaError_t e = carve_ring<C, SHAPE>();
+  if (e != cudaSuccess) return e;
   if (batch) k_sparse<C, SHAPE, true, false, false><<<grid, kWarps * 32, 0, s>>>(a);
   else if (a.unit) k_sparse<C, SHAPE, false, false, true><<<grid, kWarps * 32, 0, s>>>(a);
   else if (a.knn > 0) k_sparse<C, SHAPE, false, true, false><<<grid, kWarps * 32, 0, s>>>(a);
@@ -883,6 +889,12 @@ cudaError_t launch_any(const SparseArgs& a, int C, int shape, bool batch, int gr
 }
 
 }  // namespace
+
+cudaError_t ring_prepare(int C) {
+  cudaError_t e = C == 1 ? carve_ring<1, kTile4x32>() : carve_ring<3, kTile4x32>();
+  if (e == cudaSuccess) e = C == 1 ? carve_ring<1, kTile8x16>() : carve_ring<3, kTile8x16>();
+  return e;
+}
 
 int ring_tile_rows(int shape) { return shape == kTile8x16 ? 8 : 4; }
 int ring_tile_cols(int shape) { return shape == kTile8x16 ? 16 : 32; }

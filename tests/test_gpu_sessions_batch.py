@@ -205,3 +205,40 @@ def test_tuning_variants_identical_and_autotune(rt, tiny):
     t = rt.riann_get_tuning(idx)
     assert (t["tile_shape"], t["depth"]) == (best["tile_shape"], best["depth"])
     idx.close()
+
+
+def test_first_ring_launch_inside_a_graph_capture():
+    # a fresh process whose first ring launch is a captured batched tick: the
+    # ring kernels' per-device launch set-up happens at index build, outside
+    # any capture; the captured ticks equal plain per-frame calls made after
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = """
+import numpy as np, torch, synth
+from paper_1508_07953_gb300 import riann as rt
+w = synth.WORKLOADS["tiny"]
+R = synth.workload_reference(w); KP = synth.workload_keypoints(w, R)
+idx = rt.riann_build_reference_index(torch.from_numpy(R).cuda(), torch.from_numpy(KP).cuda())
+params = rt.riann_default_params(len(R))
+vids = [synth.Video(synth.VideoSpec(H, W, 1, 70 + i, speeds=(0.5, 2.0))) for i, (H, W) in enumerate([(40, 56), (72, 130)])]
+sess = [rt.riann_session_create(idx, 40, 56), rt.riann_session_create(idx, 72, 130)]
+b = rt.riann_batch_create(idx, 4, 20000, use_graph=True)
+got = []
+for t in range(3):
+    rt.riann_batch_run(b, params, sess, [torch.from_numpy(v.frame(t)).cuda() for v in vids])
+    got.append([rt.session_result(s)[0].cpu().numpy() for s in sess])
+assert b.info().graph_builds == 1
+for i, v in enumerate(vids):
+    prev = None
+    for t in range(3):
+        a, _, _ = rt.annf(idx, torch.from_numpy(v.frame(t)).cuda(), prev, params)
+        assert np.array_equal(a.cpu().numpy(), got[t][i]), (i, t)
+        prev = a
+assert rt.riann_status(idx) == 0
+print("ok")
+"""
+    r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip().endswith("ok")
