@@ -121,7 +121,7 @@ int riann_build_reference_index(const uint8_t* d_patches, int32_t n, int32_t cha
  * distance to the key point, 7-bit bucket of the distance to a partner key
  * point), then as in the key's sorted list; a query whose seed ring is that
  * key's scans only the buckets where both rings' code ranges meet.
- *   scan_order  RIANN_SCAN_AUTO: RIANN_SCAN_PAIRS for n >= 32768, else
+ *   scan_order  RIANN_SCAN_AUTO: RIANN_SCAN_PAIRS for n >= 16384, else
  *                 RIANN_SCAN_SINGLE (smaller buckets fragment the runs);
  *               RIANN_SCAN_PAIRS: partner = the farthest other key point;
  *               RIANN_SCAN_SINGLE: partner = the key itself (the pair order is
@@ -353,7 +353,7 @@ int riann_measure_int_peak(riann_stream_t stream, double* ops_per_s);
  * results.  The index is unusable afterwards: destroy it.  Synchronous.
  * Errors: RIANN_ERR_INVALID_ARG unless 0 <= key < K - 1 and 1 <= extra <= 64;
  * RIANN_ERR_UNSUPPORTED unless the index scans in pair order
- * (RIANN_SCAN_PAIRS, or n >= 32768).
+ * (RIANN_SCAN_PAIRS, or n >= 16384).
  */
 int riann_test_corrupt_offsets(riann_index_t idx, int32_t key, int32_t extra);
 

@@ -138,7 +138,7 @@ def tiny():
                                          ((1, 1), -1), ((0, 1), -1), ((3, 8), 64)])
 def test_tiny_chain_all_queries(rt, tiny, alpha, limit, scan):
     # "pairs": the scan of a second key's buckets, which the index uses for
-    # n >= 32768 only, forced on the tiny index
+    # n >= 16384 only, forced on the tiny index
     R, KP, frames = tiny
     params = make_params(rt, len(R), alpha, limit)
     g = gpu_chain(rt, R, KP, frames, params, None if scan == "auto" else rt.RIANN_SCAN_PAIRS)
@@ -246,13 +246,13 @@ def test_720p_rgb_full_frames_sampled(rt):
     _sampled_chain(rt, synth.WORKLOADS["720p_rgb"], 0, 3, 600, 21)
 
 
-def test_720p_rgb_pair_scan_sampled(rt):
-    # the pair scan (used for n >= 32768) forced on the 16384-patch RGB index
-    _sampled_chain(rt, synth.WORKLOADS["720p_rgb"], 0, 3, 600, 23, rt.RIANN_SCAN_PAIRS)
+def test_720p_rgb_single_key_scan_sampled(rt):
+    # the single-key scan (used for n < 16384) forced on the 16384-patch RGB index
+    _sampled_chain(rt, synth.WORKLOADS["720p_rgb"], 0, 3, 600, 23, rt.RIANN_SCAN_SINGLE)
 
 
 def test_1080p_single_key_scan_sampled(rt):
-    # the single-key scan (used for n < 32768) forced on the 65536-patch index
+    # the single-key scan (used for n < 16384) forced on the 65536-patch index
     _sampled_chain(rt, synth.WORKLOADS["1080p"], 20, 23, 400, 24, rt.RIANN_SCAN_SINGLE)
 
 
